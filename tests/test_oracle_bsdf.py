@@ -1,0 +1,88 @@
+"""Oracle material model against mathematics it must satisfy (not against itself)."""
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import orc
+
+N = np.array([0.3, 0.5, 0.8]) / np.linalg.norm([0.3, 0.5, 0.8])
+
+
+def _upper(rng, n, min_cos=0.05):
+    while True:
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        if v @ n > min_cos:
+            return v
+
+
+@pytest.mark.parametrize("mtype", [0, 1])
+def test_derivatives_match_central_differences(oracle_lib, mtype):
+    rng = np.random.default_rng(1 + mtype)
+    for _ in range(100):
+        th = np.array([*rng.uniform(0.05, 0.95, 3), rng.uniform(0, 1), rng.uniform(0.1, 1)])
+        wo, wi = _upper(rng, N), _upper(rng, N)
+        _, df, _ = orc.bsdf(mtype, th, N, wo, wi)
+        for j in range(5):
+            h = 1e-6
+            tp, tm = th.copy(), th.copy()
+            tp[j] += h
+            tm[j] -= h
+            fd = (orc.bsdf(mtype, tp, N, wo, wi)[0] - orc.bsdf(mtype, tm, N, wo, wi)[0]) / (2 * h)
+            assert np.allclose(df[j], fd, rtol=1e-6, atol=1e-7 * max(1.0, np.abs(fd).max()))
+
+
+def test_reciprocity(oracle_lib):
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        th = np.array([*rng.uniform(0.05, 0.95, 3), rng.uniform(0, 1), rng.uniform(0.1, 1)])
+        wo, wi = _upper(rng, N), _upper(rng, N)
+        assert np.allclose(orc.bsdf(1, th, N, wo, wi)[0], orc.bsdf(1, th, N, wi, wo)[0], rtol=1e-12)
+
+
+def test_lambert_value_and_hemisphere_below_is_zero(oracle_lib):
+    th = np.array([0.2, 0.5, 0.9, 0, 0])
+    f, _, pdf = orc.bsdf(0, th, N, N, N)
+    assert np.allclose(f, th[:3] / np.pi)
+    assert np.isclose(pdf, 1 / np.pi)
+    f, _, pdf = orc.bsdf(0, th, N, N, -N)
+    assert np.all(f == 0) and pdf == 0
+
+
+@pytest.mark.parametrize("alpha", [0.05, 0.3, 0.8])
+def test_ggx_normalisation(oracle_lib, alpha):
+    """int D(h) cos(theta_h) dw_h = 1 (Walter et al. 2007); D read back through f with metal=1, F0=1 at
+    normal incidence: for wo = wi = n, f = D G1^2 F / 4 with F = 1 and G1(1) = 1."""
+    r = np.sqrt(alpha)
+    th = np.array([1.0, 1.0, 1.0, 1.0, r])
+    z = np.array([0.0, 0.0, 1.0])
+
+    def D_of(ct):
+        s = np.sqrt(max(0.0, 1 - ct * ct))
+        h = np.array([s, 0.0, ct])
+        # wo = wi = h: f = D(h) * F(1) * G1(ct)^2 / (4 ct^2), F(1) = F0 = 1
+        f, _, _ = orc.bsdf(1, th, z, h, h)
+        a2 = alpha * alpha
+        g1 = 2 * ct / (ct + np.sqrt(a2 + (1 - a2) * ct * ct))
+        return f[0] * 4 * ct * ct / (g1 * g1)
+
+    val, _ = integrate.quad(lambda t: D_of(np.cos(t)) * np.cos(t) * np.sin(t) * 2 * np.pi, 0, np.pi / 2,
+                            limit=400, points=[0.01, 0.1])
+    assert abs(val - 1.0) < 1e-5, val
+
+
+@pytest.mark.parametrize("th", [[0.5, 0.5, 0.5, 0.0, 0.3], [0.2, 0.4, 0.6, 0.6, 0.8], [0.7, 0.7, 0.7, 0.8, 0.4]])
+def test_sampler_matches_pdf(oracle_lib, th):
+    """E[1{valid} / pdf(w)] over sampled w equals the upper hemisphere's solid angle 2*pi
+    exactly when the sampling routine draws with the density that pdf() returns."""
+    th = np.array(th)
+    rng = np.random.default_rng(7)
+    wo = _upper(rng, N, 0.3)
+    n = 20000
+    acc = np.zeros(n)
+    for i, (ul, u1, u2) in enumerate(rng.random((n, 3))):
+        ok, wi = orc.bsdf_sample(1, th, N, wo, ul, u1, u2)
+        if ok:
+            acc[i] = 1.0 / orc.bsdf(1, th, N, wo, wi)[2]
+    mean, se = acc.mean(), acc.std() / np.sqrt(n)
+    assert abs(mean - 2 * np.pi) < 5 * se + 1e-3, (mean, se)

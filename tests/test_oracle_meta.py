@@ -1,0 +1,161 @@
+"""Oracle meta-estimator / Moment2 / Adam against closed forms, invariants and a library Adam."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import meta
+
+
+def test_moment2_closed_form():
+    """Start-up-corrected EMA: m2_n = sum_j (1-b) b^(n-j) x_j^2 / (1 - b^n)."""
+    rng = np.random.default_rng(0)
+    for b in (0.5, 0.9, 0.99):
+        x = rng.normal(size=20)
+        m2, cnt = 0.0, 0
+        for n in range(1, 21):
+            m2, cnt = meta.moment2_step(m2, cnt, x[n - 1], b)
+            j = np.arange(1, n + 1)
+            closed = np.sum((1 - b) * b ** (n - j) * x[:n] ** 2) / (1 - b ** n)
+            assert np.isclose(m2, closed, rtol=1e-12)
+        assert cnt == 20
+
+
+def test_first_step_is_sign_step():
+    """i = 0: alpha_{-1} = -inf clips alpha to 0, so <F_0>_M = <F_0>, Var = F^2 and
+    dpi = -eta F / (|F| + eps)."""
+    h = meta.Hyper(lr=0.01)
+    F = np.array([0.3, -2.0, 1e-3, 0.0])
+    st = meta.MetaState.zeros(F.shape)
+    pi1, n2, alpha = meta.meta_update(np.zeros(4), F, np.zeros(4), st, h, 0.0)
+    assert np.all(alpha == 0)
+    assert np.allclose(st.mean, F) and np.allclose(st.var, F * F)
+    assert np.allclose(pi1, -h.lr * F / (np.abs(F) + h.eps), rtol=1e-14)
+    assert np.isclose(n2, np.sum(pi1 ** 2))
+
+
+def test_perfect_average_closed_form():
+    """|F_i| = c constant and dF = 0: Var[<F>] = c^2 for any decay, Var_dF = 0, so alpha_i = i/(i+1)
+    (unclipped value equals the clip bound) and the meta-estimate is the running arithmetic mean
+    of F_0..F_i with variance c^2/(i+1) (the 'perfect average' that Eq. alpha_clip bounds)."""
+    rng = np.random.default_rng(1)
+    c = 0.7
+    h = meta.Hyper(lr=1e-3, beta_f=0.9, beta_d=0.5)
+    st = meta.MetaState.zeros((50,))
+    Fs = []
+    pi = np.zeros(50)
+    n2 = 0.0
+    for i in range(30):
+        F = c * rng.choice([-1.0, 1.0], size=50)
+        Fs.append(F)
+        pi, n2, alpha = meta.meta_update(pi, F, np.zeros(50), st, h, n2)
+        assert np.allclose(alpha, i / (i + 1), rtol=1e-12)
+        assert np.allclose(st.mean, np.mean(Fs, 0), rtol=1e-10, atol=1e-14)
+        assert np.allclose(st.var, c * c / (i + 1), rtol=1e-10)
+
+
+def test_telescoping_with_consistent_differences():
+    """If dF_i = F_i - F_{i-1} exactly, Eq. recurrent_meta gives <F_i>_M = F_i for any alphas."""
+    rng = np.random.default_rng(2)
+    h = meta.Hyper(lr=1e-2)
+    F_prev = rng.normal(size=64)
+    st = meta.MetaState.zeros((64,))
+    pi, n2 = np.zeros(64), 0.0
+    pi, n2, _ = meta.meta_update(pi, F_prev, np.zeros(64), st, h, n2)
+    for i in range(1, 25):
+        F = F_prev + 0.3 * rng.normal(size=64)
+        pi, n2, _ = meta.meta_update(pi, F, F - F_prev, st, h, n2)
+        assert np.allclose(st.mean, F, rtol=1e-9, atol=1e-12)
+        F_prev = F
+
+
+def test_alpha_bounded_by_iteration():
+    """Eq. alpha_clip_2 from alpha_{-1} = -inf implies Eq. alpha_clip: alpha_i <= 1 - 1/(i+1)."""
+    rng = np.random.default_rng(3)
+    h = meta.Hyper(lr=1e-2, beta_f=0.99, beta_d=0.9)
+    st = meta.MetaState.zeros((256,))
+    pi, n2 = np.zeros(256), 0.0
+    for i in range(40):
+        F = rng.normal(size=256) * rng.uniform(0.1, 3)
+        dF = 0.05 * rng.normal(size=256) if i else np.zeros(256)
+        pi, n2, alpha = meta.meta_update(pi, F, dF, st, h, n2)
+        assert np.all(alpha <= 1 - 1 / (i + 1) + 1e-15) and np.all(alpha >= 0)
+
+
+def test_weight_one_on_plain_estimator_is_adam_beta1_zero():
+    """When Var[<dF>] dominates, alpha -> 0: the meta-estimate is the plain estimate, Var_M is the
+    Moment2 of F, and the update equals Adam with beta1 = 0, beta2 = beta_F (torch.optim.Adam)."""
+    rng = np.random.default_rng(4)
+    h = meta.Hyper(lr=1e-2, beta_f=0.95, beta_d=0.5, eps=1e-8)
+    n = 32
+    pi = rng.normal(size=n)
+    st = meta.MetaState.zeros((n,))
+    p_t = torch.tensor(pi.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([p_t], lr=h.lr, betas=(0.0, h.beta_f), eps=h.eps)
+    n2 = 0.0
+    for i in range(20):
+        F = rng.normal(size=n)
+        dF = 1e12 * np.ones(n) if i else np.zeros(n)     # enormous FD variance
+        pi, n2, alpha = meta.meta_update(pi, F, dF, st, h, n2)
+        opt.zero_grad()
+        p_t.grad = torch.tensor(F)
+        opt.step()
+        assert np.all(alpha < 1e-20)
+        assert np.allclose(pi, p_t.detach().numpy(), rtol=1e-9, atol=1e-12), i
+
+
+def test_adam_matches_torch():
+    rng = np.random.default_rng(5)
+    h = meta.Hyper(lr=3e-3, beta1=0.9, beta2=0.999, eps=1e-8)
+    n = 40
+    pi = rng.normal(size=n)
+    st = meta.AdamState.zeros((n,))
+    p_t = torch.tensor(pi.copy(), dtype=torch.float64)
+    p_t.requires_grad_(True)
+    opt = torch.optim.Adam([p_t], lr=h.lr, betas=(h.beta1, h.beta2), eps=h.eps)
+    for i in range(30):
+        F = rng.normal(size=n) + 0.5
+        pi, _ = meta.adam_update(pi, F, st, h)
+        p_t.grad = torch.tensor(F)
+        opt.step()
+        assert np.allclose(pi, p_t.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_clamp_and_applied_step_norm():
+    h = meta.Hyper(lr=0.5)
+    st = meta.MetaState.zeros((4,))
+    pi = np.array([0.1, 0.9, 0.5, 0.5])
+    F = np.array([1.0, -1.0, 1.0, -1.0])
+    pi1, n2, _ = meta.meta_update(pi, F, np.zeros(4), st, h, 0.0, lo=np.zeros(4), hi=np.ones(4))
+    assert np.allclose(pi1, [0.0, 1.0, 0.0, 1.0], atol=1e-7)
+    assert np.isclose(n2, np.sum((pi1 - pi) ** 2))
+
+
+@pytest.mark.parametrize("method", ["meta", "adam"])
+def test_exposition_toy_converges(method):
+    """The exposition figure's toy: the rate of an exponential distribution is optimised so
+    that the mean of 32 samples per iteration matches 2.0 under an L2 loss; the optimum rate
+    is 0.5. Samples x = -ln(u)/lambda; the FD sample reuses the same u at lambda_{i-1}."""
+    rng = np.random.default_rng(6)
+    h = meta.Hyper(lr=0.02, beta_f=0.99, beta_d=0.9)
+    lam = np.array([2.0])
+    lam_prev = lam.copy()
+    st = meta.MetaState.zeros((1,))
+    ad = meta.AdamState.zeros((1,))
+    n2 = 0.0
+
+    def grad(l, u, v):
+        y = -np.log1p(-v) / l            # independent samples for the loss residual
+        # d/dl of x = -ln(1-u)/l is ln(1-u)/l^2 (samples u drive the gradient)
+        return 2.0 * (y.mean() - 2.0) * np.mean(np.log1p(-u) / (l * l))
+
+    for i in range(600):
+        u, v = rng.random(32), rng.random(32)
+        F = np.array([grad(lam[0], u, v)])
+        if method == "meta":
+            u2, v2 = rng.random(32), rng.random(32)
+            dF = np.array([grad(lam[0], u2, v2) - grad(lam_prev[0], u2, v2)]) if i else np.zeros(1)
+            lam_prev = lam.copy()
+            lam, n2, _ = meta.meta_update(lam, F, dF, st, h, n2, lo=np.array([0.05]), hi=np.array([10.0]))
+        else:
+            lam, _ = meta.adam_update(lam, F, ad, h, lo=np.array([0.05]), hi=np.array([10.0]))
+    assert abs(lam[0] - 0.5) < 0.05, lam

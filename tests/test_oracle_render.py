@@ -1,0 +1,86 @@
+"""Oracle path tracer against closed-form radiance (white furnace, Lambertian plane under a
+constant environment, emitting closed box) and the depth convention."""
+import numpy as np
+import pytest
+
+from oracle import orc
+from paper_2309_15676_gb300 import synth
+
+
+@pytest.mark.parametrize("depth", [2, 3, 5])
+@pytest.mark.parametrize("albedo", [1.0, 0.6])
+def test_white_furnace_per_sample(oracle_lib, depth, albedo):
+    """Convex Lambert sphere in a constant environment: with NEE (cosine env sampling) and BSDF
+    sampling at equal densities the power-heuristic weights are 1/2 each, so each sample that
+    hits the sphere is exactly albedo * L_env, and each miss is L_env."""
+    env = np.array([0.5, 1.0, 2.0])
+    sc = orc.Scene(synth.furnace_scene(albedo=albedo, max_depth=depth, env=tuple(env)))
+    n = sc.n_pix * 2
+    L = orc.render_samples(sc, np.zeros((8, 8, 3)), np.arange(n) % sc.n_pix, np.arange(n) // sc.n_pix, 3,
+                           orc.ST_PROP_PRIMAL)
+    a = np.float64(np.float32(albedo))
+    hit = np.isclose(L, a * env, rtol=1e-12, atol=0).all(1)
+    miss = np.isclose(L, env, rtol=1e-12, atol=0).all(1)
+    assert np.all(hit | miss)
+    assert hit.sum() > 0.2 * n
+
+
+def test_depth_one_shows_only_emitters(oracle_lib):
+    sc = orc.Scene(synth.furnace_scene(albedo=0.6, max_depth=1, env=(0.5, 1.0, 2.0)))
+    L = orc.render_samples(sc, np.zeros((8, 8, 3)), np.arange(sc.n_pix), np.zeros(sc.n_pix), 0, 0)
+    # sphere hits show no light (not emissive), misses show the environment
+    ok = np.isclose(L, 0).all(1) | np.isclose(L, [0.5, 1.0, 2.0]).all(1)
+    assert ok.all() and np.isclose(L, 0).all(1).sum() > 0
+
+
+@pytest.mark.parametrize("depth", [2, 4])
+def test_lambert_plane_constant_env(oracle_lib, depth):
+    """rho(uv) * L_env per sample for a constant albedo on a plane that occludes nothing."""
+    env = np.array([0.7, 0.8, 0.9])
+    sc = orc.Scene(synth.plane_scene(max_depth=depth, env=tuple(env)))
+    tex = np.full((8, 8, 3), 0.3)
+    L = orc.render_samples(sc, tex, np.arange(sc.n_pix), np.ones(sc.n_pix), 5, 1)
+    assert np.allclose(L, 0.3 * env, rtol=1e-12)
+
+
+def test_lambert_plane_textured_mean(oracle_lib):
+    """With a textured albedo each sample is rho(uv_s) L_env: the image lies in the texture's
+    value range times L_env and its mean over pixels is a bilinear average of texels."""
+    env = np.array([1.0, 1.0, 1.0])
+    sc = orc.Scene(synth.plane_scene(max_depth=3, env=tuple(env)))
+    tex = np.random.default_rng(0).uniform(0.1, 0.9, (8, 8, 3))
+    img = orc.render_image(sc, tex, 2, 0, 0)
+    assert img.min() >= tex.min() - 1e-12 and img.max() <= tex.max() + 1e-12
+
+
+def test_depth_one_emitting_box_exact(oracle_lib):
+    sc = orc.Scene(synth.emitting_box_scene(albedo=0.5, le=2.0, max_depth=1))
+    img = orc.render_image(sc, np.zeros((4, 4, 3)), 3, 0, 0)
+    assert np.allclose(img, 2.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("depth", [2, 3, 4])
+def test_emitting_box_mean(oracle_lib, depth):
+    """Closed box whose walls all emit Le with albedo rho: radiance Le * sum_{k<D} rho^k everywhere.
+    Checked within 5 sigma (NEE to area lights + MIS is unbiased, not exact per sample)."""
+    rho, le = 0.5, 1.0
+    sc = orc.Scene(synth.emitting_box_scene(albedo=rho, le=le, max_depth=depth))
+    spp = 600
+    pix = np.repeat(np.arange(sc.n_pix), spp)
+    smp = np.tile(np.arange(spp), sc.n_pix)
+    L = orc.render_samples(sc, np.zeros((4, 4, 3)), pix, smp, 0, orc.ST_EVAL)[:, 0]
+    expect = le * sum(rho ** k for k in range(depth))
+    se = L.std() / np.sqrt(len(L))
+    assert abs(L.mean() - expect) < 5 * se + 1e-12, (L.mean(), expect, se)
+
+
+def test_streams_and_iterations_decorrelate(oracle_lib):
+    w = synth.workload_box(8, 8, 8, max_depth=3)
+    sc = orc.Scene(w.scene)
+    tex = w.init_tex.astype(np.float64)
+    a = orc.render_image(sc, tex, 1, 0, orc.ST_PROP_PRIMAL)
+    b = orc.render_image(sc, tex, 1, 0, orc.ST_PROP_ADJ)
+    c = orc.render_image(sc, tex, 1, 1, orc.ST_PROP_PRIMAL)
+    a2 = orc.render_image(sc, tex, 1, 0, orc.ST_PROP_PRIMAL)
+    assert np.array_equal(a, a2)
+    assert not np.allclose(a, b) and not np.allclose(a, c)
