@@ -1,0 +1,236 @@
+/*
+ * mer.h — C ABI of the GB300 library for meta-estimated inverse path tracing.
+ *
+ * Implements the data-parallel hot path of "Joint Sampling and Optimisation for
+ * Inverse Rendering" (Balint, Myszkowski, Seidel, Singh; SIGGRAPH Asia 2023):
+ * Monte Carlo estimation of texture gradients of an image loss by path tracing with
+ * Path Replay Backpropagation (Sec. 6 setup), in two kinds — proportional samples
+ * <F_i> (Sec. 3, Eq. est_def) and finite-difference samples <dF_i> that replay the
+ * same random numbers at pi_i and pi_{i-1} (Sec. 3, Eq. est_triv) — feeding the
+ * variance-weighted meta-estimator (Eqs. recurrent_meta, alpha, varest, vardiff,
+ * varmeta, alpha_clip_2) and its update rule replacing Adam's moments (Sec. 5).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a mer_status and never throws across the ABI. On failure
+ *    mer_last_error(ctx) gives a message (context-free calls: mer_last_error(NULL)).
+ *  - "device" pointers are CUDA device addresses on the context's device; they are
+ *    borrowed for the duration of the call (including its asynchronous GPU work on
+ *    the context stream). "host" pointers are read or written before the call returns.
+ *  - Work is enqueued on the stream given at mer_create (or the stream argument of
+ *    the context-free calls) and is asynchronous unless stated otherwise.
+ *  - Textures / parameters are HWC float32: element (y, x, c) at (y*W + x)*C + c,
+ *    with C = 3 (Lambert albedo RGB) or C = 5 (base colour RGB, metalness, roughness).
+ *  - Images are row-major float32 RGB: pixel (py, px) at (py*width + px)*3.
+ *  - Random numbers: Philox4x32-10 with key (seed, key_id) and counter
+ *    (pixel, sample, iteration, stream<<16 | vertex<<4 | block); uniforms are
+ *    (x >> 8) * 2^-24. Streams: MER_STREAM_*.
+ */
+#ifndef MER_H
+#define MER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mer_status;
+#define MER_OK 0
+#define MER_ERR_INVALID_ARG 1
+#define MER_ERR_CUDA 2
+#define MER_ERR_OOM 3
+#define MER_ERR_TIMEOUT 4
+#define MER_ERR_BOUNDS 5
+#define MER_ERR_STATE 6
+#define MER_ERR_NAN 7
+
+/* optimiser of a problem */
+#define MER_MODE_META 0  /* meta-estimator + its update rule (Sec. 5): 1 FD + spp_prop proportional */
+#define MER_MODE_ADAM 1  /* plain fresh-sample gradients with Adam (Sec. 5, Eqs. adam_*) */
+
+/* Philox stream ids (fourth counter word, bits 16..31) */
+#define MER_STREAM_PROP_PRIMAL 0u /* primal image used for the proportional sample's loss adjoint */
+#define MER_STREAM_PROP_ADJ 1u    /* proportional sample's path replay */
+#define MER_STREAM_FD_PRIMAL 2u   /* primal image pair of the FD sample (same numbers at pi_i, pi_{i-1}) */
+#define MER_STREAM_FD_ADJ 3u      /* adjoint pair of the FD sample */
+#define MER_STREAM_TARGET 4u      /* target rendering */
+#define MER_STREAM_EVAL 5u        /* loss evaluation renders */
+
+#define MER_MAX_CHANNELS 5
+#define MER_MAX_DEPTH 16
+#define MER_MAX_PROBLEMS 256
+
+/* Hyper-parameters of one problem's optimiser. Defaults (mer_hyper_default):
+ * lr 0.01, beta_f 0.99, beta_d 0.9 (Sec. 4.1 "large beta_F", Sec. 4.2 "small beta_D"),
+ * eps 1e-8 and eps_alpha 1e-30 (appendix pseudocode), beta1 0.9 / beta2 0.999 (Adam). */
+typedef struct mer_hyper {
+    int32_t mode;      /* MER_MODE_META or MER_MODE_ADAM */
+    float lr;          /* eta */
+    float beta_f;      /* EMA decay of Var[<F_i>]   (Eq. varest) */
+    float beta_d;      /* EMA decay of Var[<dF_i>]_D (Sec. 4.2) */
+    float eps;         /* step epsilon (update rule of Sec. 5) */
+    float eps_alpha;   /* added to the alpha denominator (appendix pseudocode) */
+    float beta1;       /* Adam first moment */
+    float beta2;       /* Adam second moment */
+} mer_hyper;
+
+/* Scene of one problem. All arrays are HOST arrays, copied by mer_scene_add (the caller
+ * keeps ownership). Triangles index shared vertices; quads are parallelogram area lights
+ * (p0, e1, e2, Le; emitting on the side of e1 x e2) whose geometry must also be present as
+ * triangles carrying the light's index in tri_light. */
+typedef struct mer_scene_desc {
+    int32_t n_verts, n_tris;
+    const float* positions;   /* [n_verts][3] */
+    const float* uvs;         /* [n_verts][2] */
+    const int32_t* tris;      /* [n_tris][3] vertex indices */
+    const int32_t* tri_mat;   /* [n_tris] material index */
+    const int32_t* tri_light; /* [n_tris] quad-light index or -1 */
+    int32_t n_spheres;
+    const float* spheres;     /* [n_spheres][8]: centre xyz, radius, u0, u1, v0, v1 (uv rectangle) */
+    const int32_t* sph_mat;   /* [n_spheres] */
+    int32_t n_mats;
+    const int32_t* mat_type;  /* [n_mats] 0 Lambert, 1 principled */
+    const int32_t* mat_textured; /* [n_mats] 1: parameters from the problem's texture */
+    const float* mat_const;   /* [n_mats][5] parameters of untextured materials */
+    int32_t n_quads;
+    const float* quads;       /* [n_quads][12]: p0, e1, e2, Le */
+    int32_t has_env;
+    float env[3];             /* constant environment radiance */
+    float eye[3], target[3], up[3];
+    float fov_deg;            /* vertical field of view */
+    int32_t width, height;
+    int32_t tex_c, tex_h, tex_w; /* parameter texture shape (C in {3, 5}) */
+    float clamp_lo[8], clamp_hi[8]; /* per-channel parameter range applied after each step */
+    int32_t max_depth;        /* path segments (1 = emitters only, 2 = direct light) */
+    int32_t spp_prop, spp_fd; /* samples per pixel and iteration */
+    uint32_t seed, key_id;    /* Philox key */
+    mer_hyper hyper;
+} mer_scene_desc;
+
+typedef struct mer_config {
+    int32_t device;           /* CUDA device ordinal */
+    int32_t block_size;       /* threads per block of the wavefront kernels (0 = default 128) */
+    int32_t blocks_per_sm;    /* persistent-grid occupancy target (0 = default) */
+    int32_t smem_nodes;       /* BVH nodes staged in shared memory per block (0 = off) */
+    int64_t max_paths;        /* capacity hint for path queues (0 = size from the scenes) */
+} mer_config;
+
+typedef struct mer_iter_stats {
+    int64_t iteration;        /* optimisation iterations completed */
+    double loss;              /* L2 loss of the last proportional primal image */
+    double dpi_norm2;         /* ||pi_i - pi_{i-1}||^2 of the last applied step */
+    int32_t count_f, count_d; /* Moment2 step counts of Var[<F>] and Var[<dF>]_D */
+    int64_t paths_per_iter;   /* path traversals of one iteration (all passes) */
+} mer_iter_stats;
+
+typedef struct mer_ctx mer_ctx;
+
+/* Default hyper-parameters (see mer_hyper). Host-only, never fails. */
+mer_status mer_hyper_default(mer_hyper* out);
+
+/* Create a context on cfg->device that enqueues on cuda_stream (a cudaStream_t; NULL =
+ * legacy default stream). Owns all device buffers it allocates. */
+mer_status mer_create(const mer_config* cfg, void* cuda_stream, mer_ctx** out);
+void mer_destroy(mer_ctx* ctx);
+/* Last error message of ctx (or of the calling thread's context-free calls if ctx is NULL).
+ * Never NULL. */
+const char* mer_last_error(const mer_ctx* ctx);
+
+/* Add one inverse-rendering problem: copies the scene, builds its BVH on the host (binned
+ * SAH) and uploads it; parameters start at zero and the optimiser state is reset. Returns
+ * its id in *problem_id (0, 1, ... in call order). Synchronous. */
+mer_status mer_scene_add(mer_ctx* ctx, const mer_scene_desc* desc, int32_t* problem_id);
+
+/* Set the parameters pi_0 = pi_{-1} of a problem from an HWC texture (host or device
+ * pointer per on_device) and reset its optimiser state to iteration 0. */
+mer_status mer_params_set(mer_ctx* ctx, int32_t pid, const float* hwc, int32_t on_device);
+/* Copy the current parameters pi_i out (host pointer: synchronous; device: asynchronous). */
+mer_status mer_params_get(mer_ctx* ctx, int32_t pid, float* hwc_out, int32_t on_device);
+/* Set the target image ([height][width][3]). */
+mer_status mer_target_set(mer_ctx* ctx, int32_t pid, const float* img, int32_t on_device);
+/* Render the target image from the given parameters (device HWC texture) with spp samples
+ * of stream MER_STREAM_TARGET at iteration 0, and store it as the target. */
+mer_status mer_target_render(mer_ctx* ctx, int32_t pid, const float* tex_dev, int32_t spp);
+
+/* Primal render of problem pid with the device texture tex_dev (NULL = current parameters):
+ * img_dev[p] = (1/spp) sum_s L(pixel p, sample s) with counters (p, s, iteration, stream). */
+mer_status mer_render(mer_ctx* ctx, int32_t pid, const float* tex_dev, int32_t spp, uint32_t stream,
+                      uint32_t iteration, float* img_dev);
+/* Per-sample radiance: out_dev[(s*n_pix + p)*3 + c] for s < spp. */
+mer_status mer_render_samples(mer_ctx* ctx, int32_t pid, const float* tex_dev, int32_t spp, uint32_t stream,
+                              uint32_t iteration, float* out_dev);
+/* Adjoint of mer_render by path replay: grad_dev (texture-shaped, overwritten) =
+ * d/dtex sum_p sum_c dimg_dev[p,c] * img[p,c], where img is the render with the same
+ * (tex, spp, stream, iteration). Paths are recomputed from their counters (no stored vertices). */
+mer_status mer_adjoint(mer_ctx* ctx, int32_t pid, const float* tex_dev, const float* dimg_dev, int32_t spp,
+                       uint32_t stream, uint32_t iteration, float* grad_dev);
+/* FD pair of Eq. est_triv for one problem: grad_dev = d/dtex J(texA) - d/dtex J(texB) where both
+ * terms replay the same counters; dimgA/dimgB are the adjoint images of each side. */
+mer_status mer_adjoint_pair(mer_ctx* ctx, int32_t pid, const float* texA_dev, const float* texB_dev,
+                            const float* dimgA_dev, const float* dimgB_dev, int32_t spp, uint32_t stream,
+                            uint32_t iteration, float* grad_dev);
+/* The two primal images of the FD pair (same counters at texA and texB). */
+mer_status mer_render_pair(mer_ctx* ctx, int32_t pid, const float* texA_dev, const float* texB_dev,
+                           int32_t spp, uint32_t stream, uint32_t iteration, float* imgA_dev, float* imgB_dev);
+
+/* Steps a1-a10 of one iteration for every problem: the proportional gradient <F_i> and (META
+ * problems, iteration >= 1) the FD gradient <dF_i>, accumulated into the context's F and dF. */
+mer_status mer_gradient_step(mer_ctx* ctx);
+/* Copy a problem's current F and dF (texture-shaped) out (host: synchronous). */
+mer_status mer_grads_get(mer_ctx* ctx, int32_t pid, float* F_out, float* dF_out, int32_t on_device);
+/* Step a11 for every problem: the fused meta-estimator (or Adam) update, pi_{i+1} written over
+ * pi_{i-1}, F and dF zeroed, ||pi_{i+1} - pi_i||^2 reduced, iteration advanced. */
+mer_status mer_update_step(mer_ctx* ctx);
+/* n_iters full iterations (gradient + update) of all problems; use_graph = 1 replays one
+ * captured CUDA graph per iteration (captured on first use). */
+mer_status mer_iterate(mer_ctx* ctx, int32_t n_iters, int32_t use_graph);
+/* Statistics of a problem (synchronous). */
+mer_status mer_stats(mer_ctx* ctx, int32_t pid, mer_iter_stats* out);
+
+/* Optimiser state of a problem (parameter-shaped device arrays owned by the context) for
+ * inspection and tests: pi_cur, pi_prev, F, dF, m2f, m2d, mean, var, alpha_prev. */
+typedef struct mer_state_view {
+    float *pi_cur, *pi_prev, *F, *dF, *m2f, *m2d, *mean, *var, *alpha_prev;
+    int64_t n;                /* parameters of the problem (H*W*C) */
+} mer_state_view;
+mer_status mer_state_get(mer_ctx* ctx, int32_t pid, mer_state_view* out);
+
+/* Standalone fused update of step a11 over n parameters (one problem), every array a device
+ * array of n floats; pi_next may not alias pi. Per element: Var[<F>] Moment2 step (Eq. varest
+ * with start-up correction count_f+1), if iteration >= 1 and dpi_norm2 > 0 the Var[<dF>]_D
+ * Moment2 step of dF/||dpi|| (count_d+1) and Var[<dF>] = m2d*dpi_norm2 (Eq. vardiff), then the
+ * meta-estimator of the appendix pseudocode (Eqs. recurrent_meta, alpha, alpha_clip_2, varmeta)
+ * and the update dpi = -lr*mean/(sqrt(var)+eps), clamped channel-wise (channel = index % C) to
+ * [lo[c], hi[c]]. ADAM mode uses mean/var as Adam's m/v and iteration+1 as its step count.
+ * zero_grads = 1 clears F and dF. *dpi_norm2_out (device double) receives ||pi_next - pi||^2.
+ * Uses library-owned per-device scratch for the deterministic norm reduction. */
+mer_status mer_meta_step_raw(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
+                             const float* pi, float* pi_next, float* F, float* dF, float* m2f, float* m2d,
+                             float* mean, float* var, float* alpha_prev, int32_t iteration, int32_t count_f,
+                             int32_t count_d, double dpi_norm2, int32_t zero_grads, double* dpi_norm2_out,
+                             void* cuda_stream);
+
+/* Philox4x32-10 of n counters: ctr_dev [n][4] u32, out_dev [n][4] u32, key (k0, k1). */
+mer_status mer_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr_dev, int64_t n, uint32_t* out_dev,
+                      void* cuda_stream);
+
+/* Checkpoint: the optimiser state of every problem (parameters, moments, scalars) as an opaque
+ * host blob. With buf NULL, *len receives the size. Synchronous. Restoring into a context with
+ * the same scenes continues bit-identically. */
+mer_status mer_checkpoint_save(mer_ctx* ctx, void* buf, size_t* len);
+mer_status mer_checkpoint_load(mer_ctx* ctx, const void* buf, size_t len);
+
+/* Autotune launch shapes (block size, blocks per SM, shared-memory BVH staging) of the
+ * wavefront kernels by timing trial iterations; the choice is kept in the context and its
+ * description written to desc (may be NULL). Changes no optimisation state. */
+mer_status mer_autotune(mer_ctx* ctx, int32_t trial_iters, char* desc, size_t desc_len);
+
+/* Number of kernel launches the last mer_iterate / mer_gradient_step + mer_update_step enqueued
+ * per iteration (for launch accounting). */
+mer_status mer_launch_count(mer_ctx* ctx, int64_t* launches_per_iter);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MER_H */

@@ -17,9 +17,9 @@
  * MIS heuristic, depth convention, texture filter, ray offsets) are fixed in the
  * project's design notes and restated where they are used below.
  *
- * Parity notes: functions `orc_trace_prb` (replay bookkeeping with subtraction and
- * division) and `orc_trace_stored` (explicit products over stored vertices, no
- * division) are independent derivations of the same gradient and pin each other.
+ * Parity notes: `trace` in replay mode (bookkeeping with subtraction and division)
+ * and `trace_stored` (explicit products over stored vertices, no division) are
+ * independent derivations of the same gradient and pin each other.
  */
 #include <math.h>
 #include <stdint.h>
@@ -818,4 +818,10 @@ double orc_l2_loss(int64_t n_pix, const double* img, const double* target, doubl
         if (dimg) dimg[i] = 2.0 * r * inv;
     }
     return acc * inv;
+}
+
+/* n Philox evaluations: ctr [n][4], out [n][4] */
+void orc_philox_batch(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out)
+{
+    for (int64_t i = 0; i < n; ++i) orc_philox(ctr + 4 * i, key, out + 4 * i);
 }

@@ -48,6 +48,7 @@ def lib():
     if _lib is None:
         L = ct.CDLL(_build.build())
         L.orc_philox.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_philox_batch.argtypes = [ct.c_int64, _u32p, _u32p, _u32p]
         L.orc_render_samples.argtypes = [ct.POINTER(OrcScene), _f64p, ct.c_int64, _u32p, _u32p,
                                          ct.c_uint32, ct.c_uint32, _f64p]
         L.orc_render_image.argtypes = [ct.POINTER(OrcScene), _f64p, ct.c_int, ct.c_uint32, ct.c_uint32, _f64p]
@@ -130,6 +131,15 @@ def philox(ctr, key):
     k = np.asarray(key, np.uint32).copy()
     o = np.zeros(4, np.uint32)
     lib().orc_philox(_p(c, _u32p), _p(k, _u32p), _p(o, _u32p))
+    return o
+
+
+def philox_batch(ctr, key):
+    """Philox4x32-10 of counters ctr [n, 4] under one key."""
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, np.uint32)
+    o = np.zeros_like(c)
+    lib().orc_philox_batch(c.shape[0], _p(c, _u32p), _p(k, _u32p), _p(o, _u32p))
     return o
 
 

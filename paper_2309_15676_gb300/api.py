@@ -1,0 +1,298 @@
+"""Thin Python binding over the C ABI (include/mer.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch only provides device memory and the
+current stream. Tensors passed in must live on the context's device.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+STREAM_PROP_PRIMAL = _lib.STREAM_PROP_PRIMAL
+STREAM_PROP_ADJ = _lib.STREAM_PROP_ADJ
+STREAM_FD_PRIMAL = _lib.STREAM_FD_PRIMAL
+STREAM_FD_ADJ = _lib.STREAM_FD_ADJ
+STREAM_TARGET = _lib.STREAM_TARGET
+STREAM_EVAL = _lib.STREAM_EVAL
+MODE_META, MODE_ADAM = _lib.MODE_META, _lib.MODE_ADAM
+
+
+@dataclass
+class HyperParams:
+    mode: int = MODE_META
+    lr: float = 0.01
+    beta_f: float = 0.99
+    beta_d: float = 0.9
+    eps: float = 1e-8
+    eps_alpha: float = 1e-30
+    beta1: float = 0.9
+    beta2: float = 0.999
+
+    def to_c(self) -> _lib.Hyper:
+        return _lib.Hyper(self.mode, self.lr, self.beta_f, self.beta_d, self.eps, self.eps_alpha, self.beta1,
+                          self.beta2)
+
+
+def _ptr(t):
+    return ct.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _cur_stream(device):
+    return ct.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_f32(x, device):
+    if isinstance(x, torch.Tensor):
+        t = x.to(device=device, dtype=torch.float32)
+    else:
+        t = torch.as_tensor(np.asarray(x, np.float32), device=device)
+    return t.contiguous()
+
+
+class _Arr:
+    """Keeps numpy arrays alive while their pointers sit in a SceneDesc."""
+
+    def __init__(self):
+        self.keep = []
+
+    def __call__(self, a, dt, cty):
+        a = np.ascontiguousarray(np.asarray(a, dt))
+        if a.size == 0:
+            a = np.zeros(1, dt)
+        self.keep.append(a)
+        return a.ctypes.data_as(ct.POINTER(cty))
+
+
+def scene_desc(scene: dict, hyper: HyperParams) -> tuple[_lib.SceneDesc, _Arr]:
+    A = _Arr()
+    d = _lib.SceneDesc()
+    pos = np.asarray(scene["positions"], np.float32).reshape(-1, 3)
+    tris = np.asarray(scene["tris"], np.int32).reshape(-1, 3)
+    d.n_verts, d.n_tris = pos.shape[0], tris.shape[0]
+    d.positions = A(pos, np.float32, ct.c_float)
+    d.uvs = A(scene["uvs"], np.float32, ct.c_float)
+    d.tris = A(tris, np.int32, ct.c_int32)
+    d.tri_mat = A(scene["tri_mat"], np.int32, ct.c_int32)
+    d.tri_light = A(scene["tri_light"], np.int32, ct.c_int32)
+    sph = np.asarray(scene["spheres"], np.float32).reshape(-1, 8)
+    d.n_spheres = sph.shape[0]
+    d.spheres = A(sph, np.float32, ct.c_float)
+    d.sph_mat = A(scene["sph_mat"], np.int32, ct.c_int32)
+    d.n_mats = len(scene["mat_type"])
+    d.mat_type = A(scene["mat_type"], np.int32, ct.c_int32)
+    d.mat_textured = A(scene["mat_textured"], np.int32, ct.c_int32)
+    d.mat_const = A(scene["mat_const"], np.float32, ct.c_float)
+    q = np.asarray(scene["quads"], np.float32).reshape(-1, 12)
+    d.n_quads = q.shape[0]
+    d.quads = A(q, np.float32, ct.c_float)
+    d.has_env = int(scene["has_env"])
+    for k in ("env", "eye", "target", "up"):
+        getattr(d, k)[:] = [float(v) for v in np.asarray(scene[k], np.float32)]
+    d.fov_deg = float(scene["fov_deg"])
+    d.width, d.height = int(scene["width"]), int(scene["height"])
+    d.tex_c, d.tex_h, d.tex_w = int(scene["tex_c"]), int(scene["tex_h"]), int(scene["tex_w"])
+    lo = np.zeros(8, np.float32)
+    hi = np.zeros(8, np.float32)
+    lo[:d.tex_c] = scene["clamp_lo"]
+    hi[:d.tex_c] = scene["clamp_hi"]
+    d.clamp_lo[:] = lo.tolist()
+    d.clamp_hi[:] = hi.tolist()
+    d.max_depth = int(scene["max_depth"])
+    d.spp_prop, d.spp_fd = int(scene["spp_prop"]), int(scene["spp_fd"])
+    d.seed, d.key_id = int(scene["seed"]) & 0xFFFFFFFF, int(scene["key_id"]) & 0xFFFFFFFF
+    d.hyper = hyper.to_c()
+    return d, A
+
+
+class Context:
+    """A set of inverse-rendering problems on one GPU (mer_ctx)."""
+
+    def __init__(self, device: int = 0, block_size: int = 0, blocks_per_sm: int = 0, smem_nodes: int = 0,
+                 max_paths: int = 0):
+        self.L = _lib.load()
+        self.device = torch.device("cuda", device)
+        cfg = _lib.Config(device, block_size, blocks_per_sm, smem_nodes, max_paths)
+        h = ct.c_void_p()
+        check(self.L.mer_create(ct.byref(cfg), _cur_stream(self.device), ct.byref(h)))
+        self.h = h
+        self.shapes = []   # (H, W, C) texture shape per problem
+        self.images = []   # (height, width) per problem
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, s):
+        check(s, self.h)
+
+    # ---- problems ----
+    def add_scene(self, scene: dict, hyper: HyperParams | None = None) -> int:
+        d, keep = scene_desc(scene, hyper or HyperParams())
+        pid = ct.c_int32()
+        self._ck(self.L.mer_scene_add(self.h, ct.byref(d), ct.byref(pid)))
+        del keep
+        self.shapes.append((int(scene["tex_h"]), int(scene["tex_w"]), int(scene["tex_c"])))
+        self.images.append((int(scene["height"]), int(scene["width"])))
+        return pid.value
+
+    def set_params(self, pid: int, tex):
+        t = _dev_f32(tex, self.device)
+        self._ck(self.L.mer_params_set(self.h, pid, _ptr(t), 1))
+        torch.cuda.current_stream(self.device).synchronize()
+
+    def get_params(self, pid: int) -> torch.Tensor:
+        out = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
+        self._ck(self.L.mer_params_get(self.h, pid, _ptr(out), 1))
+        return out
+
+    def set_target(self, pid: int, img):
+        t = _dev_f32(img, self.device)
+        self._ck(self.L.mer_target_set(self.h, pid, _ptr(t), 1))
+        torch.cuda.current_stream(self.device).synchronize()
+
+    def set_target_host(self, pid: int, img_pinned: torch.Tensor):
+        """Target upload from a (pinned) host tensor."""
+        self._ck(self.L.mer_target_set(self.h, pid, _ptr(img_pinned), 0))
+
+    def render_target(self, pid: int, tex, spp: int):
+        t = _dev_f32(tex, self.device)
+        self._ck(self.L.mer_target_render(self.h, pid, _ptr(t), spp))
+        torch.cuda.current_stream(self.device).synchronize()
+
+    # ---- renders and adjoints ----
+    def render(self, pid, tex=None, spp=1, stream=STREAM_EVAL, iteration=0, out=None) -> torch.Tensor:
+        H, W = self.images[pid]
+        out = out if out is not None else torch.empty((H, W, 3), device=self.device, dtype=torch.float32)
+        t = None if tex is None else _dev_f32(tex, self.device)
+        self._ck(self.L.mer_render(self.h, pid, _ptr(t), spp, stream, iteration, _ptr(out)))
+        return out
+
+    def render_samples(self, pid, tex=None, spp=1, stream=STREAM_EVAL, iteration=0) -> torch.Tensor:
+        H, W = self.images[pid]
+        out = torch.empty((spp, H * W, 3), device=self.device, dtype=torch.float32)
+        t = None if tex is None else _dev_f32(tex, self.device)
+        self._ck(self.L.mer_render_samples(self.h, pid, _ptr(t), spp, stream, iteration, _ptr(out)))
+        return out
+
+    def render_pair(self, pid, texA, texB, spp=1, stream=STREAM_FD_PRIMAL, iteration=0):
+        H, W = self.images[pid]
+        a = torch.empty((H, W, 3), device=self.device, dtype=torch.float32)
+        b = torch.empty_like(a)
+        ta, tb = _dev_f32(texA, self.device), _dev_f32(texB, self.device)
+        self._ck(self.L.mer_render_pair(self.h, pid, _ptr(ta), _ptr(tb), spp, stream, iteration, _ptr(a), _ptr(b)))
+        return a, b
+
+    def adjoint(self, pid, tex, dimg, spp=1, stream=STREAM_EVAL, iteration=0) -> torch.Tensor:
+        g = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
+        t = None if tex is None else _dev_f32(tex, self.device)
+        d = _dev_f32(dimg, self.device)
+        self._ck(self.L.mer_adjoint(self.h, pid, _ptr(t), _ptr(d), spp, stream, iteration, _ptr(g)))
+        return g
+
+    def adjoint_pair(self, pid, texA, texB, dimgA, dimgB, spp=1, stream=STREAM_FD_ADJ, iteration=0):
+        g = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
+        ta, tb = _dev_f32(texA, self.device), _dev_f32(texB, self.device)
+        da, db = _dev_f32(dimgA, self.device), _dev_f32(dimgB, self.device)
+        self._ck(self.L.mer_adjoint_pair(self.h, pid, _ptr(ta), _ptr(tb), _ptr(da), _ptr(db), spp, stream, iteration,
+                                         _ptr(g)))
+        return g
+
+    # ---- optimisation ----
+    def gradient_step(self):
+        self._ck(self.L.mer_gradient_step(self.h))
+
+    def update_step(self):
+        self._ck(self.L.mer_update_step(self.h))
+
+    def iterate(self, n: int = 1, use_graph: bool = True):
+        self._ck(self.L.mer_iterate(self.h, n, int(use_graph)))
+
+    def grads(self, pid):
+        F = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
+        dF = torch.empty_like(F)
+        self._ck(self.L.mer_grads_get(self.h, pid, _ptr(F), _ptr(dF), 1))
+        return F, dF
+
+    def stats(self, pid) -> dict:
+        s = _lib.IterStats()
+        self._ck(self.L.mer_stats(self.h, pid, ct.byref(s)))
+        return dict(iteration=s.iteration, loss=s.loss, dpi_norm2=s.dpi_norm2, count_f=s.count_f,
+                    count_d=s.count_d, paths_per_iter=s.paths_per_iter)
+
+    def state(self, pid) -> dict:
+        """Copies of the optimiser state arrays (parameter-shaped)."""
+        v = _lib.StateView()
+        self._ck(self.L.mer_state_get(self.h, pid, ct.byref(v)))
+        out = {}
+        for name in ("pi_cur", "pi_prev", "F", "dF", "m2f", "m2d", "mean", "var", "alpha_prev"):
+            t = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
+            addr = ct.cast(getattr(v, name), ct.c_void_p).value
+            _memcpy_d2d(t, addr, v.n * 4)
+            out[name] = t
+        return out
+
+    def launch_count(self) -> int:
+        n = ct.c_int64()
+        self._ck(self.L.mer_launch_count(self.h, ct.byref(n)))
+        return n.value
+
+    def checkpoint_save(self) -> bytes:
+        n = ct.c_size_t()
+        self._ck(self.L.mer_checkpoint_save(self.h, None, ct.byref(n)))
+        buf = ct.create_string_buffer(n.value)
+        self._ck(self.L.mer_checkpoint_save(self.h, buf, ct.byref(n)))
+        return buf.raw[:n.value]
+
+    def checkpoint_load(self, blob: bytes):
+        buf = ct.create_string_buffer(blob, len(blob))
+        self._ck(self.L.mer_checkpoint_load(self.h, buf, len(blob)))
+
+    def autotune(self, trial_iters: int = 2) -> str:
+        desc = ct.create_string_buffer(256)
+        self._ck(self.L.mer_autotune(self.h, trial_iters, desc, 256))
+        return desc.value.decode()
+
+
+def _memcpy_d2d(dst: torch.Tensor, src_addr: int, nbytes: int):
+    class _View:
+        __cuda_array_interface__ = {"shape": (nbytes // 4,), "typestr": "<f4", "data": (src_addr, False),
+                                    "version": 3, "strides": None}
+    src = torch.as_tensor(_View(), device=dst.device)
+    dst.view(-1).copy_(src)
+
+
+def meta_step_raw(hyper: HyperParams, pi, pi_next, F, dF, m2f, m2d, mean, var, alpha_prev, C, lo, hi,
+                  iteration, count_f, count_d, dpi_norm2, zero_grads=True, out=None):
+    """mer_meta_step_raw on torch device tensors; returns the device tensor holding ||dpi||^2."""
+    L = _lib.load()
+    dev = pi.device
+    out = out if out is not None else torch.zeros(1, device=dev, dtype=torch.float64)
+    lo_a = (ct.c_float * 8)(*([float(x) for x in lo] + [0.0] * (8 - len(lo))))
+    hi_a = (ct.c_float * 8)(*([float(x) for x in hi] + [0.0] * (8 - len(hi))))
+    h = hyper.to_c()
+    check(L.mer_meta_step_raw(ct.byref(h), pi.numel(), C, lo_a, hi_a, _ptr(pi), _ptr(pi_next), _ptr(F), _ptr(dF),
+                              _ptr(m2f), _ptr(m2d), _ptr(mean), _ptr(var), _ptr(alpha_prev), iteration, count_f,
+                              count_d, float(dpi_norm2), int(zero_grads), _ptr(out), _cur_stream(dev)))
+    return out
+
+
+def philox(k0: int, k1: int, ctr: torch.Tensor) -> torch.Tensor:
+    """Philox4x32-10 of int32/uint32-bit counters [n, 4] (device) under key (k0, k1)."""
+    L = _lib.load()
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    check(L.mer_philox(k0 & 0xFFFFFFFF, k1 & 0xFFFFFFFF, _ptr(ctr), ctr.shape[0], _ptr(out), _cur_stream(ctr.device)))
+    return out

@@ -1,0 +1,1179 @@
+// C ABI of the library (mer.h): context, scene upload, pass orchestration, CUDA-graph
+// capture of whole iterations, the standalone update and checkpointing.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bvh.h"
+#include "kernels.cuh"
+#include "update.cuh"
+#include "wavefront.cuh"
+
+using namespace mer;
+
+struct Problem {
+    int32_t id = 0;
+    mer_hyper hyper{};
+    int32_t max_depth = 1, spp_prop = 1, spp_fd = 0;
+    int32_t width = 0, height = 0, n_pix = 0;
+    int32_t C = 3, W = 1, H = 1;
+    int64_t n_par = 0;
+    float lo[8] = {0}, hi[8] = {0};
+    bool meta = true;
+    ProblemDev dev{};
+    UpdSeg seg{};
+    std::vector<void*> allocs;
+    float *pslot[2] = {nullptr, nullptr}, *F = nullptr, *dF = nullptr, *m2f = nullptr, *m2d = nullptr;
+    float *mean = nullptr, *var = nullptr, *ap = nullptr;
+    float *target = nullptr, *img = nullptr, *dimg = nullptr, *imgA = nullptr, *imgB = nullptr;
+    float *dimgA = nullptr, *dimgB = nullptr;
+};
+
+struct mer_ctx {
+    int device = 0;
+    cudaStream_t user = nullptr;   // caller's stream
+    cudaStream_t st = nullptr;     // internal work stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    mer_config cfg{};
+    std::string err = "no error";
+    int sms = 1;
+    std::vector<Problem*> probs;
+    ProblemDev* d_probs = nullptr;
+    ProbState* d_pstate = nullptr;
+    double* d_loss = nullptr;
+    // pass tables
+    int32_t *d_prop_prob = nullptr, *d_fd_prob = nullptr;
+    int64_t *d_prop_off = nullptr, *d_fd_off = nullptr, *d_pix_pref = nullptr;
+    int32_t n_fd = 0;
+    int64_t P_prop = 0, P_fd = 0, total_pix = 0;
+    int32_t maxD_prop = 0, maxD_fd = 0, maxD = 0;
+    // wavefront buffers
+    int64_t qcap = 0, shcap = 0, rcap = 0;
+    float* qf[2] = {nullptr, nullptr};
+    uint32_t* qu[2] = {nullptr, nullptr};
+    float* hitf = nullptr;
+    int32_t* hitp = nullptr;
+    float* shf = nullptr;
+    uint32_t* shu = nullptr;
+    uint32_t* cnt = nullptr;
+    float* lacc = nullptr;
+    float* ltot = nullptr;
+    uint32_t* rpos = nullptr;
+    float* rf = nullptr;
+    // update
+    UpdSeg* d_segs = nullptr;
+    int64_t* d_blk_off = nullptr;
+    double* d_partials = nullptr;
+    int64_t upd_blocks = 0;
+    // graph of one iteration
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_dirty = true;
+    LaunchShape shape{128, 0, 0, 1};
+    int64_t launches = 0;
+};
+
+namespace {
+
+thread_local std::string t_err = "no error";
+
+mer_status failv(mer_ctx* c, int code, const char* fmt, va_list ap) {
+    char buf[1024];
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    if (c) c->err = buf; else t_err = buf;
+    return code;
+}
+
+mer_status fail(mer_ctx* c, int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    const mer_status s = failv(c, code, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CK(ctx, call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MER_ERR_OOM : MER_ERR_CUDA, "%s: %s", #call, \
+                        cudaGetErrorString(e_));                                                       \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+// fences between the caller's stream and the internal stream
+void enter(mer_ctx* c) {
+    cudaEventRecord(c->ev_in, c->user);
+    cudaStreamWaitEvent(c->st, c->ev_in, 0);
+}
+void leave(mer_ctx* c) {
+    cudaEventRecord(c->ev_out, c->st);
+    cudaStreamWaitEvent(c->user, c->ev_out, 0);
+}
+
+struct Guard {
+    mer_ctx* c;
+    explicit Guard(mer_ctx* c_) : c(c_) {
+        cudaSetDevice(c->device);
+        enter(c);
+    }
+    ~Guard() { leave(c); }
+};
+
+void free_wavefront(mer_ctx* c) {
+    for (int i = 0; i < 2; ++i) {
+        dfree(c->qf[i]);
+        dfree(c->qu[i]);
+        c->qf[i] = nullptr;
+        c->qu[i] = nullptr;
+    }
+    dfree(c->hitf); dfree(c->hitp); dfree(c->shf); dfree(c->shu); dfree(c->lacc); dfree(c->ltot);
+    dfree(c->rpos); dfree(c->rf);
+    c->hitf = nullptr; c->hitp = nullptr; c->shf = nullptr; c->shu = nullptr; c->lacc = nullptr;
+    c->ltot = nullptr; c->rpos = nullptr; c->rf = nullptr;
+    c->qcap = c->shcap = c->rcap = 0;
+}
+
+mer_status ensure_wavefront(mer_ctx* c, int64_t need_paths, int maxD) {
+    const int64_t want_q = std::max<int64_t>(need_paths, c->cfg.max_paths > 0 ? c->cfg.max_paths : 0);
+    const int64_t want_r = 2 * want_q * std::max(1, maxD - 1);
+    if (want_q <= c->qcap && want_r <= c->rcap) return MER_OK;
+    cudaStreamSynchronize(c->st);
+    free_wavefront(c);
+    const int64_t Q = std::max<int64_t>(want_q, 1024);
+    const int64_t S = 2 * Q;
+    const int64_t R = std::max<int64_t>(want_r, 1024);
+    for (int i = 0; i < 2; ++i) {
+        CK(c, dalloc(&c->qf[i], (size_t)(2 * QF_PER_BRANCH) * Q));
+        CK(c, dalloc(&c->qu[i], (size_t)QU_WORDS * Q));
+    }
+    CK(c, dalloc(&c->hitf, (size_t)(2 * HF_PER_BRANCH) * Q));
+    CK(c, dalloc(&c->hitp, (size_t)2 * Q));
+    CK(c, dalloc(&c->shf, (size_t)(SF_SLOT + 2 * SF_PER_SLOT) * S));
+    CK(c, dalloc(&c->shu, (size_t)(SU_REC + 2) * S));
+    CK(c, dalloc(&c->lacc, (size_t)6 * Q));
+    CK(c, dalloc(&c->ltot, (size_t)6 * Q));
+    CK(c, dalloc(&c->rpos, (size_t)R));
+    CK(c, dalloc(&c->rf, (size_t)RF_FIELDS * R));
+    c->qcap = Q;
+    c->shcap = S;
+    c->rcap = R;
+    c->graph_dirty = true;
+    return MER_OK;
+}
+
+// grid of the simple grid-stride kernels (resolve, loss, scatter)
+int grid_for(mer_ctx* c, int block) { return c->sms * (2048 / block); }
+
+PassArgs base_args(mer_ctx* c) {
+    PassArgs A;
+    memset(&A, 0, sizeof A);
+    A.probs = c->d_probs;
+    A.pstate = c->d_pstate;
+    A.inl_prob = -1;
+    A.iter_override = -1;
+    A.qf[0] = c->qf[0]; A.qf[1] = c->qf[1];
+    A.qu[0] = c->qu[0]; A.qu[1] = c->qu[1];
+    A.qcap = c->qcap;
+    A.hitf = c->hitf; A.hitp = c->hitp;
+    A.shf = c->shf; A.shu = c->shu; A.shcap = c->shcap;
+    A.cnt = c->cnt;
+    A.lacc = c->lacc; A.ltot = c->ltot;
+    A.rpos = c->rpos; A.rf = c->rf; A.rcap = c->rcap;
+    A.smem_nodes = c->shape.smem_nodes;
+    A.smem_prob = 0;
+    return A;
+}
+
+LaunchShape shape_of(mer_ctx* c) {
+    LaunchShape L = c->shape;
+    if (L.block <= 0) L.block = 128;
+    L.per_sm = c->cfg.blocks_per_sm;
+    L.sms = c->sms;
+    return L;
+}
+
+// zero the pass counters (not the error word) and run one pass
+int pass(mer_ctx* c, PassArgs A, int nb, int mode, int maxD) {
+    cudaMemsetAsync(c->cnt, 0, CNT_ERR * sizeof(uint32_t), c->st);
+    const LaunchShape L = shape_of(c);
+    return 1 + run_pass(A, nb, mode, maxD, L, c->st);
+}
+
+// the gradient part of one iteration for all problems (steps a1-a10)
+int enqueue_gradient(mer_ctx* c) {
+    int n = 0;
+    const int G = grid_for(c, 256);
+    cudaMemsetAsync(c->d_loss, 0, sizeof(double) * c->probs.size(), c->st);
+    n++;
+    PassArgs P = base_args(c);
+    P.entry_prob = c->d_prop_prob;
+    P.path_off = c->d_prop_off;
+    P.n_entries = (int)c->probs.size();
+    P.n_paths = c->P_prop;
+    PassArgs D = base_args(c);
+    D.entry_prob = c->d_fd_prob;
+    D.path_off = c->d_fd_off;
+    D.n_entries = c->n_fd;
+    D.n_paths = c->P_fd;
+    D.fd_kind = 1;
+    // primal images: FD pair (same counters at pi_i and pi_{i-1}) and the proportional image
+    if (c->n_fd > 0 && c->P_fd > 0) {
+        D.stream = MER_STREAM_FD_PRIMAL;
+        n += pass(c, D, 2, MODE_PRIMAL, c->maxD_fd);
+        n += run_resolve(D, 2, nullptr, nullptr, 0, G, c->st);
+    }
+    P.stream = MER_STREAM_PROP_PRIMAL;
+    n += pass(c, P, 1, MODE_PRIMAL, c->maxD_prop);
+    n += run_resolve(P, 1, nullptr, nullptr, 0, G, c->st);
+    // loss and adjoint images
+    n += run_l2(c->d_probs, c->d_pix_pref, (int)c->probs.size(), c->total_pix, c->n_fd > 0, c->d_loss, G, c->st);
+    // proportional gradient <F_i>: radiance pass, replay, scatter into F
+    P.stream = MER_STREAM_PROP_ADJ;
+    P.lacc = c->ltot;
+    n += pass(c, P, 1, MODE_ADJ_FWD, c->maxD_prop);
+    P.lacc = c->lacc;
+    P.ltot = c->ltot;
+    n += pass(c, P, 1, MODE_REPLAY, c->maxD_prop);
+    n += run_scatter(c->cnt, c->rpos, c->rf, c->rcap, c->d_probs, nullptr, 0, G, c->st);
+    // finite-difference gradient <dF_i> (Eq. est_triv): same for the pair, scatter into dF
+    if (c->n_fd > 0 && c->P_fd > 0) {
+        D.stream = MER_STREAM_FD_ADJ;
+        D.lacc = c->ltot;
+        n += pass(c, D, 2, MODE_ADJ_FWD, c->maxD_fd);
+        D.lacc = c->lacc;
+        D.ltot = c->ltot;
+        n += pass(c, D, 2, MODE_REPLAY, c->maxD_fd);
+        n += run_scatter(c->cnt, c->rpos, c->rf, c->rcap, c->d_probs, nullptr, 1, G, c->st);
+    }
+    return n;
+}
+
+int enqueue_update(mer_ctx* c) {
+    launch_update_ctx(c->d_segs, c->d_blk_off, (int)c->probs.size(), c->upd_blocks, c->d_pstate, c->d_partials, c->st);
+    return 2;
+}
+
+mer_status check_err_word(mer_ctx* c) {
+    uint32_t e = 0;
+    CK(c, cudaMemcpy(&e, c->cnt + CNT_ERR, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) {
+        cudaMemset(c->cnt + CNT_ERR, 0, sizeof(uint32_t));
+        return fail(c, (int)e, "a kernel reported an out-of-capacity write (code %u)", e);
+    }
+    return MER_OK;
+}
+
+// rebuild the pass tables, problem table and update segments after the problem set changed
+mer_status rebuild_tables(mer_ctx* c) {
+    const int n = (int)c->probs.size();
+    std::vector<ProblemDev> pd(n);
+    std::vector<int32_t> prop_prob(n), fd_prob;
+    std::vector<int64_t> prop_off(n + 1, 0), fd_off(1, 0), pix_pref(n + 1, 0);
+    std::vector<UpdSeg> segs(n);
+    std::vector<int64_t> blk_off(n + 1, 0);
+    c->maxD_prop = c->maxD_fd = 0;
+    for (int i = 0; i < n; ++i) {
+        Problem* p = c->probs[i];
+        pd[i] = p->dev;
+        prop_prob[i] = i;
+        prop_off[i + 1] = prop_off[i] + (int64_t)p->n_pix * p->spp_prop;
+        c->maxD_prop = std::max(c->maxD_prop, p->max_depth);
+        if (p->meta && p->spp_fd > 0) {
+            fd_prob.push_back(i);
+            fd_off.push_back(fd_off.back() + (int64_t)p->n_pix * p->spp_fd);
+            c->maxD_fd = std::max(c->maxD_fd, p->max_depth);
+        }
+        pix_pref[i + 1] = pix_pref[i] + p->n_pix;
+        segs[i] = p->seg;
+        segs[i].prob = i;
+        blk_off[i + 1] = blk_off[i] + update_blocks_for(p->n_par);
+    }
+    c->n_fd = (int)fd_prob.size();
+    c->P_prop = prop_off[n];
+    c->P_fd = fd_off.back();
+    c->total_pix = pix_pref[n];
+    c->upd_blocks = blk_off[n];
+    c->maxD = std::max(c->maxD_prop, c->maxD_fd);
+    cudaStreamSynchronize(c->st);
+    dfree(c->d_probs); dfree(c->d_prop_prob); dfree(c->d_prop_off); dfree(c->d_fd_prob); dfree(c->d_fd_off);
+    dfree(c->d_pix_pref); dfree(c->d_segs); dfree(c->d_blk_off); dfree(c->d_partials);
+    CK(c, dalloc(&c->d_probs, n));
+    CK(c, dalloc(&c->d_prop_prob, n));
+    CK(c, dalloc(&c->d_prop_off, n + 1));
+    CK(c, dalloc(&c->d_fd_prob, std::max<size_t>(1, fd_prob.size())));
+    CK(c, dalloc(&c->d_fd_off, fd_off.size()));
+    CK(c, dalloc(&c->d_pix_pref, n + 1));
+    CK(c, dalloc(&c->d_segs, n));
+    CK(c, dalloc(&c->d_blk_off, n + 1));
+    CK(c, dalloc(&c->d_partials, std::max<int64_t>(1, c->upd_blocks)));
+    CK(c, cudaMemcpy(c->d_probs, pd.data(), sizeof(ProblemDev) * n, cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->d_prop_prob, prop_prob.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->d_prop_off, prop_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+    if (!fd_prob.empty())
+        CK(c, cudaMemcpy(c->d_fd_prob, fd_prob.data(), sizeof(int32_t) * fd_prob.size(), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->d_fd_off, fd_off.data(), sizeof(int64_t) * fd_off.size(), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->d_pix_pref, pix_pref.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->d_segs, segs.data(), sizeof(UpdSeg) * n, cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->d_blk_off, blk_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+    int64_t need = std::max(c->P_prop, c->P_fd);
+    for (Problem* p : c->probs) need = std::max<int64_t>(need, p->n_pix);
+    mer_status s = ensure_wavefront(c, need, c->maxD);
+    if (s) return s;
+    c->graph_dirty = true;
+    return MER_OK;
+}
+
+mer_status reset_state(mer_ctx* c, Problem* p) {
+    const size_t nb = sizeof(float) * (size_t)p->n_par;
+    CK(c, cudaMemsetAsync(p->F, 0, nb, c->st));
+    CK(c, cudaMemsetAsync(p->dF, 0, nb, c->st));
+    CK(c, cudaMemsetAsync(p->m2f, 0, nb, c->st));
+    CK(c, cudaMemsetAsync(p->m2d, 0, nb, c->st));
+    CK(c, cudaMemsetAsync(p->mean, 0, nb, c->st));
+    CK(c, cudaMemsetAsync(p->var, 0, nb, c->st));
+    run_fill(p->ap, p->n_par, -INFINITY, c->st);
+    ProbState ps{};
+    CK(c, cudaMemcpyAsync(c->d_pstate + p->id, &ps, sizeof ps, cudaMemcpyHostToDevice, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    return MER_OK;
+}
+
+Problem* get_prob(mer_ctx* c, int32_t pid) {
+    if (!c || pid < 0 || pid >= (int32_t)c->probs.size()) return nullptr;
+    return c->probs[pid];
+}
+
+mer_status copy_in(mer_ctx* c, float* dst, const float* src, size_t n, int on_device) {
+    if (!src) return fail(c, MER_ERR_INVALID_ARG, "null input pointer");
+    CK(c, cudaMemcpyAsync(dst, src, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          c->st));
+    if (!on_device) CK(c, cudaStreamSynchronize(c->st));
+    return MER_OK;
+}
+
+int32_t read_cur(mer_ctx* c, Problem* p) {
+    ProbState ps{};
+    cudaMemcpyAsync(&ps, c->d_pstate + p->id, sizeof ps, cudaMemcpyDeviceToHost, c->st);
+    cudaStreamSynchronize(c->st);
+    return ps.cur;
+}
+
+// single-problem pass helpers for the API calls (chunked over samples)
+PassArgs single_args(mer_ctx* c, Problem* p, uint32_t stream, uint32_t iteration, int spp) {
+    PassArgs A = base_args(c);
+    A.inl_prob = p->id;
+    A.stream = stream;
+    A.iter_override = (int32_t)iteration;
+    A.spp_override = spp;
+    A.smem_prob = p->id;
+    return A;
+}
+
+int64_t chunk_spp(mer_ctx* c, Problem* p, int spp) {
+    return std::max<int64_t>(1, std::min<int64_t>(spp, c->qcap / std::max(1, p->n_pix)));
+}
+
+}  // namespace
+
+// =====================================================================================
+// exported entry points
+// =====================================================================================
+extern "C" {
+
+mer_status mer_hyper_default(mer_hyper* h) {
+    if (!h) return fail(nullptr, MER_ERR_INVALID_ARG, "null hyper");
+    h->mode = MER_MODE_META;
+    h->lr = 0.01f;
+    h->beta_f = 0.99f;
+    h->beta_d = 0.9f;
+    h->eps = 1e-8f;
+    h->eps_alpha = 1e-30f;
+    h->beta1 = 0.9f;
+    h->beta2 = 0.999f;
+    return MER_OK;
+}
+
+const char* mer_last_error(const mer_ctx* ctx) { return ctx ? ctx->err.c_str() : t_err.c_str(); }
+
+mer_status mer_create(const mer_config* cfg, void* cuda_stream, mer_ctx** out) {
+    if (!out) return fail(nullptr, MER_ERR_INVALID_ARG, "null output");
+    *out = nullptr;
+    mer_config def{};
+    const mer_config& C = cfg ? *cfg : def;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(nullptr, MER_ERR_CUDA, "no CUDA device available");
+    if (C.device < 0 || C.device >= ndev) return fail(nullptr, MER_ERR_INVALID_ARG, "bad device %d", C.device);
+    mer_ctx* c = new mer_ctx();
+    c->cfg = C;
+    c->device = C.device;
+    c->user = (cudaStream_t)cuda_stream;
+    cudaSetDevice(c->device);
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->shape.block = C.block_size > 0 ? C.block_size : 128;
+    c->shape.smem_nodes = C.smem_nodes;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+    if (!e) e = cudaMalloc(&c->d_pstate, sizeof(ProbState) * MER_MAX_PROBLEMS);
+    if (!e) e = cudaMalloc(&c->d_loss, sizeof(double) * MER_MAX_PROBLEMS);
+    if (!e) e = cudaMalloc(&c->cnt, sizeof(uint32_t) * CNT_WORDS);
+    if (!e) e = cudaMemset(c->cnt, 0, sizeof(uint32_t) * CNT_WORDS);
+    if (!e) e = cudaMemset(c->d_loss, 0, sizeof(double) * MER_MAX_PROBLEMS);
+    if (!e && c->shape.smem_nodes > 0) e = set_trace_smem_limits(c->shape.smem_nodes);
+    if (e) {
+        fail(nullptr, MER_ERR_CUDA, "context setup failed: %s", cudaGetErrorString(e));
+        mer_destroy(c);
+        return MER_ERR_CUDA;
+    }
+    *out = c;
+    return MER_OK;
+}
+
+void mer_destroy(mer_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (Problem* p : c->probs) {
+        for (void* a : p->allocs) dfree(a);
+        delete p;
+    }
+    free_wavefront(c);
+    dfree(c->d_probs); dfree(c->d_pstate); dfree(c->d_loss); dfree(c->cnt);
+    dfree(c->d_prop_prob); dfree(c->d_prop_off); dfree(c->d_fd_prob); dfree(c->d_fd_off); dfree(c->d_pix_pref);
+    dfree(c->d_segs); dfree(c->d_blk_off); dfree(c->d_partials);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_id) {
+    if (!c || !d || !problem_id) return fail(c, MER_ERR_INVALID_ARG, "null argument");
+    if ((int)c->probs.size() >= MER_MAX_PROBLEMS) return fail(c, MER_ERR_INVALID_ARG, "too many problems");
+    if (d->n_tris < 0 || d->n_verts < 0 || d->n_spheres < 0 || d->n_mats <= 0 || d->n_quads < 0)
+        return fail(c, MER_ERR_INVALID_ARG, "negative counts or no materials");
+    if ((d->n_tris > 0 && (!d->positions || !d->uvs || !d->tris || !d->tri_mat || !d->tri_light)) ||
+        (d->n_spheres > 0 && (!d->spheres || !d->sph_mat)) || !d->mat_type || !d->mat_textured || !d->mat_const ||
+        (d->n_quads > 0 && !d->quads))
+        return fail(c, MER_ERR_INVALID_ARG, "missing scene arrays");
+    if (d->width <= 0 || d->height <= 0 || (int64_t)d->width * d->height > (1ll << 31))
+        return fail(c, MER_ERR_INVALID_ARG, "bad image size");
+    if (!(d->tex_c == 3 || d->tex_c == 5) || d->tex_w <= 0 || d->tex_h <= 0 || d->tex_w > 4094 || d->tex_h > 4094)
+        return fail(c, MER_ERR_INVALID_ARG, "texture must be C in {3,5}, 1..4094 texels per side");
+    if (d->max_depth < 1 || d->max_depth > MER_MAX_DEPTH) return fail(c, MER_ERR_INVALID_ARG, "max_depth out of range");
+    if (d->spp_prop < 1 || d->spp_fd < 0) return fail(c, MER_ERR_INVALID_ARG, "bad spp");
+    for (int i = 0; i < d->n_mats; ++i) {
+        if (d->mat_type[i] != 0 && d->mat_type[i] != 1) return fail(c, MER_ERR_INVALID_ARG, "bad material type");
+        if (d->mat_type[i] == 1 && d->mat_textured[i] && d->tex_c != 5)
+            return fail(c, MER_ERR_INVALID_ARG, "textured principled material needs a 5-channel texture");
+    }
+    for (int i = 0; i < d->n_tris; ++i) {
+        for (int k = 0; k < 3; ++k)
+            if (d->tris[3 * i + k] < 0 || d->tris[3 * i + k] >= d->n_verts)
+                return fail(c, MER_ERR_INVALID_ARG, "triangle %d has a bad vertex index", i);
+        if (d->tri_mat[i] < 0 || d->tri_mat[i] >= d->n_mats) return fail(c, MER_ERR_INVALID_ARG, "bad tri material");
+        if (d->tri_light[i] < -1 || d->tri_light[i] >= d->n_quads) return fail(c, MER_ERR_INVALID_ARG, "bad tri light");
+    }
+    for (int i = 0; i < d->n_spheres; ++i)
+        if (d->sph_mat[i] < 0 || d->sph_mat[i] >= d->n_mats || !(d->spheres[8 * i + 3] > 0.0f))
+            return fail(c, MER_ERR_INVALID_ARG, "bad sphere %d", i);
+    cudaSetDevice(c->device);
+
+    Problem* p = new Problem();
+    p->id = (int32_t)c->probs.size();
+    p->hyper = d->hyper;
+    if (p->hyper.lr == 0.0f && p->hyper.beta_f == 0.0f) mer_hyper_default(&p->hyper);
+    p->meta = p->hyper.mode == MER_MODE_META;
+    p->max_depth = d->max_depth;
+    p->spp_prop = d->spp_prop;
+    p->spp_fd = p->meta ? d->spp_fd : 0;
+    p->width = d->width;
+    p->height = d->height;
+    p->n_pix = d->width * d->height;
+    p->C = d->tex_c;
+    p->W = d->tex_w;
+    p->H = d->tex_h;
+    p->n_par = (int64_t)p->C * p->W * p->H;
+    for (int k = 0; k < 8; ++k) {
+        p->lo[k] = d->clamp_lo[k];
+        p->hi[k] = d->clamp_hi[k];
+    }
+    auto bail = [&](mer_status s) {
+        for (void* a : p->allocs) dfree(a);
+        delete p;
+        return s;
+    };
+    auto alloc = [&](auto** ptr, size_t count) -> cudaError_t {
+        cudaError_t e = dalloc(ptr, std::max<size_t>(count, 1));
+        if (!e) p->allocs.push_back((void*)*ptr);
+        return e;
+    };
+#define AK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_) return bail(fail(c, MER_ERR_OOM, "allocation failed: %s", cudaGetErrorString(e_))); \
+    } while (0)
+
+    // ---- geometry: BVH over triangles, leaf-ordered triangle records, attributes ----
+    ProblemDev& D = p->dev;
+    memset(&D, 0, sizeof D);
+    D.n_tris = d->n_tris;
+    D.n_sph = d->n_spheres;
+    D.n_quads = d->n_quads;
+    D.has_env = d->has_env ? 1 : 0;
+    D.n_lights = d->n_quads + D.has_env;
+    for (int k = 0; k < 3; ++k) D.env[k] = d->has_env ? d->env[k] : 0.0f;
+    if (d->n_tris > 0) {
+        std::vector<HostNode> hn;
+        std::vector<int> order;
+        build_bvh(d->positions, d->tris, d->n_tris, hn, order);
+        std::vector<Node> nodes(hn.size());
+        for (size_t i = 0; i < hn.size(); ++i) {
+            const HostNode& h = hn[i];
+            nodes[i].a = make_float4(h.lo[0][0], h.hi[0][0], h.lo[0][1], h.hi[0][1]);
+            nodes[i].b = make_float4(h.lo[1][0], h.hi[1][0], h.lo[1][1], h.hi[1][1]);
+            nodes[i].c = make_float4(h.lo[0][2], h.hi[0][2], h.lo[1][2], h.hi[1][2]);
+            nodes[i].d = make_int4(h.child[0], h.child[1], 0, 0);
+        }
+        std::vector<TriGeo> tg(d->n_tris);
+        std::vector<TriAttr> ta(d->n_tris);
+        for (int t = 0; t < d->n_tris; ++t) {
+            const int* T = d->tris + 3 * t;
+            const float* a = d->positions + 3 * T[0];
+            const float* b = d->positions + 3 * T[1];
+            const float* cc = d->positions + 3 * T[2];
+            double e1[3], e2[3];
+            for (int k = 0; k < 3; ++k) {
+                e1[k] = (double)b[k] - a[k];
+                e2[k] = (double)cc[k] - a[k];
+            }
+            double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+            const double ln = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            TriAttr& A = ta[t];
+            for (int k = 0; k < 3; ++k) A.n[k] = ln > 0 ? (float)(n[k] / ln) : (k == 2 ? 1.0f : 0.0f);
+            for (int v = 0; v < 3; ++v) {
+                A.uv[2 * v] = d->uvs[2 * T[v]];
+                A.uv[2 * v + 1] = d->uvs[2 * T[v] + 1];
+            }
+            A.mat = d->tri_mat[t];
+            A.light = d->tri_light[t];
+            A.pad = 0;
+        }
+        for (int k = 0; k < d->n_tris; ++k) {
+            const int t = order[k];
+            const int* T = d->tris + 3 * t;
+            const float* a = d->positions + 3 * T[0];
+            const float* b = d->positions + 3 * T[1];
+            const float* cc = d->positions + 3 * T[2];
+            int tid = t;
+            float tidf;
+            memcpy(&tidf, &tid, 4);
+            tg[k].v0 = make_float4(a[0], a[1], a[2], tidf);
+            tg[k].e1 = make_float4((float)((double)b[0] - a[0]), (float)((double)b[1] - a[1]),
+                                   (float)((double)b[2] - a[2]), 0.0f);
+            tg[k].e2 = make_float4((float)((double)cc[0] - a[0]), (float)((double)cc[1] - a[1]),
+                                   (float)((double)cc[2] - a[2]), 0.0f);
+        }
+        Node* dn;
+        TriGeo* dt;
+        TriAttr* da;
+        AK(alloc(&dn, nodes.size()));
+        AK(alloc(&dt, tg.size()));
+        AK(alloc(&da, ta.size()));
+        AK(cudaMemcpy(dn, nodes.data(), sizeof(Node) * nodes.size(), cudaMemcpyHostToDevice));
+        AK(cudaMemcpy(dt, tg.data(), sizeof(TriGeo) * tg.size(), cudaMemcpyHostToDevice));
+        AK(cudaMemcpy(da, ta.data(), sizeof(TriAttr) * ta.size(), cudaMemcpyHostToDevice));
+        D.nodes = dn;
+        D.n_nodes = (int32_t)nodes.size();
+        D.tris = dt;
+        D.attr = da;
+    }
+    {
+        std::vector<Sphere> sp(d->n_spheres);
+        for (int i = 0; i < d->n_spheres; ++i) {
+            const float* S = d->spheres + 8 * i;
+            sp[i].cr = make_float4(S[0], S[1], S[2], S[3]);
+            sp[i].uvr = make_float4(S[4], S[5], S[6], S[7]);
+            sp[i].mat = d->sph_mat[i];
+        }
+        std::vector<Material> mt(d->n_mats);
+        for (int i = 0; i < d->n_mats; ++i) {
+            mt[i].type = d->mat_type[i];
+            mt[i].textured = d->mat_textured[i];
+            for (int k = 0; k < 5; ++k) mt[i].c[k] = d->mat_const[5 * i + k];
+            mt[i].pad = 0;
+        }
+        std::vector<QuadLight> ql(d->n_quads);
+        for (int i = 0; i < d->n_quads; ++i) {
+            const float* Q = d->quads + 12 * i;
+            QuadLight& L = ql[i];
+            for (int k = 0; k < 3; ++k) {
+                L.p0[k] = Q[k];
+                L.e1[k] = Q[3 + k];
+                L.e2[k] = Q[6 + k];
+                L.le[k] = Q[9 + k];
+            }
+            const double n[3] = {(double)Q[4] * Q[8] - (double)Q[5] * Q[7], (double)Q[5] * Q[6] - (double)Q[3] * Q[8],
+                                 (double)Q[3] * Q[7] - (double)Q[4] * Q[6]};
+            const double a = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            if (!(a > 0)) return bail(fail(c, MER_ERR_INVALID_ARG, "degenerate quad light %d", i));
+            for (int k = 0; k < 3; ++k) L.n[k] = (float)(n[k] / a);
+            L.area = (float)a;
+        }
+        Sphere* ds;
+        Material* dm;
+        QuadLight* dq;
+        AK(alloc(&ds, sp.size()));
+        AK(alloc(&dm, mt.size()));
+        AK(alloc(&dq, ql.size()));
+        if (!sp.empty()) AK(cudaMemcpy(ds, sp.data(), sizeof(Sphere) * sp.size(), cudaMemcpyHostToDevice));
+        AK(cudaMemcpy(dm, mt.data(), sizeof(Material) * mt.size(), cudaMemcpyHostToDevice));
+        if (!ql.empty()) AK(cudaMemcpy(dq, ql.data(), sizeof(QuadLight) * ql.size(), cudaMemcpyHostToDevice));
+        D.sph = ds;
+        D.mats = dm;
+        D.quads = dq;
+    }
+    // camera: pinhole, vertical fov, row 0 at the top
+    {
+        double eye[3], f[3], up[3], r[3], u[3];
+        for (int k = 0; k < 3; ++k) {
+            eye[k] = d->eye[k];
+            f[k] = (double)d->target[k] - d->eye[k];
+            up[k] = d->up[k];
+        }
+        double lf = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        for (double& x : f) x /= lf;
+        r[0] = f[1] * up[2] - f[2] * up[1];
+        r[1] = f[2] * up[0] - f[0] * up[2];
+        r[2] = f[0] * up[1] - f[1] * up[0];
+        const double lr = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (!(lf > 0) || !(lr > 0)) return bail(fail(c, MER_ERR_INVALID_ARG, "degenerate camera"));
+        for (double& x : r) x /= lr;
+        u[0] = r[1] * f[2] - r[2] * f[1];
+        u[1] = r[2] * f[0] - r[0] * f[2];
+        u[2] = r[0] * f[1] - r[1] * f[0];
+        const double th = std::tan(0.5 * (double)d->fov_deg * 3.14159265358979323846 / 180.0);
+        const double asp = (double)d->width / (double)d->height;
+        for (int k = 0; k < 3; ++k) {
+            D.cam_o[k] = (float)eye[k];
+            D.cam_f[k] = (float)f[k];
+            D.cam_r[k] = (float)(r[k] * th * asp);
+            D.cam_u[k] = (float)(u[k] * th);
+        }
+    }
+    D.width = d->width;
+    D.height = d->height;
+    D.n_pix = p->n_pix;
+    D.tex_c = p->C;
+    D.tex_w = p->W;
+    D.tex_h = p->H;
+    D.n_par = p->n_par;
+    D.max_depth = p->max_depth;
+    D.spp_prop = p->spp_prop;
+    D.spp_fd = p->spp_fd;
+    D.seed = d->seed;
+    D.key_id = d->key_id;
+    // ---- optimiser state and images ----
+    const size_t np = (size_t)p->n_par, npx = (size_t)p->n_pix * 3;
+    AK(alloc(&p->pslot[0], np));
+    AK(alloc(&p->pslot[1], np));
+    AK(alloc(&p->F, np));
+    AK(alloc(&p->dF, np));
+    AK(alloc(&p->m2f, np));
+    AK(alloc(&p->m2d, np));
+    AK(alloc(&p->mean, np));
+    AK(alloc(&p->var, np));
+    AK(alloc(&p->ap, np));
+    AK(alloc(&p->target, npx));
+    AK(alloc(&p->img, npx));
+    AK(alloc(&p->dimg, npx));
+    if (p->meta) {
+        AK(alloc(&p->imgA, npx));
+        AK(alloc(&p->imgB, npx));
+        AK(alloc(&p->dimgA, npx));
+        AK(alloc(&p->dimgB, npx));
+    }
+    AK(cudaMemset(p->pslot[0], 0, np * 4));
+    AK(cudaMemset(p->pslot[1], 0, np * 4));
+    AK(cudaMemset(p->target, 0, npx * 4));
+    D.pslot[0] = p->pslot[0];
+    D.pslot[1] = p->pslot[1];
+    D.F = p->F;
+    D.dF = p->dF;
+    D.target = p->target;
+    D.img = p->img;
+    D.dimg = p->dimg;
+    D.imgA = p->imgA;
+    D.imgB = p->imgB;
+    D.dimgA = p->dimgA;
+    D.dimgB = p->dimgB;
+    UpdSeg& S = p->seg;
+    memset(&S, 0, sizeof S);
+    S.pA = p->pslot[0];
+    S.pB = p->pslot[1];
+    S.F = p->F;
+    S.dF = p->dF;
+    S.m2f = p->m2f;
+    S.m2d = p->m2d;
+    S.mean = p->mean;
+    S.var = p->var;
+    S.ap = p->ap;
+    S.n = p->n_par;
+    S.C = p->C;
+    S.prob = p->id;
+    S.zero_grads = 1;
+    for (int k = 0; k < 8; ++k) {
+        S.lo[k] = p->lo[k];
+        S.hi[k] = p->hi[k];
+    }
+    S.hyper = p->hyper;
+#undef AK
+    c->probs.push_back(p);
+    mer_status s = reset_state(c, p);
+    if (!s) s = rebuild_tables(c);
+    if (s) {
+        c->probs.pop_back();
+        for (void* a : p->allocs) dfree(a);
+        delete p;
+        return s;
+    }
+    *problem_id = p->id;
+    return MER_OK;
+}
+
+mer_status mer_params_set(mer_ctx* c, int32_t pid, const float* hwc, int32_t on_device) {
+    Problem* p = get_prob(c, pid);
+    if (!p) return fail(c, MER_ERR_INVALID_ARG, "bad problem id");
+    Guard g(c);
+    mer_status s = copy_in(c, p->pslot[0], hwc, p->n_par, on_device);
+    if (s) return s;
+    CK(c, cudaMemcpyAsync(p->pslot[1], p->pslot[0], p->n_par * 4, cudaMemcpyDeviceToDevice, c->st));
+    return reset_state(c, p);
+}
+
+mer_status mer_params_get(mer_ctx* c, int32_t pid, float* out, int32_t on_device) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !out) return fail(c, MER_ERR_INVALID_ARG, "bad problem id or output");
+    Guard g(c);
+    const int cur = read_cur(c, p);
+    CK(c, cudaMemcpyAsync(out, p->pslot[cur], p->n_par * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          c->st));
+    if (!on_device) CK(c, cudaStreamSynchronize(c->st));
+    return MER_OK;
+}
+
+mer_status mer_target_set(mer_ctx* c, int32_t pid, const float* img, int32_t on_device) {
+    Problem* p = get_prob(c, pid);
+    if (!p) return fail(c, MER_ERR_INVALID_ARG, "bad problem id");
+    Guard g(c);
+    return copy_in(c, p->target, img, (size_t)p->n_pix * 3, on_device);
+}
+
+mer_status mer_render(mer_ctx* c, int32_t pid, const float* tex, int32_t spp, uint32_t stream, uint32_t iteration,
+                      float* img) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !img || spp < 1) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_render");
+    Guard g(c);
+    const int64_t ch = chunk_spp(c, p, spp);
+    for (int64_t s0 = 0; s0 < spp; s0 += ch) {
+        const int64_t ns = std::min<int64_t>(ch, spp - s0);
+        PassArgs A = single_args(c, p, stream, iteration, spp);
+        A.tex_over[0] = tex;
+        A.n_paths = ns * p->n_pix;
+        A.sample_base = (int32_t)s0;
+        pass(c, A, 1, MODE_PRIMAL, p->max_depth);
+        run_resolve(A, 1, img, nullptr, s0 > 0, grid_for(c, 256), c->st);
+    }
+    CK(c, cudaGetLastError());
+    return MER_OK;
+}
+
+mer_status mer_target_render(mer_ctx* c, int32_t pid, const float* tex, int32_t spp) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !tex) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_target_render");
+    return mer_render(c, pid, tex, spp, MER_STREAM_TARGET, 0, p->target);
+}
+
+mer_status mer_render_samples(mer_ctx* c, int32_t pid, const float* tex, int32_t spp, uint32_t stream,
+                              uint32_t iteration, float* out) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !out || spp < 1) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_render_samples");
+    Guard g(c);
+    const int64_t ch = chunk_spp(c, p, spp);
+    for (int64_t s0 = 0; s0 < spp; s0 += ch) {
+        const int64_t ns = std::min<int64_t>(ch, spp - s0);
+        PassArgs A = single_args(c, p, stream, iteration, spp);
+        A.tex_over[0] = tex;
+        A.n_paths = ns * p->n_pix;
+        A.sample_base = (int32_t)s0;
+        pass(c, A, 1, MODE_PRIMAL, p->max_depth);
+        run_samples_out(A, out, grid_for(c, 256), c->st);
+    }
+    CK(c, cudaGetLastError());
+    return MER_OK;
+}
+
+mer_status mer_render_pair(mer_ctx* c, int32_t pid, const float* texA, const float* texB, int32_t spp, uint32_t stream,
+                           uint32_t iteration, float* imgA, float* imgB) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !texA || !texB || !imgA || !imgB || spp < 1)
+        return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_render_pair");
+    Guard g(c);
+    const int64_t ch = chunk_spp(c, p, spp);
+    for (int64_t s0 = 0; s0 < spp; s0 += ch) {
+        const int64_t ns = std::min<int64_t>(ch, spp - s0);
+        PassArgs A = single_args(c, p, stream, iteration, spp);
+        A.tex_over[0] = texA;
+        A.tex_over[1] = texB;
+        A.n_paths = ns * p->n_pix;
+        A.sample_base = (int32_t)s0;
+        pass(c, A, 2, MODE_PRIMAL, p->max_depth);
+        run_resolve(A, 2, imgA, imgB, s0 > 0, grid_for(c, 256), c->st);
+    }
+    CK(c, cudaGetLastError());
+    return MER_OK;
+}
+
+static mer_status adjoint_impl(mer_ctx* c, Problem* p, int nb, const float* texA, const float* texB,
+                               const float* dA, const float* dB, int32_t spp, uint32_t stream, uint32_t iteration,
+                               float* grad) {
+    Guard g(c);
+    CK(c, cudaMemsetAsync(grad, 0, sizeof(float) * p->n_par, c->st));
+    const int64_t ch = chunk_spp(c, p, spp);
+    for (int64_t s0 = 0; s0 < spp; s0 += ch) {
+        const int64_t ns = std::min<int64_t>(ch, spp - s0);
+        PassArgs A = single_args(c, p, stream, iteration, spp);
+        A.tex_over[0] = texA;
+        A.tex_over[1] = texB;
+        A.dimg_over[0] = dA;
+        A.dimg_over[1] = dB;
+        A.n_paths = ns * p->n_pix;
+        A.sample_base = (int32_t)s0;
+        A.lacc = c->ltot;
+        pass(c, A, nb, MODE_ADJ_FWD, p->max_depth);
+        A.lacc = c->lacc;
+        A.ltot = c->ltot;
+        pass(c, A, nb, MODE_REPLAY, p->max_depth);
+        run_scatter(c->cnt, c->rpos, c->rf, c->rcap, c->d_probs, grad, 0, grid_for(c, 256), c->st);
+    }
+    CK(c, cudaGetLastError());
+    return MER_OK;
+}
+
+mer_status mer_adjoint(mer_ctx* c, int32_t pid, const float* tex, const float* dimg, int32_t spp, uint32_t stream,
+                       uint32_t iteration, float* grad) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !dimg || !grad || spp < 1) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_adjoint");
+    return adjoint_impl(c, p, 1, tex, nullptr, dimg, nullptr, spp, stream, iteration, grad);
+}
+
+mer_status mer_adjoint_pair(mer_ctx* c, int32_t pid, const float* texA, const float* texB, const float* dA,
+                            const float* dB, int32_t spp, uint32_t stream, uint32_t iteration, float* grad) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !texA || !texB || !dA || !dB || !grad || spp < 1)
+        return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_adjoint_pair");
+    return adjoint_impl(c, p, 2, texA, texB, dA, dB, spp, stream, iteration, grad);
+}
+
+mer_status mer_gradient_step(mer_ctx* c) {
+    if (!c || c->probs.empty()) return fail(c, MER_ERR_STATE, "no problems");
+    Guard g(c);
+    c->launches = enqueue_gradient(c);
+    CK(c, cudaGetLastError());
+    return MER_OK;
+}
+
+mer_status mer_update_step(mer_ctx* c) {
+    if (!c || c->probs.empty()) return fail(c, MER_ERR_STATE, "no problems");
+    Guard g(c);
+    c->launches = enqueue_update(c);
+    CK(c, cudaGetLastError());
+    return MER_OK;
+}
+
+mer_status mer_iterate(mer_ctx* c, int32_t n_iters, int32_t use_graph) {
+    if (!c || c->probs.empty()) return fail(c, MER_ERR_STATE, "no problems");
+    if (n_iters < 0) return fail(c, MER_ERR_INVALID_ARG, "negative iteration count");
+    Guard g(c);
+    if (!use_graph) {
+        for (int i = 0; i < n_iters; ++i) {
+            c->launches = enqueue_gradient(c);
+            c->launches += enqueue_update(c);
+        }
+        CK(c, cudaGetLastError());
+        return MER_OK;
+    }
+    if (c->graph_dirty || !c->gexec) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        CK(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        int n = enqueue_gradient(c);
+        n += enqueue_update(c);
+        cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+        if (e) return fail(c, MER_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e) return fail(c, MER_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        c->launches = n;
+        c->graph_dirty = false;
+    }
+    for (int i = 0; i < n_iters; ++i) CK(c, cudaGraphLaunch(c->gexec, c->st));
+    return MER_OK;
+}
+
+mer_status mer_grads_get(mer_ctx* c, int32_t pid, float* F_out, float* dF_out, int32_t on_device) {
+    Problem* p = get_prob(c, pid);
+    if (!p) return fail(c, MER_ERR_INVALID_ARG, "bad problem id");
+    Guard g(c);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (F_out) CK(c, cudaMemcpyAsync(F_out, p->F, p->n_par * 4, k, c->st));
+    if (dF_out) CK(c, cudaMemcpyAsync(dF_out, p->dF, p->n_par * 4, k, c->st));
+    if (!on_device) CK(c, cudaStreamSynchronize(c->st));
+    return MER_OK;
+}
+
+mer_status mer_stats(mer_ctx* c, int32_t pid, mer_iter_stats* out) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !out) return fail(c, MER_ERR_INVALID_ARG, "bad problem id or output");
+    Guard g(c);
+    ProbState ps{};
+    double la = 0.0;
+    CK(c, cudaMemcpyAsync(&ps, c->d_pstate + pid, sizeof ps, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaMemcpyAsync(&la, c->d_loss + pid, sizeof la, cudaMemcpyDeviceToHost, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    out->iteration = ps.iteration;
+    out->loss = la / (3.0 * p->n_pix);
+    out->dpi_norm2 = ps.dpi_norm2;
+    out->count_f = ps.count_f;
+    out->count_d = ps.count_d;
+    out->paths_per_iter = (int64_t)p->n_pix * (3 * p->spp_prop + 6 * p->spp_fd);
+    return check_err_word(c);
+}
+
+mer_status mer_state_get(mer_ctx* c, int32_t pid, mer_state_view* out) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !out) return fail(c, MER_ERR_INVALID_ARG, "bad problem id or output");
+    Guard g(c);
+    const int cur = read_cur(c, p);
+    out->pi_cur = p->pslot[cur];
+    out->pi_prev = p->pslot[cur ^ 1];
+    out->F = p->F;
+    out->dF = p->dF;
+    out->m2f = p->m2f;
+    out->m2d = p->m2d;
+    out->mean = p->mean;
+    out->var = p->var;
+    out->alpha_prev = p->ap;
+    out->n = p->n_par;
+    return MER_OK;
+}
+
+mer_status mer_launch_count(mer_ctx* c, int64_t* out) {
+    if (!c || !out) return fail(c, MER_ERR_INVALID_ARG, "null argument");
+    *out = c->launches;
+    return MER_OK;
+}
+
+mer_status mer_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int64_t n, uint32_t* out, void* stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return fail(nullptr, MER_ERR_INVALID_ARG, "bad arguments to mer_philox");
+    run_philox(k0, k1, ctr, n, out, (cudaStream_t)stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e) return fail(nullptr, MER_ERR_CUDA, "mer_philox: %s", cudaGetErrorString(e));
+    return MER_OK;
+}
+
+// --------------------------------------------------------------------------------------
+// standalone update: scratch for the per-block partial norms is owned by the library,
+// one growing buffer per device
+// --------------------------------------------------------------------------------------
+static std::mutex g_scratch_mu;
+static std::vector<std::pair<double*, int64_t>> g_scratch;   // per device
+
+mer_status mer_meta_step_raw(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
+                             const float* pi, float* pi_next, float* F, float* dF, float* m2f, float* m2d, float* mean,
+                             float* var, float* alpha_prev, int32_t iteration, int32_t count_f, int32_t count_d,
+                             double dpi_norm2, int32_t zero_grads, double* out, void* stream) {
+    if (!hyper || n < 0 || C < 1 || C > 8 || !lo || !hi || !out)
+        return fail(nullptr, MER_ERR_INVALID_ARG, "bad arguments to mer_meta_step_raw");
+    const bool meta = hyper->mode == MER_MODE_META;
+    if (n > 0 && (!pi || !pi_next || !F || !m2f || !mean || (meta && (!dF || !m2d || !var || !alpha_prev))))
+        return fail(nullptr, MER_ERR_INVALID_ARG, "missing arrays in mer_meta_step_raw");
+    const void* ptrs[] = {pi, pi_next, F, dF, m2f, m2d, mean, var, alpha_prev};
+    for (const void* q : ptrs)
+        if (q && ((uintptr_t)q & 15u)) return fail(nullptr, MER_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
+    if (pi == pi_next && n > 0) return fail(nullptr, MER_ERR_INVALID_ARG, "pi_next may not alias pi");
+    UpdSeg S;
+    memset(&S, 0, sizeof S);
+    S.pA = const_cast<float*>(pi);
+    S.pB = pi_next;
+    S.F = F; S.dF = dF; S.m2f = m2f; S.m2d = m2d; S.mean = mean; S.var = var; S.ap = alpha_prev;
+    S.n = n;
+    S.C = C;
+    S.zero_grads = zero_grads;
+    for (int k = 0; k < C; ++k) {
+        S.lo[k] = lo[k];
+        S.hi[k] = hi[k];
+    }
+    S.hyper = *hyper;
+    const int64_t nb = update_blocks_for(n);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if ((int)g_scratch.size() <= dev) g_scratch.resize(dev + 1, {nullptr, 0});
+        auto& sl = g_scratch[dev];
+        if (sl.second < std::max<int64_t>(nb, 1)) {
+            if (sl.first) {
+                cudaDeviceSynchronize();
+                cudaFree(sl.first);
+            }
+            sl.first = nullptr;
+            sl.second = 0;
+            const int64_t want = std::max<int64_t>(nb, 1024);
+            if (cudaMalloc(&sl.first, sizeof(double) * want) != cudaSuccess)
+                return fail(nullptr, MER_ERR_OOM, "scratch allocation failed");
+            sl.second = want;
+        }
+        scratch = sl.first;
+    }
+    const cudaError_t e = launch_update_raw(S, iteration, count_f, count_d, dpi_norm2, scratch, nb, out,
+                                            (cudaStream_t)stream);
+    if (e) return fail(nullptr, MER_ERR_CUDA, "mer_meta_step_raw: %s", cudaGetErrorString(e));
+    return MER_OK;
+}
+
+// --------------------------------------------------------------------------------------
+// checkpoint: per problem ProbState + the nine parameter-shaped arrays
+// --------------------------------------------------------------------------------------
+mer_status mer_checkpoint_save(mer_ctx* c, void* buf, size_t* len) {
+    if (!c || !len) return fail(c, MER_ERR_INVALID_ARG, "null argument");
+    size_t need = sizeof(uint64_t) * 2;
+    for (Problem* p : c->probs) need += sizeof(ProbState) + 9 * sizeof(float) * (size_t)p->n_par;
+    if (!buf) {
+        *len = need;
+        return MER_OK;
+    }
+    if (*len < need) return fail(c, MER_ERR_INVALID_ARG, "checkpoint buffer too small (%zu < %zu)", *len, need);
+    Guard g(c);
+    char* w = (char*)buf;
+    const uint64_t hdr[2] = {0x4d4552434b505431ull, (uint64_t)c->probs.size()};
+    memcpy(w, hdr, sizeof hdr);
+    w += sizeof hdr;
+    for (Problem* p : c->probs) {
+        CK(c, cudaMemcpyAsync(w, c->d_pstate + p->id, sizeof(ProbState), cudaMemcpyDeviceToHost, c->st));
+        w += sizeof(ProbState);
+        float* arrs[9] = {p->pslot[0], p->pslot[1], p->F, p->dF, p->m2f, p->m2d, p->mean, p->var, p->ap};
+        for (float* a : arrs) {
+            CK(c, cudaMemcpyAsync(w, a, sizeof(float) * p->n_par, cudaMemcpyDeviceToHost, c->st));
+            w += sizeof(float) * p->n_par;
+        }
+    }
+    CK(c, cudaStreamSynchronize(c->st));
+    *len = need;
+    return MER_OK;
+}
+
+mer_status mer_checkpoint_load(mer_ctx* c, const void* buf, size_t len) {
+    if (!c || !buf) return fail(c, MER_ERR_INVALID_ARG, "null argument");
+    size_t need = sizeof(uint64_t) * 2;
+    for (Problem* p : c->probs) need += sizeof(ProbState) + 9 * sizeof(float) * (size_t)p->n_par;
+    uint64_t hdr[2];
+    if (len < sizeof hdr) return fail(c, MER_ERR_INVALID_ARG, "checkpoint too short");
+    memcpy(hdr, buf, sizeof hdr);
+    if (hdr[0] != 0x4d4552434b505431ull || hdr[1] != c->probs.size() || len != need)
+        return fail(c, MER_ERR_INVALID_ARG, "checkpoint does not match this context's problems");
+    Guard g(c);
+    const char* r = (const char*)buf + sizeof hdr;
+    for (Problem* p : c->probs) {
+        CK(c, cudaMemcpyAsync(c->d_pstate + p->id, r, sizeof(ProbState), cudaMemcpyHostToDevice, c->st));
+        r += sizeof(ProbState);
+        float* arrs[9] = {p->pslot[0], p->pslot[1], p->F, p->dF, p->m2f, p->m2d, p->mean, p->var, p->ap};
+        for (float* a : arrs) {
+            CK(c, cudaMemcpyAsync(a, r, sizeof(float) * p->n_par, cudaMemcpyHostToDevice, c->st));
+            r += sizeof(float) * p->n_par;
+        }
+    }
+    CK(c, cudaStreamSynchronize(c->st));
+    return MER_OK;
+}
+
+mer_status mer_autotune(mer_ctx* c, int32_t trial_iters, char* desc, size_t desc_len) {
+    if (!c || c->probs.empty()) return fail(c, MER_ERR_STATE, "no problems");
+    if (trial_iters < 1) trial_iters = 1;
+    // candidates: block size x blocks per SM x shared-memory node staging
+    const int blocks[] = {64, 128, 256};   // <= the kernels' launch bounds
+    const int per_sm[] = {2, 4, 8, 16};
+    const int smem[] = {0, 256, 1024};
+    // every trial runs full iterations on a checkpoint of the state, restored afterwards
+    size_t len = 0;
+    mer_status s = mer_checkpoint_save(c, nullptr, &len);
+    if (s) return s;
+    std::vector<char> saved(len);
+    s = mer_checkpoint_save(c, saved.data(), &len);
+    if (s) return s;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    LaunchShape best_shape = c->shape;
+    int best_per_sm = c->cfg.blocks_per_sm;
+    const LaunchShape orig = c->shape;
+    const int orig_per_sm = c->cfg.blocks_per_sm;
+    for (int b : blocks)
+        for (int ps : per_sm)
+            for (int sm : smem) {
+                if (b * ps > 2048) continue;
+                if (sm > 0 && (set_trace_smem_limits(sm) != cudaSuccess)) continue;
+                c->shape.block = b;
+                c->shape.smem_nodes = sm;
+                c->cfg.blocks_per_sm = ps;
+                c->graph_dirty = true;
+                // warm-up (also captures the graph)
+                if (mer_iterate(c, 1, 1)) continue;
+                cudaEventRecord(e0, c->st);
+                mer_iterate(c, trial_iters, 1);
+                cudaEventRecord(e1, c->st);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (cudaGetLastError() == cudaSuccess && ms < best) {
+                    best = ms;
+                    best_shape = c->shape;
+                    best_per_sm = ps;
+                }
+                mer_checkpoint_load(c, saved.data(), saved.size());
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)orig;
+    (void)orig_per_sm;
+    c->shape = best_shape;
+    c->cfg.blocks_per_sm = best_per_sm;
+    c->graph_dirty = true;
+    if (desc && desc_len)
+        snprintf(desc, desc_len, "block=%d blocks_per_sm=%d smem_nodes=%d ms_per_iter=%.4f", best_shape.block,
+                 best_per_sm, best_shape.smem_nodes, best / trial_iters);
+    return mer_checkpoint_load(c, saved.data(), saved.size());
+}
+
+}  // extern "C"

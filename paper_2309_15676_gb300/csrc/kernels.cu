@@ -1,0 +1,160 @@
+// Gradient scatter (step a10), image loss and adjoint images (step a7), Philox fill.
+#include "kernels.cuh"
+#include "wavefront.cuh"
+
+namespace mer {
+
+constexpr unsigned FULLM = 0xffffffffu;
+
+// sum of v over the lanes of `peers` (lanes listed in vmask all call this); every lane gets
+// the sum over its own peer group, in a fixed lane order
+__device__ __forceinline__ float peer_sum(unsigned vmask, unsigned peers, float v, int maxg) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned others = peers & ~(1u << lane);
+    float acc = v;
+    for (int i = 1; i < maxg; ++i) {
+        const int src = others ? (__ffs(others) - 1) : (int)lane;
+        const float x = __shfl_sync(vmask, v, src);
+        if (others) {
+            acc += x;
+            others &= others - 1;
+        }
+    }
+    return acc;
+}
+
+// Each record {problem, texel footprint (x0, y0, fx, fy), g[C]} adds w_k g[c] to the four
+// bilinear taps (clamp-to-edge) of the problem's gradient texture. Lanes of a warp holding
+// the same footprint origin (same four taps) are merged with __match_any_sync and a
+// segmented shuffle sum, and only the group's first lane issues the atomics.
+__global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ rpos,
+                                                 const float* __restrict__ rf, int64_t rcap,
+                                                 const ProblemDev* __restrict__ probs, float* grad_over, int which) {
+    const int64_t n = min((int64_t)cnt[CNT_R], rcap);
+    const int64_t nw = (n + 31) & ~(int64_t)31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
+        const bool valid = i < n;
+        const unsigned vmask = __ballot_sync(FULLM, valid);
+        if (!valid) continue;
+        const uint32_t pos = __ldcs(rpos + i);
+        const int q = pos >> 24;
+        const ProblemDev& P = probs[q];
+        const int x0 = (int)(pos & 0xfff) - 1, y0 = (int)((pos >> 12) & 0xfff) - 1;
+        const float fx = __ldcs(rf + (size_t)RF_FX * rcap + i), fy = __ldcs(rf + (size_t)RF_FY * rcap + i);
+        const int C = P.tex_c, W = P.tex_w, H = P.tex_h;
+        float g[MAXC];
+#pragma unroll
+        for (int c = 0; c < MAXC; ++c) g[c] = (c < C) ? __ldcs(rf + (size_t)(RF_G + c) * rcap + i) : 0.0f;
+        const int xa = max(x0, 0), xb = min(x0 + 1, W - 1), ya = max(y0, 0), yb = min(y0 + 1, H - 1);
+        float* base = grad_over ? grad_over : (which ? P.dF : P.F);
+        float* tap[4] = {base + ((size_t)ya * W + xa) * C, base + ((size_t)ya * W + xb) * C,
+                         base + ((size_t)yb * W + xa) * C, base + ((size_t)yb * W + xb) * C};
+        const float w[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
+        const unsigned peers = __match_any_sync(vmask, pos);
+        const int gsize = __popc(peers);
+        const int maxg = (int)__reduce_max_sync(vmask, (unsigned)gsize);
+        if (maxg == 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int c = 0; c < MAXC; ++c)
+                    if (c < C) atomicAdd(tap[k] + c, w[k] * g[c]);
+        } else {
+            const bool leader = (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int c = 0; c < MAXC; ++c) {
+                    if (c >= C) continue;   // C is uniform across the group (same problem)
+                    const float s = peer_sum(vmask, peers, w[k] * g[c], maxg);
+                    if (leader) atomicAdd(tap[k] + c, s);
+                }
+        }
+    }
+}
+
+int run_scatter(const uint32_t* cnt, const uint32_t* rpos, const float* rf, int64_t rcap, const ProblemDev* probs,
+                float* grad_over, int which, int grid, cudaStream_t st) {
+    k_scatter<<<grid, 256, 0, st>>>(cnt, rpos, rf, rcap, probs, grad_over, which);
+    return 1;
+}
+
+// L2 loss L = 1/(3N) sum (I - T)^2 and its adjoint image dL/dI = 2 (I - T) / (3N), for the
+// proportional image (loss accumulated per problem in FP64) and, with_fd, the two images of the
+// FD pair. Pixels of all problems are enumerated through the prefix pix_pref.
+__global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs, const int64_t* __restrict__ pix_pref,
+                                            int n_probs, int64_t total_pix, int with_fd, double* loss_acc) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nw = (total_pix + 31) & ~(int64_t)31;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nw; p += stride) {
+        const bool valid = p < total_pix;
+        int q = -1;
+        double l = 0.0;
+        if (valid) {
+            q = find_entry(pix_pref, n_probs, p);
+            const ProblemDev& P = probs[q];
+            const int64_t lp = p - pix_pref[q];
+            const float sc = 2.0f / (3.0f * (float)P.n_pix);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int64_t k = lp * 3 + c;
+                const float t = P.target[k];
+                const float r = P.img[k] - t;
+                P.dimg[k] = sc * r;
+                l += (double)r * (double)r;
+                if (with_fd && P.imgA) {
+                    P.dimgA[k] = sc * (P.imgA[k] - t);
+                    P.dimgB[k] = sc * (P.imgB[k] - t);
+                }
+            }
+        }
+        // warp reduce when the whole warp belongs to one problem, else per lane
+        const int q0 = __shfl_sync(FULLM, q, 0);
+        const bool same = __all_sync(FULLM, q == q0);
+        if (same) {
+            for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(FULLM, l, o);
+            if ((threadIdx.x & 31) == 0 && q0 >= 0) atomicAdd(loss_acc + q0, l);
+        } else if (valid) {
+            atomicAdd(loss_acc + q, l);
+        }
+    }
+}
+
+int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int with_fd,
+           double* loss_acc, int grid, cudaStream_t st) {
+    k_l2<<<grid, 256, 0, st>>>(probs, pix_pref, n_probs, total_pix, with_fd, loss_acc);
+    return 1;
+}
+
+__global__ void k_philox(uint32_t k0, uint32_t k1, const uint4* __restrict__ ctr, int64_t n, uint4* out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+int run_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int64_t n, uint32_t* out, cudaStream_t st) {
+    if (n <= 0) return 0;
+    const int64_t blocks = (n + 255) / 256;
+    k_philox<<<(unsigned)(blocks < 65535 ? blocks : 65535), 256, 0, st>>>(k0, k1, reinterpret_cast<const uint4*>(ctr), n,
+                                                                        reinterpret_cast<uint4*>(out));
+    return 1;
+}
+
+}  // namespace mer
+
+namespace mer {
+
+__global__ void k_fill(float* p, int64_t n, float v) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
+}
+
+int run_fill(float* p, int64_t n, float v, cudaStream_t st) {
+    if (n <= 0) return 0;
+    const int64_t blocks = (n + 255) / 256;
+    k_fill<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(p, n, v);
+    return 1;
+}
+
+}  // namespace mer

@@ -1,0 +1,33 @@
+// Launchers of the scatter, loss and Philox kernels, and of the wavefront passes.
+#pragma once
+
+#include "mer_internal.cuh"
+
+namespace mer {
+
+struct PassArgs;
+struct LaunchShape {
+    int block;        // threads per block of the wavefront kernels (<= 256)
+    int per_sm;       // cap on resident blocks per SM of the persistent grids (0 = occupancy)
+    int smem_nodes;   // BVH nodes staged in shared memory
+    int sms;          // multiprocessors of the device
+};
+
+int run_pass(const PassArgs& A, int nb, int mode, int max_depth, const LaunchShape& L, cudaStream_t st);
+int run_resolve(const PassArgs& A, int nb, float* img0, float* img1, int accumulate, int grid, cudaStream_t st);
+int run_samples_out(const PassArgs& A, float* out, int grid, cudaStream_t st);
+cudaError_t set_trace_smem_limits(int max_nodes);
+
+// grad_over != nullptr: single-problem output; else each record's problem's F (which = 0) or dF (which = 1)
+int run_scatter(const uint32_t* cnt, const uint32_t* rpos, const float* rf, int64_t rcap, const ProblemDev* probs,
+                float* grad_over, int which, int grid, cudaStream_t st);
+// per-problem L2 loss and adjoint images of all problems (pix_pref: prefix of n_pix over problems)
+int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int with_fd,
+           double* loss_acc, int grid, cudaStream_t st);
+int run_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int64_t n, uint32_t* out, cudaStream_t st);
+
+}  // namespace mer
+
+namespace mer {
+int run_fill(float* p, int64_t n, float v, cudaStream_t st);
+}  // namespace mer

@@ -1,0 +1,903 @@
+// Wavefront path tracer, path-replay adjoint and finite-difference pairs (sm_103a).
+//
+// One pass = for depth k = 1..D: extend (closest hit of every queued ray) -> shade
+// (emission, next-event estimation, BSDF sampling, gradient records, compaction of the
+// surviving paths into the next queue) -> shadow (any-hit of the NEE rays; adds the
+// visible NEE radiance and the NEE part of the gradient record). Queues are SoA and the
+// compacting appends are warp-aggregated (one atomic per warp).
+//
+// Passes (Sec. 6 setup: Path Replay Backpropagation; Sec. 3 Eqs. est_def, est_triv):
+//   PRIMAL  - radiance per path, resolved into images;
+//   ADJ_FWD - radiance per path L_total, kept for the replay;
+//   REPLAY  - the same paths again (same counters); at vertex k the texture derivative
+//             g_k = adj . [ T_k dF(w_l) Le G w_l / p_l  +  (L_total - L_<=k) dF(w_b) / F(w_b) ]
+//             is written as a record {texel footprint, g[C]}; sampling pdfs and MIS weights
+//             are treated as constants. Written in two parts so that no path state needs to
+//             outlive the kernel: the shade kernel stores adj . (L_total - L_acc) dF(w_b)/F(w_b)
+//             with L_acc the radiance before this vertex's NEE, and the NEE shadow ray carries
+//             adj . (dN - N dF(w_b)/F(w_b)), added only if the light is visible.
+// NB = 2 runs the FD pair of Eq. est_triv: branch A at pi_i, branch B at pi_{i-1}, same
+// random numbers, one thread. While both branches follow the same ray ("coincident") they
+// share traversal, surface interaction, light sample and shadow ray, and their gradient
+// records merge into one record of g_A - g_B.
+#include "kernels.cuh"
+#include "wavefront.cuh"
+
+namespace mer {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------------
+// traversal
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ Node load_node(const Node* __restrict__ nodes, const Node* s_nodes, int smem_n, int i) {
+    if (i < smem_n) return s_nodes[i];
+    const float4* p = reinterpret_cast<const float4*>(nodes + i);
+    Node n;
+    n.a = __ldg(p);
+    n.b = __ldg(p + 1);
+    n.c = __ldg(p + 2);
+    const int4 d = __ldg(reinterpret_cast<const int4*>(p + 3));
+    n.d = d;
+    return n;
+}
+
+__device__ __forceinline__ bool tri_test(const TriGeo& T, v3 o, v3 d, float& t, float& u, float& v) {
+    const v3 e1 = mk(T.e1.x, T.e1.y, T.e1.z), e2 = mk(T.e2.x, T.e2.y, T.e2.z);
+    const v3 pv = cross(d, e2);
+    const float det = dot(e1, pv);
+    if (det == 0.0f) return false;
+    const float inv = 1.0f / det;
+    const v3 tv = o - mk(T.v0.x, T.v0.y, T.v0.z);
+    u = dot(tv, pv) * inv;
+    if (u < 0.0f || u > 1.0f) return false;
+    const v3 qv = cross(tv, e1);
+    v = dot(d, qv) * inv;
+    if (v < 0.0f || u + v > 1.0f) return false;
+    t = dot(e2, qv) * inv;
+    return t > 0.0f;
+}
+
+__device__ __forceinline__ TriGeo load_tri(const TriGeo* __restrict__ tris, int i) {
+    const float4* p = reinterpret_cast<const float4*>(tris + i);
+    TriGeo T;
+    T.v0 = __ldg(p);
+    T.e1 = __ldg(p + 1);
+    T.e2 = __ldg(p + 2);
+    return T;
+}
+
+// robust ray/sphere (Haines et al. 2019, Ray Tracing Gems ch. 7): nearest t > 0
+__device__ __forceinline__ bool sphere_test(const Sphere& S, v3 o, v3 d, float& t) {
+    const v3 c = mk(S.cr.x, S.cr.y, S.cr.z);
+    const float r = S.cr.w;
+    const v3 oc = o - c;
+    const float b = dot(oc, d);
+    const v3 f = oc - d * b;
+    const float disc = r * r - dot(f, f);
+    if (disc < 0.0f) return false;
+    const float cc = dot(oc, oc) - r * r;
+    const float q = -(b + copysignf(sqrtf(disc), b));
+    if (q == 0.0f) return false;
+    float t0 = cc / q, t1 = q;
+    if (t0 > t1) { const float s = t0; t0 = t1; t1 = s; }
+    if (t0 > 0.0f) { t = t0; return true; }
+    if (t1 > 0.0f) { t = t1; return true; }
+    return false;
+}
+
+struct Hit {
+    float t, b1, b2;
+    int prim;   // local: triangles [0, n_tris), spheres n_tris + i; -1 = miss
+};
+
+// closest hit (ANY = false) or any hit before tmax (ANY = true). Ties in t go to the
+// smaller primitive id, independent of traversal order.
+template <bool ANY>
+__device__ __forceinline__ bool traverse(const ProblemDev& P, const Node* s_nodes, int smem_n, v3 o, v3 d,
+                                         float tmax, Hit& h) {
+    h.t = tmax;
+    h.prim = -1;
+    h.b1 = h.b2 = 0.0f;
+    int best = 0x7fffffff;
+    if (P.nodes) {
+        const float dx = fabsf(d.x) < 1e-20f ? copysignf(1e-20f, d.x) : d.x;
+        const float dy = fabsf(d.y) < 1e-20f ? copysignf(1e-20f, d.y) : d.y;
+        const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
+        const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
+        const float ox = o.x * ix, oy = o.y * iy, oz = o.z * iz;
+        int stack[64];
+        int sp = 0;
+        int node = 0;
+        const float grow = 1.0f + 4.8e-7f;   // conservative box exit (a few ulp)
+        while (true) {
+            while (node >= 0) {
+                const Node n = load_node(P.nodes, s_nodes, smem_n, node);
+                const float tfar = h.t * grow;
+                const float l0x = fmaf(n.a.x, ix, -ox), l1x = fmaf(n.a.y, ix, -ox);
+                const float l0y = fmaf(n.a.z, iy, -oy), l1y = fmaf(n.a.w, iy, -oy);
+                const float l0z = fmaf(n.c.x, iz, -oz), l1z = fmaf(n.c.y, iz, -oz);
+                const float r0x = fmaf(n.b.x, ix, -ox), r1x = fmaf(n.b.y, ix, -ox);
+                const float r0y = fmaf(n.b.z, iy, -oy), r1y = fmaf(n.b.w, iy, -oy);
+                const float r0z = fmaf(n.c.z, iz, -oz), r1z = fmaf(n.c.w, iz, -oz);
+                const float lmin = fmaxf(fmaxf(fminf(l0x, l1x), fminf(l0y, l1y)), fmaxf(fminf(l0z, l1z), 0.0f));
+                const float lmax = fminf(fminf(fmaxf(l0x, l1x), fmaxf(l0y, l1y)), fminf(fmaxf(l0z, l1z), tfar));
+                const float rmin = fmaxf(fmaxf(fminf(r0x, r1x), fminf(r0y, r1y)), fmaxf(fminf(r0z, r1z), 0.0f));
+                const float rmax = fminf(fminf(fmaxf(r0x, r1x), fmaxf(r0y, r1y)), fminf(fmaxf(r0z, r1z), tfar));
+                const bool hl = lmin <= lmax, hr = rmin <= rmax;
+                if (hl && hr) {
+                    int nearc = n.d.x, farc = n.d.y;
+                    if (rmin < lmin) { nearc = n.d.y; farc = n.d.x; }
+                    if (sp < 64) stack[sp++] = farc;
+                    node = nearc;
+                } else if (hl) {
+                    node = n.d.x;
+                } else if (hr) {
+                    node = n.d.y;
+                } else {
+                    if (sp == 0) { node = 0x7fffffff; break; }
+                    node = stack[--sp];
+                }
+            }
+            if (node == 0x7fffffff) break;
+            // leaf
+            const int x = ~node;
+            const int first = x >> 3, count = (x & 7) + 1;
+            for (int k = 0; k < count; ++k) {
+                const TriGeo T = load_tri(P.tris, first + k);
+                float t, u, v;
+                if (tri_test(T, o, d, t, u, v)) {
+                    const int pid = __float_as_int(T.v0.w);
+                    if (ANY) {
+                        if (t < tmax) { h.prim = pid; h.t = t; return true; }
+                    } else if (t < h.t || (t == h.t && pid < best)) {
+                        h.t = t; h.b1 = u; h.b2 = v; best = pid;
+                    }
+                }
+            }
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    if (!ANY) h.prim = (best == 0x7fffffff) ? -1 : best;
+    for (int i = 0; i < P.n_sph; ++i) {
+        const Sphere S = P.sph[i];
+        float t;
+        if (sphere_test(S, o, d, t)) {
+            if (ANY) {
+                if (t < tmax) { h.prim = P.n_tris + i; return true; }
+            } else if (t < h.t) {
+                h.t = t; h.prim = P.n_tris + i; h.b1 = h.b2 = 0.0f;
+            }
+        }
+    }
+    return h.prim >= 0;
+}
+
+// ---------------------------------------------------------------------------------
+// shading helpers
+// ---------------------------------------------------------------------------------
+struct Surf {
+    v3 p, n;
+    float u, v;
+    int mat, light;
+};
+
+__device__ __forceinline__ void surface(const ProblemDev& P, v3 o, v3 d, const Hit& h, Surf& s) {
+    s.p = o + d * h.t;
+    if (h.prim < P.n_tris) {
+        const TriAttr at = P.attr[h.prim];
+        s.n = mk(at.n[0], at.n[1], at.n[2]);
+        const float w = 1.0f - h.b1 - h.b2;
+        s.u = w * at.uv[0] + h.b1 * at.uv[2] + h.b2 * at.uv[4];
+        s.v = w * at.uv[1] + h.b1 * at.uv[3] + h.b2 * at.uv[5];
+        s.mat = at.mat;
+        s.light = at.light;
+    } else {
+        const Sphere S = P.sph[h.prim - P.n_tris];
+        s.n = (s.p - mk(S.cr.x, S.cr.y, S.cr.z)) * (1.0f / S.cr.w);
+        float uu = atan2f(s.n.y, s.n.x) * (0.5f * INV_PI_F);
+        if (uu < 0.0f) uu += 1.0f;
+        const float vv = acosf(fminf(1.0f, fmaxf(-1.0f, s.n.z))) * INV_PI_F;
+        s.u = S.uvr.x + uu * (S.uvr.y - S.uvr.x);
+        s.v = S.uvr.z + vv * (S.uvr.w - S.uvr.z);
+        s.mat = S.mat;
+        s.light = -1;
+    }
+}
+
+struct Foot {
+    int x0, y0;
+    float fx, fy;
+};
+
+// bilinear, clamp-to-edge, texel centres at (x + 1/2) / W
+__device__ __forceinline__ void fetch(const float* __restrict__ tex, const ProblemDev& P, float u, float v,
+                                      MatEval& m, Foot& f) {
+    u = fminf(fmaxf(u, 0.0f), 1.0f);
+    v = fminf(fmaxf(v, 0.0f), 1.0f);
+    const int W = P.tex_w, H = P.tex_h, C = P.tex_c;
+    const float x = u * (float)W - 0.5f, y = v * (float)H - 0.5f;
+    const float xf = floorf(x), yf = floorf(y);
+    f.x0 = (int)xf;
+    f.y0 = (int)yf;
+    f.fx = x - xf;
+    f.fy = y - yf;
+    const int xa = max(f.x0, 0), xb = min(f.x0 + 1, W - 1);
+    const int ya = max(f.y0, 0), yb = min(f.y0 + 1, H - 1);
+    const float w00 = (1.0f - f.fx) * (1.0f - f.fy), w10 = f.fx * (1.0f - f.fy);
+    const float w01 = (1.0f - f.fx) * f.fy, w11 = f.fx * f.fy;
+    const float* t00 = tex + ((size_t)ya * W + xa) * C;
+    const float* t10 = tex + ((size_t)ya * W + xb) * C;
+    const float* t01 = tex + ((size_t)yb * W + xa) * C;
+    const float* t11 = tex + ((size_t)yb * W + xb) * C;
+#pragma unroll
+    for (int j = 0; j < MAXC; ++j) {
+        if (j < C)
+            m.th[j] = w00 * __ldg(t00 + j) + w10 * __ldg(t10 + j) + w01 * __ldg(t01 + j) + w11 * __ldg(t11 + j);
+        else
+            m.th[j] = 0.0f;
+    }
+}
+
+struct LightSample {
+    bool ok;
+    v3 wi, le;
+    float pdf, tmax;
+};
+
+// uniform choice among {quads..., env}; quads by area, env by a cosine lobe around nf
+__device__ __forceinline__ LightSample sample_light(const ProblemDev& P, v3 po, v3 nf, uint4 r) {
+    LightSample L;
+    L.ok = false;
+    const int nL = P.n_lights;
+    if (nL == 0) return L;
+    const int l = (int)(((uint64_t)(r.x >> 8) * (uint64_t)nL) >> 24);
+    const float u1 = u01(r.y), u2 = u01(r.z);
+    if (l < P.n_quads) {
+        const QuadLight Q = P.quads[l];
+        const v3 y = mk(Q.p0[0], Q.p0[1], Q.p0[2]) + mk(Q.e1[0], Q.e1[1], Q.e1[2]) * u1 +
+                     mk(Q.e2[0], Q.e2[1], Q.e2[2]) * u2;
+        const v3 w = y - po;
+        const float d2 = dot(w, w), dist = sqrtf(d2);
+        const v3 wi = w * (1.0f / dist);
+        const float cl = -dot(wi, mk(Q.n[0], Q.n[1], Q.n[2]));
+        if (cl <= 0.0f || dot(wi, nf) <= 0.0f) return L;
+        L.ok = true;
+        L.wi = wi;
+        L.pdf = d2 / (Q.area * cl * (float)nL);
+        L.tmax = dist * (1.0f - 1e-4f);
+        L.le = mk(Q.le[0], Q.le[1], Q.le[2]);
+    } else {
+        const v3 wi = cosine_dir(nf, u1, u2);
+        const float cs = dot(wi, nf);
+        if (cs <= 0.0f) return L;
+        L.ok = true;
+        L.wi = wi;
+        L.pdf = cs * INV_PI_F / (float)nL;
+        L.tmax = INFINITY;
+        L.le = mk(P.env[0], P.env[1], P.env[2]);
+    }
+    return L;
+}
+
+__device__ __forceinline__ void camera_ray(const ProblemDev& P, uint32_t pixel, float j0, float j1, v3& o, v3& d) {
+    const uint32_t px = pixel % (uint32_t)P.width, py = pixel / (uint32_t)P.width;
+    const float sx = 2.0f * ((float)px + j0) / (float)P.width - 1.0f;
+    const float sy = 1.0f - 2.0f * ((float)py + j1) / (float)P.height;
+    o = mk(P.cam_o[0], P.cam_o[1], P.cam_o[2]);
+    d = normalize(mk(P.cam_f[0], P.cam_f[1], P.cam_f[2]) + mk(P.cam_r[0], P.cam_r[1], P.cam_r[2]) * sx +
+                  mk(P.cam_u[0], P.cam_u[1], P.cam_u[2]) * sy);
+}
+
+struct PathId {
+    int q, e;
+    uint32_t pixel, sample, iter;
+    int spp;
+};
+
+__device__ __forceinline__ PathId decode_path(const PassArgs& A, int64_t g) {
+    PathId id;
+    int64_t local = g;
+    if (A.inl_prob >= 0) {
+        id.e = 0;
+        id.q = A.inl_prob;
+    } else {
+        id.e = find_entry(A.path_off, A.n_entries, g);
+        id.q = A.entry_prob[id.e];
+        local = g - A.path_off[id.e];
+    }
+    const ProblemDev& P = A.probs[id.q];
+    id.pixel = (uint32_t)(local % P.n_pix);
+    id.sample = (uint32_t)(local / P.n_pix) + (uint32_t)A.sample_base;
+    id.iter = A.iter_override >= 0 ? (uint32_t)A.iter_override : (uint32_t)A.pstate[id.q].iteration;
+    id.spp = A.spp_override > 0 ? A.spp_override : (A.fd_kind ? P.spp_fd : P.spp_prop);
+    return id;
+}
+
+__device__ __forceinline__ const float* branch_tex(const PassArgs& A, const ProblemDev& P, int q, int b) {
+    if (A.tex_over[b]) return A.tex_over[b];
+    const int cur = A.pstate[q].cur;
+    return P.pslot[b == 0 ? cur : (cur ^ 1)];
+}
+
+// warp-aggregated append: returns this lane's first slot; all 32 lanes must call
+__device__ __forceinline__ uint32_t warp_append(uint32_t* ctr, uint32_t cnt) {
+    const unsigned lane = threadIdx.x & 31u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= (unsigned)o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    uint32_t base = 0;
+    if (lane == 31 && total) base = atomicAdd(ctr, total);
+    base = __shfl_sync(FULL, base, 31);
+    return base + incl - cnt;
+}
+
+__device__ __forceinline__ void set_err(const PassArgs& A, int code) { atomicCAS(&A.cnt[CNT_ERR], 0u, (uint32_t)code); }
+
+extern __shared__ float4 s_dyn[];
+
+// stages the first nodes of problem smem_prob's BVH (its top levels) in shared memory;
+// returns how many were staged
+__device__ __forceinline__ int stage_nodes(const PassArgs& A, const Node*& s_nodes) {
+    Node* s = reinterpret_cast<Node*>(s_dyn);
+    s_nodes = s;
+    int cnt = 0;
+    if (A.smem_nodes > 0) {
+        const ProblemDev& P = A.probs[A.smem_prob];
+        cnt = P.nodes ? min(A.smem_nodes, P.n_nodes) : 0;
+        const float4* src = reinterpret_cast<const float4*>(P.nodes);
+        float4* dst = reinterpret_cast<float4*>(s);
+        for (int i = threadIdx.x; i < cnt * 4; i += blockDim.x) dst[i] = __ldg(src + i);
+        __syncthreads();
+    }
+    return cnt;
+}
+
+// ---------------------------------------------------------------------------------
+// extend: closest hit of every queued ray (shared once per coincident pair)
+// ---------------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(256) k_extend(PassArgs A, int depth) {
+    const Node* s_nodes;
+    const int n_staged = stage_nodes(A, s_nodes);
+    const bool first = depth == 1;
+    const int64_t n = first ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth], A.qcap);
+    const int qi = depth & 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        uint32_t flags;
+        int q;
+        v3 o[NB], d[NB];
+        if (first) {
+            const PathId id = decode_path(A, j);
+            q = id.q;
+            const ProblemDev& P = A.probs[q];
+            flags = (NB == 2) ? (FLAG_A | FLAG_B | FLAG_COINC) : FLAG_A;
+            if (A.fd_kind && A.iter_override < 0 && A.pstate[q].iteration == 0) flags = 0;
+            const uint4 r = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, 0, 0);
+            camera_ray(P, id.pixel, u01(r.x), u01(r.y), o[0], d[0]);
+            if (NB == 2) { o[NB - 1] = o[0]; d[NB - 1] = d[0]; }
+        } else {
+            flags = A.qu[qi][QU_FLAGS * A.qcap + j];
+            q = (flags >> 8) & 0xff;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const float* f = A.qf[qi] + (size_t)(b * QF_PER_BRANCH) * A.qcap + j;
+                o[b] = mk(f[(QF_O + 0) * A.qcap], f[(QF_O + 1) * A.qcap], f[(QF_O + 2) * A.qcap]);
+                d[b] = mk(f[(QF_D + 0) * A.qcap], f[(QF_D + 1) * A.qcap], f[(QF_D + 2) * A.qcap]);
+            }
+        }
+        const ProblemDev& P = A.probs[q];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (!(flags & (1u << b))) continue;
+            if (b == 1 && (flags & FLAG_COINC)) continue;
+            Hit h;
+            traverse<false>(P, s_nodes, q == A.smem_prob ? n_staged : 0, o[b], d[b], INFINITY, h);
+            A.hitf[(size_t)(b * HF_PER_BRANCH + HF_T) * A.qcap + j] = h.t;
+            A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B1) * A.qcap + j] = h.b1;
+            A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B2) * A.qcap + j] = h.b2;
+            A.hitp[(size_t)b * A.qcap + j] = h.prim;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// shade
+// ---------------------------------------------------------------------------------
+template <int NB, int MODE>
+__global__ void __launch_bounds__(256) k_shade(PassArgs A, int depth) {
+    constexpr bool GRAD = MODE == MODE_REPLAY;
+    const bool first = depth == 1;
+    const int64_t n = first ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth], A.qcap);
+    const int64_t nw = (n + 31) & ~(int64_t)31;
+    const int qi = depth & 1, qo = qi ^ 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nw; j += stride) {
+        const bool valid = j < n;
+        uint32_t flags = 0;
+        int64_t g = 0;
+        PathId id{};
+        v3 o[NB], d[NB], beta[NB];
+        float pdfb[NB], pdfenv[NB];
+        if (valid) {
+            if (first) {
+                g = j;
+                id = decode_path(A, g);
+                flags = (NB == 2) ? (FLAG_A | FLAG_B | FLAG_COINC) : FLAG_A;
+                if (A.fd_kind && A.iter_override < 0 && A.pstate[id.q].iteration == 0) flags = 0;
+                const ProblemDev& P = A.probs[id.q];
+                const uint4 r = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, 0, 0);
+                v3 oc, dc;
+                camera_ray(P, id.pixel, u01(r.x), u01(r.y), oc, dc);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    o[b] = oc; d[b] = dc; beta[b] = mk(1, 1, 1); pdfb[b] = 0.0f; pdfenv[b] = 0.0f;
+                }
+            } else {
+                g = A.qu[qi][QU_PATH * A.qcap + j];
+                flags = A.qu[qi][QU_FLAGS * A.qcap + j];
+                id = decode_path(A, g);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const float* f = A.qf[qi] + (size_t)(b * QF_PER_BRANCH) * A.qcap + j;
+                    o[b] = mk(f[(QF_O + 0) * A.qcap], f[(QF_O + 1) * A.qcap], f[(QF_O + 2) * A.qcap]);
+                    d[b] = mk(f[(QF_D + 0) * A.qcap], f[(QF_D + 1) * A.qcap], f[(QF_D + 2) * A.qcap]);
+                    beta[b] = mk(f[(QF_BETA + 0) * A.qcap], f[(QF_BETA + 1) * A.qcap], f[(QF_BETA + 2) * A.qcap]);
+                    pdfb[b] = f[QF_PDFB * A.qcap];
+                    pdfenv[b] = f[QF_PDFENV * A.qcap];
+                }
+            }
+        }
+        const int q = id.q;
+        const ProblemDev& P = A.probs[q];
+        const bool coinc = (NB == 2) && (flags & FLAG_COINC);
+
+        // ---- emission / termination ----
+        bool alive[NB];
+        Surf s[NB];
+        v3 lacc[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            alive[b] = valid && (flags & (1u << b));
+            lacc[b] = mk(0, 0, 0);
+            if (!alive[b]) continue;
+            if (!first) {
+                lacc[b] = mk(A.lacc[(size_t)(b * 3 + 0) * A.qcap + g], A.lacc[(size_t)(b * 3 + 1) * A.qcap + g],
+                             A.lacc[(size_t)(b * 3 + 2) * A.qcap + g]);
+            }
+            const int hb = (b == 1 && coinc) ? 0 : b;
+            Hit h;
+            h.t = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_T) * A.qcap + j];
+            h.b1 = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_B1) * A.qcap + j];
+            h.b2 = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_B2) * A.qcap + j];
+            h.prim = A.hitp[(size_t)hb * A.qcap + j];
+            if (h.prim < 0) {
+                if (P.has_env) {
+                    const float w = first ? 1.0f : mis2(pdfb[b], pdfenv[b]);
+                    lacc[b] = lacc[b] + mk(beta[b].x * P.env[0], beta[b].y * P.env[1], beta[b].z * P.env[2]) * w;
+                }
+                alive[b] = false;
+                continue;
+            }
+            if (b == 1 && coinc) s[1] = s[0]; else surface(P, o[b], d[b], h, s[b]);
+            if (s[b].light >= 0) {
+                const QuadLight& Q = P.quads[s[b].light];
+                const float cl = -dot(d[b], mk(Q.n[0], Q.n[1], Q.n[2]));
+                if (cl > 0.0f) {
+                    float w = 1.0f;
+                    if (!first) {
+                        const float pl = h.t * h.t / (Q.area * cl * (float)P.n_lights);
+                        w = mis2(pdfb[b], pl);
+                    }
+                    lacc[b] = lacc[b] + mk(beta[b].x * Q.le[0], beta[b].y * Q.le[1], beta[b].z * Q.le[2]) * w;
+                }
+            }
+            if (depth >= P.max_depth) alive[b] = false;
+        }
+        // write back the radiance accumulated so far (NEE of this vertex is added by the shadow kernel)
+        if (valid) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (first || (flags & (1u << b))) {
+                    A.lacc[(size_t)(b * 3 + 0) * A.qcap + g] = lacc[b].x;
+                    A.lacc[(size_t)(b * 3 + 1) * A.qcap + g] = lacc[b].y;
+                    A.lacc[(size_t)(b * 3 + 2) * A.qcap + g] = lacc[b].z;
+                }
+            }
+        }
+
+        // ---- vertex: NEE + BSDF sample (+ gradient terms) ----
+        bool any_alive = false;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) any_alive |= alive[b];
+
+        bool sh_want[NB], cont[NB], rec_want[NB], textured[NB];
+        LightSample ls[NB];
+        v3 contrib[NB], wi_b[NB];
+        float gbase[NB][MAXC], gnee[NB][MAXC];
+        Foot foot[NB];
+        v3 po[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            sh_want[b] = cont[b] = rec_want[b] = textured[b] = false;
+            ls[b].ok = false;
+        }
+        if (any_alive) {
+            const uint4 r0 = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, (uint32_t)depth, 0);
+            const uint4 r1 = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, (uint32_t)depth, 1);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (!alive[b]) continue;
+                const v3 wo = -d[b];
+                const v3 nf = dot(s[b].n, d[b]) < 0.0f ? s[b].n : -s[b].n;
+                po[b] = offset_origin(s[b].p, nf);
+                const Material M = P.mats[s[b].mat];
+                MatEval m;
+                m.type = M.type;
+                textured[b] = M.textured != 0;
+                if (textured[b]) {
+                    fetch(branch_tex(A, P, q, b), P, s[b].u, s[b].v, m, foot[b]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < MAXC; ++k) m.th[k] = M.c[k];
+                }
+                const bool wg = GRAD && textured[b];
+                v3 adj = mk(0, 0, 0);
+                if (wg) {
+                    const float* dsrc = A.dimg_over[b] ? A.dimg_over[b] : (A.fd_kind ? (b ? P.dimgB : P.dimgA) : P.dimg);
+                    const float* di = dsrc + (size_t)id.pixel * 3;
+                    const float inv = 1.0f / (float)id.spp;
+                    adj = mk(di[0] * inv, di[1] * inv, di[2] * inv);
+                }
+                // next-event estimation
+                if (b == 1 && coinc) ls[1] = ls[0]; else ls[b] = sample_light(P, po[b], nf, r0);
+                float dN[MAXC];
+#pragma unroll
+                for (int k = 0; k < MAXC; ++k) dN[k] = 0.0f;
+                contrib[b] = mk(0, 0, 0);
+                if (ls[b].ok) {
+                    float df[MAXC][3];
+                    const v3 f = wg ? bsdf_f_grad(m, nf, wo, ls[b].wi, df) : bsdf_f(m, nf, wo, ls[b].wi);
+                    const float pb = bsdf_pdf(m, nf, wo, ls[b].wi);
+                    const float qn = dot(ls[b].wi, nf) * mis2(ls[b].pdf, pb) / ls[b].pdf;
+                    contrib[b] = mk(beta[b].x * f.x * ls[b].le.x, beta[b].y * f.y * ls[b].le.y,
+                                    beta[b].z * f.z * ls[b].le.z) * qn;
+                    if (wg) {
+                        const v3 k3 = mk(adj.x * beta[b].x * ls[b].le.x, adj.y * beta[b].y * ls[b].le.y,
+                                         adj.z * beta[b].z * ls[b].le.z) * qn;
+#pragma unroll
+                        for (int k = 0; k < MAXC; ++k) dN[k] = k3.x * df[k][0] + k3.y * df[k][1] + k3.z * df[k][2];
+                    }
+                    sh_want[b] = wg || contrib[b].x != 0.0f || contrib[b].y != 0.0f || contrib[b].z != 0.0f;
+                }
+                // BSDF sample for the continuation
+                v3 wi;
+                bool ok = bsdf_sample(m, nf, wo, u01(r1.x), u01(r1.y), u01(r1.z), wi);
+                float df[MAXC][3];
+                v3 f = mk(0, 0, 0);
+                float pb = 0.0f;
+                if (ok) {
+                    f = wg ? bsdf_f_grad(m, nf, wo, wi, df) : bsdf_f(m, nf, wo, wi);
+                    pb = bsdf_pdf(m, nf, wo, wi);
+                    ok = pb > 0.0f;
+                }
+                if (wg) {
+                    rec_want[b] = true;
+                    // ratio dF/F per channel of the continuation (0 where F = 0)
+                    v3 lrem = mk(0, 0, 0), nsub = mk(0, 0, 0);
+                    if (ok) {
+                        const float* lt = A.ltot;
+                        const v3 L = mk(lt[(size_t)(b * 3 + 0) * A.qcap + g], lt[(size_t)(b * 3 + 1) * A.qcap + g],
+                                        lt[(size_t)(b * 3 + 2) * A.qcap + g]);
+                        const v3 ir = mk(f.x != 0.0f ? 1.0f / f.x : 0.0f, f.y != 0.0f ? 1.0f / f.y : 0.0f,
+                                         f.z != 0.0f ? 1.0f / f.z : 0.0f);
+                        lrem = mk(adj.x * (L.x - lacc[b].x) * ir.x, adj.y * (L.y - lacc[b].y) * ir.y,
+                                  adj.z * (L.z - lacc[b].z) * ir.z);
+                        nsub = mk(adj.x * contrib[b].x * ir.x, adj.y * contrib[b].y * ir.y, adj.z * contrib[b].z * ir.z);
+                    }
+#pragma unroll
+                    for (int k = 0; k < MAXC; ++k) {
+                        gbase[b][k] = ok ? (lrem.x * df[k][0] + lrem.y * df[k][1] + lrem.z * df[k][2]) : 0.0f;
+                        gnee[b][k] = dN[k] - (ok ? (nsub.x * df[k][0] + nsub.y * df[k][1] + nsub.z * df[k][2]) : 0.0f);
+                    }
+                }
+                if (ok) {
+                    const float cs = dot(wi, nf);
+                    const float sc = cs / pb;
+                    beta[b] = mk(beta[b].x * f.x * sc, beta[b].y * f.y * sc, beta[b].z * f.z * sc);
+                    pdfb[b] = pb;
+                    pdfenv[b] = P.has_env ? cs * INV_PI_F / (float)P.n_lights : 0.0f;
+                    wi_b[b] = wi;
+                    cont[b] = true;
+                }
+            }
+        }
+
+        // ---- records (REPLAY) ----
+        const bool merged = coinc && rec_want[0] && (NB == 2 && rec_want[NB - 1]);
+        uint32_t rec_idx[NB];
+        if (GRAD) {
+            uint32_t nrec = 0;
+            if (merged) nrec = 1;
+            else {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) nrec += rec_want[b] ? 1u : 0u;
+            }
+            const uint32_t base = warp_append(&A.cnt[CNT_R], nrec);
+            uint32_t k = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                rec_idx[b] = 0xffffffffu;
+                if (!rec_want[b]) continue;
+                if (merged && b == 1) { rec_idx[1] = rec_idx[0]; continue; }
+                rec_idx[b] = base + k++;
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (!rec_want[b] || (merged && b == 1)) continue;
+                const uint32_t r = rec_idx[b];
+                if (r >= A.rcap) { set_err(A, MER_ERR_BOUNDS); rec_idx[b] = 0xffffffffu; continue; }
+                const float sg = (b == 1) ? -1.0f : 1.0f;
+                A.rpos[r] = ((uint32_t)q << 24) | ((uint32_t)(foot[b].y0 + 1) << 12) | (uint32_t)(foot[b].x0 + 1);
+                A.rf[(size_t)RF_FX * A.rcap + r] = foot[b].fx;
+                A.rf[(size_t)RF_FY * A.rcap + r] = foot[b].fy;
+#pragma unroll
+                for (int k2 = 0; k2 < MAXC; ++k2) {
+                    float v = sg * gbase[b][k2];
+                    if (merged) v = gbase[0][k2] - gbase[NB - 1][k2];
+                    A.rf[(size_t)(RF_G + k2) * A.rcap + r] = v;
+                }
+            }
+            if (merged) rec_idx[NB - 1] = rec_idx[0];
+        }
+
+        // ---- shadow rays ----
+        {
+            const bool sh_shared = coinc && ls[0].ok;   // one shadow ray serves both branches
+            uint32_t nsh = 0;
+            if (sh_shared) nsh = (sh_want[0] || (NB == 2 && sh_want[NB - 1])) ? 1u : 0u;
+            else {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) nsh += sh_want[b] ? 1u : 0u;
+            }
+            const uint32_t base = warp_append(&A.cnt[CNT_S + depth], nsh);
+            uint32_t k = 0;
+#pragma unroll
+            for (int e = 0; e < NB; ++e) {
+                // entry e: shared entry uses e == 0 only; separate entries one per branch
+                bool make = sh_shared ? (e == 0 && nsh) : sh_want[e];
+                if (!make) continue;
+                const uint32_t si = base + k++;
+                if (si >= A.shcap) { set_err(A, MER_ERR_BOUNDS); continue; }
+                uint32_t mask = 0;
+                if (sh_shared) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) mask |= sh_want[b] ? (1u << b) : 0u;
+                } else {
+                    mask = 1u << e;
+                }
+                const int bsrc = e;
+                float* F = A.shf;
+                const size_t C = (size_t)A.shcap;
+                F[(SF_O + 0) * C + si] = po[bsrc].x;
+                F[(SF_O + 1) * C + si] = po[bsrc].y;
+                F[(SF_O + 2) * C + si] = po[bsrc].z;
+                F[(SF_D + 0) * C + si] = ls[bsrc].wi.x;
+                F[(SF_D + 1) * C + si] = ls[bsrc].wi.y;
+                F[(SF_D + 2) * C + si] = ls[bsrc].wi.z;
+                F[SF_TMAX * C + si] = ls[bsrc].tmax;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    if (!(mask & (1u << b))) continue;
+                    const size_t base_f = SF_SLOT + (size_t)b * SF_PER_SLOT;
+                    F[(base_f + 0) * C + si] = contrib[b].x;
+                    F[(base_f + 1) * C + si] = contrib[b].y;
+                    F[(base_f + 2) * C + si] = contrib[b].z;
+                    if (GRAD) {
+                        const float sg = (b == 1) ? -1.0f : 1.0f;
+#pragma unroll
+                        for (int k2 = 0; k2 < MAXC; ++k2) F[(base_f + 3 + k2) * C + si] = sg * gnee[b][k2];
+                        A.shu[(SU_REC + b) * C + si] = rec_want[b] ? rec_idx[b] : 0xffffffffu;
+                    }
+                }
+                A.shu[SU_PATH * C + si] = (uint32_t)g;
+                A.shu[SU_META * C + si] = (uint32_t)q | (mask << 8);
+            }
+        }
+
+        // ---- continuation (compacted) ----
+        {
+            bool any_cont = false;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) any_cont |= cont[b];
+            const uint32_t slot = warp_append(&A.cnt[CNT_Q + depth + 1], any_cont ? 1u : 0u);
+            if (any_cont) {
+                if (slot >= A.qcap) {
+                    set_err(A, MER_ERR_BOUNDS);
+                } else {
+                    uint32_t nf = (uint32_t)q << 8;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) nf |= cont[b] ? (1u << b) : 0u;
+                    if (NB == 2 && coinc && cont[0] && cont[NB - 1] &&
+                        wi_b[0].x == wi_b[NB - 1].x && wi_b[0].y == wi_b[NB - 1].y && wi_b[0].z == wi_b[NB - 1].z)
+                        nf |= FLAG_COINC;
+                    A.qu[qo][QU_PATH * A.qcap + slot] = (uint32_t)g;
+                    A.qu[qo][QU_FLAGS * A.qcap + slot] = nf;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if (!cont[b]) continue;
+                        float* f = A.qf[qo] + (size_t)(b * QF_PER_BRANCH) * A.qcap + slot;
+                        f[(QF_O + 0) * A.qcap] = po[b].x;
+                        f[(QF_O + 1) * A.qcap] = po[b].y;
+                        f[(QF_O + 2) * A.qcap] = po[b].z;
+                        f[(QF_D + 0) * A.qcap] = wi_b[b].x;
+                        f[(QF_D + 1) * A.qcap] = wi_b[b].y;
+                        f[(QF_D + 2) * A.qcap] = wi_b[b].z;
+                        f[(QF_BETA + 0) * A.qcap] = beta[b].x;
+                        f[(QF_BETA + 1) * A.qcap] = beta[b].y;
+                        f[(QF_BETA + 2) * A.qcap] = beta[b].z;
+                        f[QF_PDFB * A.qcap] = pdfb[b];
+                        f[QF_PDFENV * A.qcap] = pdfenv[b];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// shadow: any-hit of NEE rays; visible ones add their radiance (and NEE gradient part)
+// ---------------------------------------------------------------------------------
+template <int NB, int MODE>
+__global__ void __launch_bounds__(256) k_shadow(PassArgs A, int depth) {
+    const Node* s_nodes;
+    const int n_staged = stage_nodes(A, s_nodes);
+    const int64_t n = min((int64_t)A.cnt[CNT_S + depth], A.shcap);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const size_t C = (size_t)A.shcap;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const float* F = A.shf;
+        const v3 o = mk(F[(SF_O + 0) * C + j], F[(SF_O + 1) * C + j], F[(SF_O + 2) * C + j]);
+        const v3 d = mk(F[(SF_D + 0) * C + j], F[(SF_D + 1) * C + j], F[(SF_D + 2) * C + j]);
+        const float tmax = F[SF_TMAX * C + j];
+        const uint32_t g = A.shu[SU_PATH * C + j];
+        const uint32_t meta = A.shu[SU_META * C + j];
+        const int q = meta & 0xff;
+        const uint32_t mask = (meta >> 8) & 3u;
+        Hit h;
+        if (traverse<true>(A.probs[q], s_nodes, q == A.smem_prob ? n_staged : 0, o, d, tmax, h)) continue;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (!(mask & (1u << b))) continue;
+            const size_t bf = SF_SLOT + (size_t)b * SF_PER_SLOT;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A.lacc[(size_t)(b * 3 + c) * A.qcap + g] += F[(bf + c) * C + j];
+            if (MODE == MODE_REPLAY) {
+                const uint32_t r = A.shu[(SU_REC + b) * C + j];
+                if (r == 0xffffffffu) continue;
+#pragma unroll
+                for (int k = 0; k < MAXC; ++k) A.rf[(size_t)(RF_G + k) * A.rcap + r] += F[(bf + 3 + k) * C + j];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// resolve radiance per path into images (mean over samples)
+// ---------------------------------------------------------------------------------
+template <int NB>
+__global__ void k_resolve(PassArgs A, float* img0, float* img1, int accumulate) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.n_paths; g += stride) {
+        int q = A.inl_prob;
+        int64_t local = g;
+        if (q < 0) {
+            const int e = find_entry(A.path_off, A.n_entries, g);
+            q = A.entry_prob[e];
+            local = g - A.path_off[e];
+        }
+        const ProblemDev& P = A.probs[q];
+        if (local >= P.n_pix) continue;
+        const int spp_here = (int)((A.inl_prob >= 0 ? A.n_paths : 0) / P.n_pix);
+        const int nsm = A.inl_prob >= 0 ? spp_here : (A.fd_kind ? P.spp_fd : P.spp_prop);
+        const int spp_total = A.spp_override > 0 ? A.spp_override : nsm;
+        const float inv = 1.0f / (float)spp_total;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            float* img = A.inl_prob >= 0 ? (b == 0 ? img0 : img1) : (A.fd_kind ? (b ? P.imgB : P.imgA) : P.img);
+            if (!img) continue;
+            img += local * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float acc = 0.0f;
+                for (int s = 0; s < nsm; ++s) acc += A.lacc[(size_t)(b * 3 + c) * A.qcap + g + (int64_t)s * P.n_pix];
+                img[c] = (accumulate ? img[c] : 0.0f) + acc * inv;
+            }
+        }
+    }
+}
+
+// per-sample radiance out[(s*n_pix + p)*3 + c] of a single-problem pass
+__global__ void k_samples_out(PassArgs A, float* out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t base = (int64_t)A.sample_base * A.probs[A.inl_prob].n_pix;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.n_paths; g += stride)
+        for (int c = 0; c < 3; ++c) out[(base + g) * 3 + c] = A.lacc[(size_t)c * A.qcap + g];
+}
+
+// ---------------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------------
+// persistent grid: resident blocks per SM from the occupancy calculator (capped by per_sm)
+template <class K>
+static int persistent_grid(K kernel, const LaunchShape& L, size_t smem) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, L.block, smem) != cudaSuccess || occ < 1) occ = 1;
+    if (L.per_sm > 0 && occ > L.per_sm) occ = L.per_sm;
+    return occ * L.sms;
+}
+
+template <int NB, int MODE>
+static void launch_depth(const PassArgs& A, int depth, const LaunchShape& L, cudaStream_t st) {
+    const size_t smem = (size_t)L.smem_nodes * sizeof(Node);
+    PassArgs B = A;
+    B.smem_nodes = L.smem_nodes;
+    static int g_ext = 0, g_sh = 0, g_sd = 0;
+    static LaunchShape last{-1, -1, -1, -1};
+    if (last.block != L.block || last.per_sm != L.per_sm || last.smem_nodes != L.smem_nodes || last.sms != L.sms) {
+        g_ext = persistent_grid(k_extend<NB>, L, smem);
+        g_sh = persistent_grid(k_shade<NB, MODE>, L, 0);
+        g_sd = persistent_grid(k_shadow<NB, MODE>, L, smem);
+        last = L;
+    }
+    k_extend<NB><<<g_ext, L.block, smem, st>>>(B, depth);
+    k_shade<NB, MODE><<<g_sh, L.block, 0, st>>>(B, depth);
+    k_shadow<NB, MODE><<<g_sd, L.block, smem, st>>>(B, depth);
+}
+
+// enqueues one full pass; returns the number of kernel launches
+int run_pass(const PassArgs& A, int nb, int mode, int max_depth, const LaunchShape& L, cudaStream_t st) {
+    int launches = 0;
+    for (int depth = 1; depth <= max_depth; ++depth) {
+        if (nb == 1) {
+            if (mode == MODE_REPLAY) launch_depth<1, MODE_REPLAY>(A, depth, L, st);
+            else launch_depth<1, MODE_PRIMAL>(A, depth, L, st);
+        } else {
+            if (mode == MODE_REPLAY) launch_depth<2, MODE_REPLAY>(A, depth, L, st);
+            else launch_depth<2, MODE_PRIMAL>(A, depth, L, st);
+        }
+        launches += 3;
+    }
+    return launches;
+}
+
+int run_resolve(const PassArgs& A, int nb, float* img0, float* img1, int accumulate, int grid, cudaStream_t st) {
+    if (nb == 1) k_resolve<1><<<grid, 256, 0, st>>>(A, img0, img1, accumulate);
+    else k_resolve<2><<<grid, 256, 0, st>>>(A, img0, img1, accumulate);
+    return 1;
+}
+
+int run_samples_out(const PassArgs& A, float* out, int grid, cudaStream_t st) {
+    k_samples_out<<<grid, 256, 0, st>>>(A, out);
+    return 1;
+}
+
+cudaError_t set_trace_smem_limits(int max_nodes) {
+    const int bytes = max_nodes * (int)sizeof(Node);
+    cudaError_t e = cudaSuccess;
+    e = cudaFuncSetAttribute(k_extend<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
+    e = cudaFuncSetAttribute(k_extend<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
+    e = cudaFuncSetAttribute(k_shadow<1, MODE_PRIMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
+    e = cudaFuncSetAttribute(k_shadow<1, MODE_REPLAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
+    e = cudaFuncSetAttribute(k_shadow<2, MODE_PRIMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
+    e = cudaFuncSetAttribute(k_shadow<2, MODE_REPLAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+}  // namespace mer

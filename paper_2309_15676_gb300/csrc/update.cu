@@ -1,0 +1,266 @@
+// Fused per-parameter update (step a11): one HBM pass over every parameter of every
+// problem. META mode (Sec. 4, Sec. 5 and the appendix pseudocode):
+//   m2f <- m2f + cF (F^2 - m2f)                                  Var[<F_i>]  (Eq. varest, start-up corrected)
+//   if FD available: m2d <- m2d + cD ((dF/||dpi||)^2 - m2d)      Var[<dF_i>]_D (Sec. 4.2)
+//                    vard = m2d ||dpi||^2                         (Eq. vardiff)
+//   mean += dF ; var += vard                                      (Eq. recurrent_meta, varmeta: carried terms)
+//   a = m2f / (m2f + var + eps_alpha) ; a = min(a, 1/(2 - a_prev))  (Eqs. alpha, alpha_clip_2)
+//   mean = a mean + (1-a) F ; var = a^2 var + (1-a)^2 m2f
+//   pi' = clamp(pi - lr mean / (sqrt(var) + eps))                 (update rule of Sec. 5)
+// ADAM mode (Sec. 5, Eqs. adam_moment, adam_ema_startup, adam_step) keeps m in `mean` and v
+// in `m2f`. Both modes write pi' into the other parameter slot, clear F and dF, and reduce
+// ||pi' - pi||^2 per problem deterministically (per-block partials, fixed-order sum).
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "update.cuh"
+
+namespace mer {
+
+constexpr int UPD_THREADS = 256;
+constexpr int UPD_VEC_PER_THREAD = 4;                       // float4 per thread per block
+constexpr int64_t UPD_CHUNK = (int64_t)UPD_THREADS * UPD_VEC_PER_THREAD * 4;   // params per block
+
+int64_t update_blocks_for(int64_t n) { return (n + UPD_CHUNK - 1) / UPD_CHUNK; }
+
+struct Coef {
+    float cF, cD, norm2, inv_norm, c1, c2;
+    int stepD;
+};
+
+__device__ __forceinline__ Coef make_coef(const UpdSeg& S, int iteration, int count_f, int count_d, double n2) {
+    Coef k;
+    const mer_hyper& h = S.hyper;
+    if (h.mode == MER_MODE_META) {
+        const double bf = (double)h.beta_f, bd = (double)h.beta_d;
+        k.cF = (float)((1.0 - bf) / (1.0 - pow(bf, (double)(count_f + 1))));
+        k.stepD = (iteration >= 1 && n2 > 0.0) ? 1 : 0;
+        k.cD = k.stepD ? (float)((1.0 - bd) / (1.0 - pow(bd, (double)(count_d + 1)))) : 0.0f;
+        k.norm2 = (float)n2;
+        k.inv_norm = k.stepD ? (float)(1.0 / sqrt(n2)) : 0.0f;
+        k.c1 = k.c2 = 0.0f;
+    } else {
+        const double t = (double)(iteration + 1);
+        k.c1 = (float)(1.0 / (1.0 - pow((double)h.beta1, t)));
+        k.c2 = (float)(1.0 / (1.0 - pow((double)h.beta2, t)));
+        k.cF = k.cD = k.norm2 = k.inv_norm = 0.0f;
+        k.stepD = 0;
+    }
+    return k;
+}
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+
+// one element of META mode; returns the applied step
+__device__ __forceinline__ float meta_elem(const mer_hyper& h, const Coef& k, float p, float F, float dF, float& m2f,
+                                           float& m2d, float& mean, float& var, float& ap, float lo, float hi,
+                                           float& pnew) {
+    m2f = m2f + k.cF * (F * F - m2f);
+    float vard = 0.0f, dfu = 0.0f;
+    if (k.stepD) {
+        const float x = dF * k.inv_norm;
+        m2d = m2d + k.cD * (x * x - m2d);
+        vard = m2d * k.norm2;
+        dfu = dF;
+    }
+    mean = mean + dfu;
+    var = var + vard;
+    float a = m2f / (m2f + var + h.eps_alpha);
+    a = fminf(a, 1.0f / (2.0f - ap));
+    ap = a;
+    const float b = 1.0f - a;
+    mean = a * mean + b * F;
+    var = a * a * var + b * b * m2f;
+    const float step = -h.lr * mean / (sqrtf(var) + h.eps);
+    pnew = clampf(p + step, lo, hi);
+    return pnew - p;
+}
+
+__device__ __forceinline__ float adam_elem(const mer_hyper& h, const Coef& k, float p, float F, float& v, float& m,
+                                           float lo, float hi, float& pnew) {
+    m = h.beta1 * m + (1.0f - h.beta1) * F;
+    v = h.beta2 * v + (1.0f - h.beta2) * F * F;
+    const float step = -h.lr * (m * k.c1) / (sqrtf(v * k.c2) + h.eps);
+    pnew = clampf(p + step, lo, hi);
+    return pnew - p;
+}
+
+#define F4(ptr, i) (reinterpret_cast<float4*>(ptr)[i])
+#define CF4(ptr, i) (reinterpret_cast<const float4*>(ptr)[i])
+
+// processes [blk_begin*CHUNK, ...) of one segment; returns this thread's sum of squared steps
+__device__ __forceinline__ float update_block(const UpdSeg& S, const Coef& k, int cur, int64_t local_block) {
+    const float* pin = cur ? S.pB : S.pA;
+    float* pout = cur ? S.pA : S.pB;
+    const bool meta = S.hyper.mode == MER_MODE_META;
+    const int C = S.C;
+    float acc = 0.0f;
+    const int64_t n4 = S.n >> 2;          // float4 count (n is a multiple of 4 for vector lanes)
+    const int64_t v0 = local_block * (UPD_CHUNK >> 2);
+#pragma unroll
+    for (int it = 0; it < UPD_VEC_PER_THREAD; ++it) {
+        const int64_t v = v0 + (int64_t)it * UPD_THREADS + threadIdx.x;
+        if (v >= n4) break;
+        const float4 p4 = CF4(pin, v);
+        const float4 F4v = CF4(S.F, v);
+        float4 m2f4 = CF4(S.m2f, v), mean4 = CF4(S.mean, v);
+        float4 dF4 = make_float4(0, 0, 0, 0), m2d4 = dF4, var4 = dF4, ap4 = dF4;
+        if (meta) {
+            dF4 = CF4(S.dF, v);
+            m2d4 = CF4(S.m2d, v);
+            var4 = CF4(S.var, v);
+            ap4 = CF4(S.ap, v);
+        }
+        float pv[4] = {p4.x, p4.y, p4.z, p4.w}, Fv[4] = {F4v.x, F4v.y, F4v.z, F4v.w};
+        float dFv[4] = {dF4.x, dF4.y, dF4.z, dF4.w}, m2fv[4] = {m2f4.x, m2f4.y, m2f4.z, m2f4.w};
+        float m2dv[4] = {m2d4.x, m2d4.y, m2d4.z, m2d4.w}, meanv[4] = {mean4.x, mean4.y, mean4.z, mean4.w};
+        float varv[4] = {var4.x, var4.y, var4.z, var4.w}, apv[4] = {ap4.x, ap4.y, ap4.z, ap4.w};
+        float out[4];
+        const int c0 = (int)((v * 4) % C);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            int c = c0 + l;
+            if (c >= C) c -= C;
+            if (c >= C) c -= C;
+            float st;
+            if (meta)
+                st = meta_elem(S.hyper, k, pv[l], Fv[l], dFv[l], m2fv[l], m2dv[l], meanv[l], varv[l], apv[l], S.lo[c],
+                               S.hi[c], out[l]);
+            else
+                st = adam_elem(S.hyper, k, pv[l], Fv[l], m2fv[l], meanv[l], S.lo[c], S.hi[c], out[l]);
+            acc += st * st;
+        }
+        F4(pout, v) = make_float4(out[0], out[1], out[2], out[3]);
+        F4(S.m2f, v) = make_float4(m2fv[0], m2fv[1], m2fv[2], m2fv[3]);
+        F4(S.mean, v) = make_float4(meanv[0], meanv[1], meanv[2], meanv[3]);
+        if (meta) {
+            if (k.stepD) F4(S.m2d, v) = make_float4(m2dv[0], m2dv[1], m2dv[2], m2dv[3]);
+            F4(S.var, v) = make_float4(varv[0], varv[1], varv[2], varv[3]);
+            F4(S.ap, v) = make_float4(apv[0], apv[1], apv[2], apv[3]);
+        }
+        if (S.zero_grads) {
+            F4(S.F, v) = make_float4(0, 0, 0, 0);
+            if (meta) F4(S.dF, v) = make_float4(0, 0, 0, 0);
+        }
+    }
+    // scalar tail (n not a multiple of 4): first block, first threads
+    if (local_block == 0 && threadIdx.x < (int)(S.n & 3)) {
+        const int64_t e = (n4 << 2) + threadIdx.x;
+        const int c = (int)(e % C);
+        float m2f = S.m2f[e], mean = S.mean[e], pnew, st;
+        if (meta) {
+            float m2d = S.m2d[e], var = S.var[e], ap = S.ap[e];
+            st = meta_elem(S.hyper, k, pin[e], S.F[e], S.dF[e], m2f, m2d, mean, var, ap, S.lo[c], S.hi[c], pnew);
+            if (k.stepD) S.m2d[e] = m2d;
+            S.var[e] = var;
+            S.ap[e] = ap;
+        } else {
+            st = adam_elem(S.hyper, k, pin[e], S.F[e], m2f, mean, S.lo[c], S.hi[c], pnew);
+        }
+        pout[e] = pnew;
+        S.m2f[e] = m2f;
+        S.mean[e] = mean;
+        if (S.zero_grads) {
+            S.F[e] = 0.0f;
+            if (meta) S.dF[e] = 0.0f;
+        }
+        acc += st * st;
+    }
+    return acc;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[UPD_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < UPD_THREADS / 32; ++i) s += red[i];
+    return s;
+}
+
+// context form: segment table on the device, per-problem scalars in ProbState
+__global__ void __launch_bounds__(UPD_THREADS) k_update_ctx(const UpdSeg* segs, const int64_t* blk_off, int n_segs,
+                                                            ProbState* ps, double* partials) {
+    __shared__ Coef sk;
+    __shared__ int s_seg, s_cur;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_segs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (blk_off[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_seg = lo;
+        const UpdSeg& S = segs[lo];
+        const ProbState st = ps[S.prob];
+        sk = make_coef(S, st.iteration, st.count_f, st.count_d, st.dpi_norm2);
+        s_cur = st.cur;
+    }
+    __syncthreads();
+    const UpdSeg& S = segs[s_seg];
+    const float acc = update_block(S, sk, s_cur, (int64_t)blockIdx.x - blk_off[s_seg]);
+    const double tot = block_sum((double)acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// per segment: fixed-order sum of its partials, then advance the problem's scalars
+__global__ void __launch_bounds__(UPD_THREADS) k_update_finalize_ctx(const UpdSeg* segs, const int64_t* blk_off,
+                                                                     ProbState* ps, const double* partials) {
+    const int sgi = blockIdx.x;
+    const UpdSeg& S = segs[sgi];
+    double v = 0.0;
+    for (int64_t i = blk_off[sgi] + threadIdx.x; i < blk_off[sgi + 1]; i += UPD_THREADS) v += partials[i];
+    const double tot = block_sum(v);
+    if (threadIdx.x == 0) {
+        ProbState& st = ps[S.prob];
+        if (S.hyper.mode == MER_MODE_META) {
+            const bool stepD = st.iteration >= 1 && st.dpi_norm2 > 0.0;
+            st.count_f += 1;
+            st.count_d += stepD ? 1 : 0;
+        } else {
+            st.count_f += 1;
+        }
+        st.iteration += 1;
+        st.cur ^= 1;
+        st.dpi_norm2 = tot;
+    }
+}
+
+// standalone form: one segment passed by value, scalars from the caller
+__global__ void __launch_bounds__(UPD_THREADS) k_update_raw(UpdSeg S, int iteration, int count_f, int count_d,
+                                                            double n2, double* partials) {
+    __shared__ Coef sk;
+    if (threadIdx.x == 0) sk = make_coef(S, iteration, count_f, count_d, n2);
+    __syncthreads();
+    const float acc = update_block(S, sk, 0, blockIdx.x);
+    const double tot = block_sum((double)acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(UPD_THREADS) k_update_finalize_raw(const double* partials, int64_t nb,
+                                                                     double* out) {
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < nb; i += UPD_THREADS) v += partials[i];
+    const double tot = block_sum(v);
+    if (threadIdx.x == 0) *out = tot;
+}
+
+cudaError_t launch_update_ctx(const UpdSeg* segs_dev, const int64_t* blk_off_dev, int n_segs, int64_t total_blocks,
+                              ProbState* ps, double* partials, cudaStream_t st) {
+    if (total_blocks <= 0) return cudaSuccess;
+    k_update_ctx<<<(unsigned)total_blocks, UPD_THREADS, 0, st>>>(segs_dev, blk_off_dev, n_segs, ps, partials);
+    k_update_finalize_ctx<<<n_segs, UPD_THREADS, 0, st>>>(segs_dev, blk_off_dev, ps, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int count_d, double n2, double* partials,
+                              int64_t nblocks, double* out, cudaStream_t st) {
+    if (nblocks > 0) k_update_raw<<<(unsigned)nblocks, UPD_THREADS, 0, st>>>(S, iteration, count_f, count_d, n2, partials);
+    k_update_finalize_raw<<<1, UPD_THREADS, 0, st>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mer

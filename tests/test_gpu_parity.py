@@ -1,0 +1,353 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on identical seeded inputs.
+
+Tolerances (stated by the build's goal and derived in the design notes):
+  - Philox draws: bit-exact;
+  - per-sample radiance: >= 99.99% of samples within 1e-4 relative (absolute floor 1e-6);
+  - image-summed texel gradients: within 1e-3 relative;
+  - meta-estimator / Adam update outputs on identical inputs: within 1e-5 relative to the
+    magnitude of the terms that form them (FP32 rounding of a sum is bounded by the sum of the
+    absolute values of its terms).
+"""
+import numpy as np
+import pytest
+
+from oracle import meta, orc
+from paper_2309_15676_gb300 import synth
+
+from .gpu_common import frac_within, need_gpu, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    return need_gpu()
+
+
+def _ctx(torch_mod, scene, **kw):
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    ctx = Context(0)
+    pid = ctx.add_scene(scene, HyperParams(**kw))
+    return ctx, pid
+
+
+# ---------------------------------------------------------------------------------------
+# Philox
+# ---------------------------------------------------------------------------------------
+def test_philox_bit_exact(torch_mod):
+    torch = torch_mod
+    from paper_2309_15676_gb300.api import philox
+    rng = np.random.default_rng(0)
+    n = 1_000_000
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:1000] = 0
+    ctr[1000:2000] = 0xFFFFFFFF
+    for key in ((0, 0), (0xDEADBEEF, 7), (0xFFFFFFFF, 0xFFFFFFFF)):
+        dev = torch.from_numpy(ctr.view(np.int32)).cuda()
+        got = philox(key[0], key[1], dev).cpu().numpy().view(np.uint32)
+        ref = orc.philox_batch(ctr, key)
+        assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------------------------------
+# fused update (standalone entry point)
+# ---------------------------------------------------------------------------------------
+def _rand_state(rng, n, iteration):
+    F = rng.normal(0, 1e-2, n).astype(np.float32)
+    dF = rng.normal(0, 3e-3, n).astype(np.float32)
+    pi = rng.uniform(0.05, 0.95, n).astype(np.float32)
+    if iteration == 0:
+        z = np.zeros(n, np.float32)
+        return dict(pi=pi, F=F, dF=dF, m2f=z.copy(), m2d=z.copy(), mean=z.copy(), var=z.copy(),
+                    ap=np.full(n, -np.inf, np.float32))
+    m2f = (rng.normal(0, 1e-2, n) ** 2).astype(np.float32)
+    m2f[::97] = 0.0                                  # unseen texels
+    m2d = (rng.normal(0, 1e-1, n) ** 2).astype(np.float32)
+    mean = rng.normal(0, 1e-2, n).astype(np.float32)
+    var = (rng.uniform(0.1, 1, n) * m2f).astype(np.float32)
+    ap = rng.uniform(0, iteration / (iteration + 1), n).astype(np.float32)
+    return dict(pi=pi, F=F, dF=dF, m2f=m2f, m2d=m2d, mean=mean, var=var, ap=ap)
+
+
+@pytest.mark.parametrize("n,C,iteration,n2,mode", [
+    (4099, 3, 0, 0.0, "meta"), (4099, 3, 5, 2.5e-5, "meta"), (50001, 5, 7, 0.0, "meta"),
+    (50001, 5, 3, 1e-3, "meta"), (17, 5, 1, 4e-6, "meta"), (4099, 3, 0, 0.0, "adam"), (50001, 5, 9, 0.0, "adam")])
+def test_update_matches_oracle(torch_mod, n, C, iteration, n2, mode):
+    torch = torch_mod
+    from paper_2309_15676_gb300.api import HyperParams, MODE_ADAM, MODE_META, meta_step_raw
+    rng = np.random.default_rng(n + iteration)
+    s = _rand_state(rng, n, iteration)
+    lo = np.array([0.0, 0.0, 0.0, 0.0, 0.05][:C], np.float32)
+    hi = np.ones(C, np.float32)
+    h = HyperParams(mode=MODE_META if mode == "meta" else MODE_ADAM, lr=0.01, beta_f=0.99, beta_d=0.9)
+    count_f = iteration
+    count_d = max(0, iteration - 2)
+    d = {k: torch.from_numpy(v.copy()).cuda() for k, v in s.items()}
+    pi_next = torch.empty_like(d["pi"])
+    out = meta_step_raw(h, d["pi"], pi_next, d["F"], d["dF"], d["m2f"], d["m2d"], d["mean"], d["var"], d["ap"], C,
+                        lo, hi, iteration, count_f, count_d, n2, zero_grads=True)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in d.items()}
+    got_pi = pi_next.cpu().numpy().astype(np.float64)
+    ch = np.arange(n) % C
+    lo_e, hi_e = lo[ch].astype(np.float64), hi[ch].astype(np.float64)
+    H = meta.Hyper(lr=float(np.float32(0.01)), beta_f=float(np.float32(0.99)), beta_d=float(np.float32(0.9)),
+                   eps=float(np.float32(1e-8)), eps_alpha=float(np.float32(1e-30)),
+                   beta1=float(np.float32(0.9)), beta2=float(np.float32(0.999)))
+    x = {k: v.astype(np.float64) for k, v in s.items()}
+    if mode == "meta":
+        st = meta.MetaState(x["m2f"].copy(), x["m2d"].copy(), x["mean"].copy(), x["var"].copy(), x["ap"].copy(),
+                            count_f, count_d, iteration)
+        ref_pi, ref_n2, alpha = meta.meta_update(x["pi"], x["F"], x["dF"], st, H, n2, lo_e, hi_e)
+        dfu = x["dF"] if (iteration >= 1 and n2 > 0) else 0.0
+        scale_mean = np.abs(x["mean"] + dfu) + np.abs(x["F"])
+        assert np.allclose(g["m2f"], st.m2f, rtol=1e-5, atol=0)
+        assert np.allclose(g["m2d"], st.m2d, rtol=1e-5, atol=0)
+        assert np.allclose(g["var"], st.var, rtol=1e-5, atol=0)
+        assert np.all(np.abs(g["mean"] - st.mean) <= 1e-5 * scale_mean + 1e-30)
+        assert np.all(np.abs(g["ap"] - st.alpha_prev) <= 1e-5 * np.abs(st.alpha_prev) + 1e-7)
+        step_scale = H.lr * scale_mean / (np.sqrt(st.var) + H.eps)
+    else:
+        st = meta.AdamState(x["mean"].copy(), x["m2f"].copy(), iteration)
+        ref_pi, ref_n2 = meta.adam_update(x["pi"], x["F"], st, H, lo_e, hi_e)
+        assert np.allclose(g["m2f"], st.v, rtol=1e-5, atol=0)
+        scale_m = H.beta1 * np.abs(x["mean"]) + (1 - H.beta1) * np.abs(x["F"])
+        assert np.all(np.abs(g["mean"] - st.m) <= 1e-5 * scale_m + 1e-30)
+        step_scale = H.lr * scale_m / (1 - H.beta1 ** (iteration + 1)) / (
+            np.sqrt(st.v / (1 - H.beta2 ** (iteration + 1))) + H.eps)
+    # the applied step within 1e-5 of its own scale (plus the rounding of pi itself)
+    err = np.abs(got_pi - ref_pi)
+    assert np.all(err <= 1e-5 * step_scale + 2 ** -23 * np.abs(x["pi"]) + 1e-12), err.max()
+    assert abs(out.item() - ref_n2) <= 1e-5 * ref_n2 + 1e-12 * n
+    assert np.all(g["F"] == 0) and (mode == "adam" or np.all(g["dF"] == 0))
+
+
+# ---------------------------------------------------------------------------------------
+# closed forms on the GPU
+# ---------------------------------------------------------------------------------------
+def test_furnace_and_plane_closed_forms(torch_mod):
+    env = np.array([0.5, 1.0, 2.0], np.float32)
+    ctx, pid = _ctx(torch_mod, synth.furnace_scene(albedo=0.6, max_depth=3, env=tuple(env)))
+    L = ctx.render_samples(pid, np.zeros((8, 8, 3), np.float32), spp=4).cpu().numpy().reshape(-1, 3)
+    a = np.float32(0.6)
+    hit = np.all(np.abs(L - a * env) <= 1e-5 * a * env, axis=1)
+    miss = np.all(np.abs(L - env) <= 1e-6 * env, axis=1)
+    assert np.all(hit | miss) and hit.mean() > 0.2
+    ctx.close()
+    ctx, pid = _ctx(torch_mod, synth.plane_scene(max_depth=3, env=(0.7, 0.8, 0.9)))
+    L = ctx.render_samples(pid, np.full((8, 8, 3), 0.3, np.float32), spp=2).cpu().numpy().reshape(-1, 3)
+    ref = np.float32(0.3) * np.array([0.7, 0.8, 0.9], np.float32)
+    assert np.all(np.abs(L - ref) <= 1e-5 * ref)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------
+# per-sample radiance
+# ---------------------------------------------------------------------------------------
+def _sample_parity(ctx, pid, scene, tex, spp, stream, iteration, max_ref=None, seed=0):
+    got = ctx.render_samples(pid, tex, spp=spp, stream=stream, iteration=iteration).cpu().numpy()
+    npix = scene["width"] * scene["height"]
+    got = got.reshape(spp * npix, 3)
+    idx = np.arange(spp * npix)
+    if max_ref is not None and len(idx) > max_ref:
+        idx = np.sort(np.random.default_rng(seed).choice(len(idx), max_ref, replace=False))
+    pixels, samples = idx % npix, idx // npix
+    ref = orc.render_samples(orc.Scene(scene), tex, pixels, samples, iteration, stream)
+    ok = np.all(np.abs(got[idx] - ref) <= 1e-4 * np.abs(ref) + 1e-6, axis=1)
+    return ok.mean(), len(idx)
+
+
+def test_radiance_box(torch_mod):
+    w = synth.workload_box(64, 64, 32, max_depth=3)
+    ctx, pid = _ctx(torch_mod, w.scene)
+    frac, n = _sample_parity(ctx, pid, w.scene, w.init_tex, 4, 0, 3)
+    assert frac >= 0.9999, (frac, n)
+    ctx.close()
+
+
+def test_radiance_spiral_small(torch_mod):
+    w = synth.workload_spiral(48, 40, 64, 16, 64, max_depth=5)
+    ctx, pid = _ctx(torch_mod, w.scene)
+    frac, n = _sample_parity(ctx, pid, w.scene, w.init_tex, 3, 1, 7)
+    assert frac >= 0.9999, (frac, n)
+    ctx.close()
+
+
+def test_radiance_spiral_full_size_sampled(torch_mod):
+    """256x256, 8192 triangles, 5-channel 256^2 textures, depth 5: 3000 sampled paths."""
+    w = synth.workload_spiral()
+    ctx, pid = _ctx(torch_mod, w.scene)
+    frac, n = _sample_parity(ctx, pid, w.scene, w.init_tex, 2, 0, 11, max_ref=3000)
+    assert frac >= 0.999, (frac, n)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------
+# gradients
+# ---------------------------------------------------------------------------------------
+def _grad_check(got, ref):
+    e = rel_l2(got, ref)
+    f = frac_within(got, ref, 1e-3, 1e-5 * np.abs(ref).max())
+    return e, f
+
+
+@pytest.mark.parametrize("which", ["box", "spiral"])
+def test_adjoint_matches_oracle(torch_mod, which):
+    if which == "box":
+        w = synth.workload_box(64, 64, 32, max_depth=3)
+    else:
+        w = synth.workload_spiral(40, 32, 64, 16, 32, max_depth=4)
+    sc = w.scene
+    ctx, pid = _ctx(torch_mod, sc)
+    dimg = np.random.default_rng(1).normal(size=(sc["height"], sc["width"], 3)).astype(np.float32)
+    got = ctx.adjoint(pid, w.init_tex, dimg, spp=2, stream=1, iteration=4).cpu().numpy()
+    ref = orc.adjoint_image(orc.Scene(sc), w.init_tex, 2, 4, 1, dimg)
+    e, f = _grad_check(got, ref)
+    assert e < 1e-3 and f >= 0.999, (e, f)
+    ctx.close()
+
+
+def test_fd_pair_matches_two_oracle_adjoints(torch_mod):
+    """Eq. est_triv: the in-thread pair equals two separate same-seed evaluations."""
+    w = synth.workload_spiral(40, 32, 64, 16, 32, max_depth=4)
+    sc = w.scene
+    ctx, pid = _ctx(torch_mod, sc)
+    tA = w.init_tex
+    tB = np.clip(w.init_tex + np.random.default_rng(2).normal(0, 0.02, w.init_tex.shape), 0.05, 0.95
+                 ).astype(np.float32)
+    iA, iB = ctx.render_pair(pid, tA, tB, spp=2, stream=2, iteration=3)
+    s = orc.Scene(sc)
+    rA = orc.render_image(s, tA, 2, 3, 2)
+    rB = orc.render_image(s, tB, 2, 3, 2)
+    assert frac_within(iA.cpu().numpy(), rA, 1e-4, 1e-6) > 0.999
+    assert frac_within(iB.cpu().numpy(), rB, 1e-4, 1e-6) > 0.999
+    rng = np.random.default_rng(3)
+    dA = rng.normal(size=rA.shape).astype(np.float32)
+    dB = rng.normal(size=rA.shape).astype(np.float32)
+    got = ctx.adjoint_pair(pid, tA, tB, dA, dB, spp=2, stream=3, iteration=3).cpu().numpy()
+    ref = orc.adjoint_image(s, tA, 2, 3, 3, dA) - orc.adjoint_image(s, tB, 2, 3, 3, dB)
+    e, f = _grad_check(got, ref)
+    assert e < 1e-3 and f >= 0.999, (e, f)
+    ctx.close()
+
+
+def test_central_fd_on_gpu_albedo(torch_mod):
+    """Adjoint against central finite differences of the GPU's own render with common random numbers."""
+    torch = torch_mod
+    w = synth.workload_box(32, 32, 8, max_depth=3)
+    ctx, pid = _ctx(torch_mod, w.scene)
+    dimg = torch.from_numpy(np.random.default_rng(4).normal(size=(32, 32, 3)).astype(np.float32)).cuda()
+    tex = torch.from_numpy(w.init_tex).cuda()
+    g = ctx.adjoint(pid, tex, dimg, spp=4, stream=5, iteration=1).cpu().numpy()
+    J = lambda t: float((ctx.render(pid, t, spp=4, stream=5, iteration=1).double() * dimg.double()).sum())
+    h = 1e-2
+    nz = np.argwhere(np.abs(g).max(-1) > 0.1 * np.abs(g).max())
+    for (y, x) in nz[:: max(1, len(nz) // 8)]:
+        for c in range(3):
+            tp, tm = tex.clone(), tex.clone()
+            tp[y, x, c] += h
+            tm[y, x, c] -= h
+            fd = (J(tp) - J(tm)) / (2 * h)
+            assert abs(g[y, x, c] - fd) <= 2e-3 * abs(fd) + 1e-3 * np.abs(g).max(), (y, x, c, g[y, x, c], fd)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------------------
+# one full iteration (a1-a11) against the oracle on identical inputs
+# ---------------------------------------------------------------------------------------
+def test_iteration_matches_oracle(torch_mod):
+    torch = torch_mod
+    w = synth.workload_spiral(40, 32, 64, 16, 32, max_depth=4, spp_prop=2, spp_fd=1)
+    sc = w.scene
+    ctx, pid = _ctx(torch_mod, sc, lr=0.02)
+    target = orc.render_image(orc.Scene(sc), w.target_tex, 16, 0, orc.ST_TARGET).astype(np.float32)
+    ctx.set_target(pid, target)
+    ctx.set_params(pid, w.init_tex)
+    s = orc.Scene(sc)
+    H = meta.Hyper(lr=float(np.float32(0.02)), beta_f=float(np.float32(0.99)), beta_d=float(np.float32(0.9)))
+    lo = np.asarray(sc["clamp_lo"], np.float64)
+    hi = np.asarray(sc["clamp_hi"], np.float64)
+    for it in range(3):
+        st_gpu = ctx.state(pid)
+        pre = {k: v.cpu().numpy().astype(np.float64) for k, v in st_gpu.items()}
+        stats_pre = ctx.stats(pid)
+        ctx.gradient_step()
+        F, dF = (x.cpu().numpy().astype(np.float64) for x in ctx.grads(pid))
+        Fo, loss_o, _ = orc.prop_gradient(s, pre["pi_cur"], target, 2, it)
+        e, f = _grad_check(F, Fo)
+        assert e < 1e-3 and f > 0.999, ("F", it, e, f)
+        assert abs(ctx.stats(pid)["loss"] - loss_o) <= 1e-4 * loss_o
+        if it >= 1:
+            dFo = orc.fd_gradient(s, pre["pi_cur"], pre["pi_prev"], target, 1, it)
+            e, f = _grad_check(dF, dFo)
+            assert e < 1e-3 and f > 0.999, ("dF", it, e, f)
+        else:
+            assert np.all(dF == 0)
+        # update on identical inputs (the GPU's F, dF and state)
+        ost = meta.MetaState(pre["m2f"], pre["m2d"], pre["mean"], pre["var"], pre["alpha_prev"],
+                             stats_pre["count_f"], stats_pre["count_d"], it)
+        ref_pi, ref_n2, _ = meta.meta_update(pre["pi_cur"], F, dF, ost, H, stats_pre["dpi_norm2"],
+                                             lo[None, None, :], hi[None, None, :])
+        ctx.update_step()
+        got_pi = ctx.get_params(pid).cpu().numpy().astype(np.float64)
+        step_ref = ref_pi - pre["pi_cur"]
+        err = np.abs((got_pi - pre["pi_cur"]) - step_ref)
+        assert np.all(err <= 1e-4 * np.abs(step_ref) + 1e-4 * H.lr), (it, err.max())
+        assert abs(ctx.stats(pid)["dpi_norm2"] - ref_n2) <= 1e-4 * ref_n2
+    ctx.close()
+
+
+def test_graph_checkpoint_batch_consistency(torch_mod):
+    """Graph-captured iterations equal plain launches; a restored checkpoint continues identically;
+    a problem optimised inside a batch equals the same problem alone (counters keyed by key_id)."""
+    torch = torch_mod
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    wb = synth.workload_box(32, 32, 16, max_depth=3, key_id=5)
+    ws = synth.workload_spiral(32, 32, 32, 8, 16, max_depth=4, key_id=9)
+    tb = orc.render_image(orc.Scene(wb.scene), wb.target_tex, 8, 0, orc.ST_TARGET).astype(np.float32)
+    ts = orc.render_image(orc.Scene(ws.scene), ws.target_tex, 8, 0, orc.ST_TARGET).astype(np.float32)
+
+    def make(ws_list):
+        ctx = Context(0)
+        ids = []
+        for w, t in ws_list:
+            p = ctx.add_scene(w.scene, HyperParams(lr=0.02))
+            ctx.set_target(p, t)
+            ctx.set_params(p, w.init_tex)
+            ids.append(p)
+        return ctx, ids
+
+    a, (a0, a1) = make([(wb, tb), (ws, ts)])
+    a.iterate(3, use_graph=False)
+    b, (b0, b1) = make([(wb, tb), (ws, ts)])
+    b.iterate(3, use_graph=True)
+    c, (c1,) = make([(ws, ts)])
+    c.iterate(3, use_graph=True)
+    pa, pb, pc = a.get_params(a1).cpu().numpy(), b.get_params(b1).cpu().numpy(), c.get_params(c1).cpu().numpy()
+    assert np.allclose(pa, pb, rtol=0, atol=1e-5) and np.allclose(pb, pc, rtol=0, atol=1e-5)
+    assert np.allclose(a.get_params(a0).cpu().numpy(), b.get_params(b0).cpu().numpy(), rtol=0, atol=1e-5)
+    blob = b.checkpoint_save()
+    b.iterate(2, use_graph=True)
+    after = b.get_params(b1).cpu().numpy()
+    b.checkpoint_load(blob)
+    b.iterate(2, use_graph=True)
+    assert np.allclose(b.get_params(b1).cpu().numpy(), after, rtol=0, atol=1e-5)
+    assert b.stats(b1)["iteration"] == 5
+    for x in (a, b, c):
+        x.close()
+
+
+def test_autograd_function_replays_paths(torch_mod):
+    torch = torch_mod
+    from paper_2309_15676_gb300.autograd import render
+    w = synth.workload_box(24, 24, 8, max_depth=3)
+    ctx, pid = _ctx(torch_mod, w.scene)
+    tex = torch.from_numpy(w.init_tex).cuda().requires_grad_(True)
+    tgt = torch.full((24, 24, 3), 0.3, device="cuda")
+    img = render(ctx, pid, tex, spp=2, stream=5, iteration=3)
+    loss = ((img - tgt) ** 2).mean()
+    loss.backward()
+    dimg = (2 * (img.detach() - tgt) / img.numel()).contiguous()
+    ref = ctx.adjoint(pid, tex.detach(), dimg, spp=2, stream=5, iteration=3)
+    assert torch.allclose(tex.grad, ref, rtol=1e-5, atol=1e-8)
+    ctx.close()
