@@ -195,9 +195,16 @@ struct MatEval {
     float th[MAXC];   // bc.rgb (or albedo), metal, rough
 };
 
-__device__ __forceinline__ float ggx_d(float a2, float ch) {
-    const float k = ch * ch * (a2 - 1.0f) + 1.0f;
+// GGX D with k = cos^2 a^2 + sin^2, sin^2 taken from |n x h|^2 so that it keeps its
+// relative precision near the specular peak (1 - cos^2 would cancel in FP32)
+__device__ __forceinline__ float ggx_k(float a2, float ch, float sh2) { return ch * ch * a2 + sh2; }
+__device__ __forceinline__ float ggx_d(float a2, float ch, float sh2) {
+    const float k = ggx_k(a2, ch, sh2);
     return a2 / (PI_F * k * k);
+}
+__device__ __forceinline__ float sin2(v3 n, v3 h) {
+    const v3 c = cross(n, h);
+    return dot(c, c);
 }
 
 __device__ __forceinline__ float smith_g1(float a2, float c) {
@@ -218,7 +225,7 @@ __device__ __forceinline__ v3 bsdf_f(const MatEval& m, v3 n, v3 wo, v3 wi) {
     const float a = r * r, a2 = a * a;
     const v3 h = normalize(wo + wi);
     const float ch = dot(n, h), vh = dot(wi, h);
-    const float S = ggx_d(a2, ch) * smith_g1(a2, co) * smith_g1(a2, ci) / (4.0f * co * ci);
+    const float S = ggx_d(a2, ch, sin2(n, h)) * smith_g1(a2, co) * smith_g1(a2, ci) / (4.0f * co * ci);
     const float fw = pow5(1.0f - vh);
     const float kd = (1.0f - metal) * INV_PI_F;
     float f[3];
@@ -244,7 +251,7 @@ __device__ __forceinline__ v3 bsdf_f_grad(const MatEval& m, v3 n, v3 wo, v3 wi, 
     const float a = r * r, a2 = a * a;
     const v3 h = normalize(wo + wi);
     const float ch = dot(n, h), vh = dot(wi, h);
-    const float k = ch * ch * (a2 - 1.0f) + 1.0f;
+    const float k = ggx_k(a2, ch, sin2(n, h));
     const float D = a2 / (PI_F * k * k);
     const float so = sqrtf(a2 + (1.0f - a2) * co * co), si = sqrtf(a2 + (1.0f - a2) * ci * ci);
     const float Go = 2.0f * co / (co + so), Gi = 2.0f * ci / (ci + si);
@@ -279,7 +286,7 @@ __device__ __forceinline__ float bsdf_pdf(const MatEval& m, v3 n, v3 wo, v3 wi) 
     const float ps = 0.5f * (1.0f + m.th[3]);
     const v3 h = normalize(wo + wi);
     const float ch = dot(n, h), oh = dot(wo, h);
-    const float pspec = oh > 0.0f ? ggx_d(a2, ch) * ch / (4.0f * oh) : 0.0f;
+    const float pspec = oh > 0.0f ? ggx_d(a2, ch, sin2(n, h)) * ch / (4.0f * oh) : 0.0f;
     return ps * pspec + (1.0f - ps) * ci * INV_PI_F;
 }
 
@@ -287,9 +294,9 @@ __device__ __forceinline__ float bsdf_pdf(const MatEval& m, v3 n, v3 wo, v3 wi) 
 __device__ __forceinline__ bool bsdf_sample(const MatEval& m, v3 n, v3 wo, float ul, float u1, float u2, v3& wi) {
     if (m.type == 1 && ul < 0.5f * (1.0f + m.th[3])) {
         const float a = m.th[4] * m.th[4], a2 = a * a;
-        const float t2 = a2 * u1 / (1.0f - u1);
-        const float ct = rsqrtf(1.0f + t2) ;
-        const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+        const float t2 = a2 * u1 / (1.0f - u1);       // tan^2 of the half-vector angle
+        const float ct = 1.0f / sqrtf(1.0f + t2);
+        const float st = sqrtf(t2) * ct;
         float s, c;
         sincospif(2.0f * u2, &s, &c);
         const v3 h = local_to_world(n, st * c, st * s, ct);

@@ -168,7 +168,7 @@ def test_radiance_box(torch_mod):
 def test_radiance_spiral_small(torch_mod):
     w = synth.workload_spiral(48, 40, 64, 16, 64, max_depth=5)
     ctx, pid = _ctx(torch_mod, w.scene)
-    frac, n = _sample_parity(ctx, pid, w.scene, w.init_tex, 3, 1, 7)
+    frac, n = _sample_parity(ctx, pid, w.scene, w.init_tex, 12, 1, 7)
     assert frac >= 0.9999, (frac, n)
     ctx.close()
 
