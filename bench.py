@@ -1,0 +1,413 @@
+"""Benchmark: paths/s and iterations/s of the meta-estimated inverse path tracing hot path,
+and time to a loss threshold for the meta-estimator vs plain fresh-sample MC with Adam.
+
+Workload (one optimisation iteration = one step, steps a1-a11 of the hot path):
+  spiral256: 256x256 image, procedural spiral tube of 8192 triangles over a ground quad,
+  principled BSDF with 256x256x5 fp32 textures (base colour, metalness, roughness; seeded
+  value-noise init and target), constant environment + 1 area light, max depth 5,
+  1 FD + 2 proportional spp per iteration (12 path traversals per pixel).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). With torchrun (N > 1) every rank optimises its own replica of
+the problem (different Philox key): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "paths/s, iters/s; time to loss threshold, meta-estimator vs plain MC, 1 GB300"
+PATHS_PER_PIXEL = 12            # 2 proportional x (primal, adjoint fwd, replay) + 1 FD pair x 6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--ttt-iters", type=int, default=600)
+    ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2309_15676_gb300 import synth
+    return synth.workload_spiral(256, 256, 256, 16, 256, max_depth=5, spp_prop=2, spp_fd=1)
+
+
+# ----------------------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback", 2070.0
+
+
+# ----------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, single thread, on a bounded sample of paths
+# ----------------------------------------------------------------------------------------
+def cpu_baseline(w, budget_s=15.0):
+    import numpy as np
+    from oracle import orc
+    sc = orc.Scene(w.scene)
+    tex = w.init_tex.astype(np.float64)
+    npix = w.scene["width"] * w.scene["height"]
+    rng = np.random.default_rng(0)
+    done_paths, elapsed, n = 0, 0.0, 8
+    adj = np.full((1, 3), 1e-3)
+    while elapsed < budget_s:
+        pix = rng.integers(0, npix, n).astype(np.uint32)
+        smp = rng.integers(0, 4, n).astype(np.uint32)
+        t0 = time.perf_counter()
+        orc.render_samples(sc, tex, pix, smp, 1, orc.ST_PROP_PRIMAL)          # primal traversals
+        orc.adjoint_samples(sc, tex, pix, smp, 1, orc.ST_PROP_ADJ,            # forward + replay traversals
+                            np.repeat(adj, n, 0))
+        dt = time.perf_counter() - t0
+        done_paths += 3 * n
+        elapsed += dt
+        n = int(min(4 * n, max(8, n * (budget_s - elapsed) / max(dt, 1e-3))))
+        if budget_s - elapsed < 0.5:
+            break
+    return {"value": done_paths / elapsed, "unit": "paths/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done_paths} path traversals (primal + PRB forward + replay) of the spiral256 scene, "
+                      f"random pixels, FP64 brute-force intersection, single thread, {elapsed:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands on this host's cores, same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle.build
+    oracle.build.build()
+    w = workload()
+    steps = []
+    for _ in range(max(args.warmup, 0)):
+        cpu_baseline(w, budget_s=1.0)
+    for _ in range(max(args.steps, 1)):
+        steps.append(cpu_baseline(w, budget_s=max(2.0, 60.0 / max(args.steps, 1))))
+    v = sum(s["value"] for s in steps) / len(steps)
+    iters = v / (PATHS_PER_PIXEL * w.scene["width"] * w.scene["height"])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "paths/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / iters, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "spiral256", "image": [256, 256], "triangles": 8192, "texture": [256, 256, 5],
+                       "max_depth": 5, "spp_prop": 2, "spp_fd": 1},
+            "iters_per_s": iters,
+            "cpu_baseline": {"value": v, "unit": "paths/s", "cores": 1, "kind": "oracle",
+                             "sample": steps[0]["sample"]},
+            "e2e": {"value": v, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+def l2_flush(torch, buf):
+    buf.zero_()            # 256 MiB > the 129 MB L2
+
+
+def eval_loss(torch, ctx, pid, target, spp=64):
+    img = ctx.render(pid, None, spp=spp, stream=5, iteration=0)
+    return float(((img - target) ** 2).mean())
+
+
+def time_to_threshold(torch, w, target_img, max_iters, lrs=(0.003, 0.01, 0.03)):
+    """Iterations and GPU time until the 64-spp eval loss drops below 10% of its initial value;
+    meta (1 FD + 2 proportional spp) vs Adam on 3 fresh proportional spp (equal spp per iteration)."""
+    from paper_2309_15676_gb300.api import Context, HyperParams, MODE_ADAM, MODE_META
+    out = {}
+    for name, mode, spp_prop, spp_fd in (("meta", MODE_META, 2, 1), ("adam", MODE_ADAM, 3, 0)):
+        best = None
+        for lr in lrs:
+            sc = dict(w.scene)
+            sc["spp_prop"], sc["spp_fd"] = spp_prop, spp_fd
+            ctx = Context(0)
+            pid = ctx.add_scene(sc, HyperParams(mode=mode, lr=lr))
+            ctx.set_target(pid, target_img)
+            ctx.set_params(pid, w.init_tex)
+            l0 = eval_loss(torch, ctx, pid, target_img)
+            thr = 0.1 * l0
+            gpu_ms, it, reached, last = 0.0, 0, None, l0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            while it < max_iters:
+                e0.record()
+                ctx.iterate(10, use_graph=True)
+                e1.record()
+                e1.synchronize()
+                gpu_ms += e0.elapsed_time(e1)
+                it += 10
+                last = eval_loss(torch, ctx, pid, target_img)
+                if last <= thr:
+                    reached = it
+                    break
+            r = {"lr": lr, "iters": reached, "gpu_s": gpu_ms / 1e3 if reached else None,
+                 "loss0": l0, "final_loss_ratio": last / l0, "iters_run": it}
+            ctx.close()
+            key = (0 if reached else 1, r["gpu_s"] if reached else r["final_loss_ratio"])
+            if best is None or key < best[0]:
+                best = (key, r)
+        out[name] = best[1]
+    out["threshold"] = "10% of the iteration-0 64-spp eval loss"
+    out["lr_grid"] = list(lrs)
+    return out
+
+
+def update_roofline(torch, hbm_peak, n=67_108_864, reps=10):
+    """Standalone fused update (META) at 67M parameters (a 256^3 x 4 volume): 64 B per parameter."""
+    from paper_2309_15676_gb300.api import HyperParams, meta_step_raw
+    g = torch.Generator(device="cuda").manual_seed(0)
+    mk = lambda: torch.rand(n, device="cuda", generator=g) * 0.01
+    pi, F, dF, m2f, m2d, mean, var = mk() + 0.5, mk(), mk(), mk() ** 2, mk() ** 2, mk(), mk() ** 2
+    ap = torch.rand(n, device="cuda", generator=g) * 0.5
+    nxt = torch.empty_like(pi)
+    h = HyperParams(lr=0.01)
+    lo, hi = [0, 0, 0, 0, 0.05], [1, 1, 1, 1, 1]
+    out = torch.zeros(1, device="cuda", dtype=torch.float64)
+    for _ in range(3):
+        meta_step_raw(h, pi, nxt, F, dF, m2f, m2d, mean, var, ap, 5, lo, hi, 5, 5, 3, 1e-4, False, out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        meta_step_raw(h, pi, nxt, F, dF, m2f, m2d, mean, var, ap, 5, lo, hi, 5, 5, 3, 1e-4, True, out)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        pi, nxt = nxt, pi
+    ms = sorted(ts)[len(ts) // 2]
+    byts = 64 * n
+    gbs = byts / (ms * 1e-3) / 1e9
+    del pi, F, dF, m2f, m2d, mean, var, ap, nxt
+    torch.cuda.empty_cache()
+    return {"kernel": "update (META, standalone)", "params": n, "bytes_per_launch": byts, "ms": ms,
+            "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
+
+
+def run_mine(args):
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2309_15676_gb300.api import Context, HyperParams
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hbm_peak, peak_kind, sm_max = measured_peaks()
+
+    w = workload()
+    sc = dict(w.scene)
+    sc["key_id"] = rank                       # independent replica per rank
+    ctx = Context(local, max_paths=1 << 20)     # queue capacity: 16 spp chunks for the target render
+    pid = ctx.add_scene(sc, HyperParams(lr=0.01))
+    ctx.render_target(pid, torch.from_numpy(w.target_tex).cuda(), 256)
+    ctx.set_params(pid, w.init_tex)
+    npix = sc["width"] * sc["height"]
+    paths_per_iter = ctx.stats(pid)["paths_per_iter"]
+    assert paths_per_iter == PATHS_PER_PIXEL * npix
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    # warm-up (captures the iteration graph)
+    ctx.iterate(max(args.warmup, 3), use_graph=True)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K graph-launched iterations, L2 flushed between them ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            l2_flush(torch, flush)
+            ev[k][0].record()
+            ctx.iterate(1, use_graph=True)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    launches_per_iter = ctx.launch_count()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * paths_per_iter * args.steps / (ms_max * 1e-3)
+    iters_per_s = world * args.steps / (ms_max * 1e-3)
+
+    # ---- per-kernel breakdown: event-timed launches of the same iteration (no graph) ----
+    blob = ctx.checkpoint_save()
+    ctx.profile(True)
+    n_prof = 3
+    for _ in range(n_prof):
+        l2_flush(torch, flush)
+        ctx.iterate(1, use_graph=False)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.checkpoint_load(blob)
+    tot = sum(v["ms"] for v in prof.values())
+    kernels = {k: {"launches_per_iter": v["launches"] / n_prof, "ms_per_iter": v["ms"] / n_prof,
+                   "share": v["ms"] / tot, "units_per_iter": v["units"] / n_prof} for k, v in prof.items()}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_iter"])
+
+    # ---- rooflines ----
+    rooflines = []
+    if "scatter" in prof:
+        p = prof["scatter"]
+        rec_bytes = 4 + 4 * (2 + sc["tex_c"])
+        per_launch_units = p["units"] / p["launches"]
+        byts = per_launch_units * rec_bytes + 2 * 4 * sc["tex_h"] * sc["tex_w"] * sc["tex_c"]
+        avg_ms = p["ms"] / p["launches"]
+        gbs = byts / (avg_ms * 1e-3) / 1e9
+        rooflines.append({"kernel": "scatter", "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": gbs / hbm_peak, "bytes_per_launch": byts, "records_per_launch": per_launch_units,
+                          "ms": avg_ms})
+    if "update" in prof:
+        p = prof["update"]
+        byts = 64 * p["units"] / p["launches"]
+        avg_ms = p["ms"] / p["launches"]
+        gbs = byts / (avg_ms * 1e-3) / 1e9
+        rooflines.append({"kernel": "update", "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": gbs / hbm_peak, "bytes_per_launch": byts, "ms": avg_ms,
+                          "note": "327,680 params (21 MB) stay L2-resident at this size"})
+    upd67 = update_roofline(torch, hbm_peak) if rank == 0 else None
+    # dominant kernel: FP32 issue-bound traversal/shading; peak = FP32 lanes x 2 x max SM clock
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    dk = prof[dom]
+    roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
+            "traffic": None, "ms_per_launch": dk["ms"] / dk["launches"], "share": kernels[dom]["share"],
+            "rays_per_s": dk["units"] / (dk["ms"] * 1e-3)}
+    if dom in ("update", "scatter"):
+        rr = [r for r in rooflines if r["kernel"] == dom][0]
+        roof = dict(rr, traffic=None, share=kernels[dom]["share"])
+
+    # ---- e2e through the public API with host buffers ----
+    # the target image (same counters as the stored target) staged in pinned host memory
+    target_img = ctx.render(pid, torch.from_numpy(w.target_tex).cuda(), spp=256, stream=4, iteration=0)
+    tgt_host = target_img.cpu().pin_memory()
+    ctx.checkpoint_load(blob)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_target_host(pid, tgt_host)          # H2D of the step's input
+        ctx.iterate(1, use_graph=True)
+        ctx.stats(pid)                              # D2H of the step's result (loss)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * paths_per_iter * args.steps / e2e_s, "unit": "paths/s",
+           "h2d_bytes_per_step": int(tgt_host.numel() * 4), "d2h_bytes_per_step": 48,
+           "iters_per_s": world * args.steps / e2e_s}
+    ctx.close()
+
+    cpu = None
+    ttt = None
+    if rank == 0 and not args.no_ttt:
+        ttt = time_to_threshold(torch, w, target_img, args.ttt_iters)
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "spiral256", "image": [256, 256], "triangles": 8192,
+                           "texture": [256, 256, 5], "max_depth": 5, "spp_prop": 2, "spp_fd": 1,
+                           "paths_per_iter": paths_per_iter, "l2": "flushed (256 MiB write) between timed steps",
+                           "parallelism": f"replicas x{world}"},
+                "iters_per_s": iters_per_s,
+                "roofline": roof, "rooflines": rooflines + ([upd67] if upd67 else []),
+                "kernels": kernels, "peak_source": peak_kind,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "gpu_launches": int(launches_per_iter * args.steps),
+                "time_to_threshold": ttt}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -230,6 +230,21 @@ mer_status mer_autotune(mer_ctx* ctx, int32_t trial_iters, char* desc, size_t de
  * per iteration (for launch accounting). */
 mer_status mer_launch_count(mer_ctx* ctx, int64_t* launches_per_iter);
 
+/* Per-kernel timing (diagnostic). While enabled, every launch of the wavefront, scatter, loss and
+ * update kernels made outside graph capture (by ctx, or by mer_meta_step_raw) is bracketed by CUDA
+ * events on the stream it is launched on, and pass counters are read back after each pass (this
+ * synchronises). Not for concurrent use from several threads. */
+typedef struct mer_kernel_time {
+    char name[32];
+    int64_t launches;
+    int64_t units;     /* work items: rays (extend/shade/shadow), records (scatter), parameters (update),
+                          paths (resolve), pixels (loss) */
+    double total_ms;   /* sum of event-measured launch durations */
+} mer_kernel_time;
+mer_status mer_profile_enable(mer_ctx* ctx, int32_t enable);
+/* Synchronises, writes up to max_entries launch classes that ran (in a fixed order) and clears them. */
+mer_status mer_profile_read(mer_ctx* ctx, mer_kernel_time* out, int32_t max_entries, int32_t* n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,10 @@ class StateView(ct.Structure):
                [("n", ct.c_int64)]
 
 
+class KernelTime(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("units", ct.c_int64), ("total_ms", ct.c_double)]
+
+
 # name -> (restype, argtypes); every symbol mer.h declares
 SIGNATURES = {
     "mer_hyper_default": (ct.c_int, [ct.POINTER(Hyper)]),
@@ -92,6 +96,8 @@ SIGNATURES = {
     "mer_checkpoint_load": (ct.c_int, [_vp, _vp, ct.c_size_t]),
     "mer_autotune": (ct.c_int, [_vp, ct.c_int32, ct.c_char_p, ct.c_size_t]),
     "mer_launch_count": (ct.c_int, [_vp, ct.POINTER(ct.c_int64)]),
+    "mer_profile_enable": (ct.c_int, [_vp, ct.c_int32]),
+    "mer_profile_read": (ct.c_int, [_vp, ct.POINTER(KernelTime), ct.c_int32, ct.POINTER(ct.c_int32)]),
 }
 
 _lib = None

@@ -244,6 +244,16 @@ class Context:
             out[name] = t
         return out
 
+    def profile(self, enable: bool = True):
+        self._ck(self.L.mer_profile_enable(self.h, int(enable)))
+
+    def profile_read(self) -> dict:
+        arr = (_lib.KernelTime * 32)()
+        n = ct.c_int32()
+        self._ck(self.L.mer_profile_read(self.h, arr, 32, ct.byref(n)))
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, units=arr[i].units, ms=arr[i].total_ms)
+                for i in range(n.value)}
+
     def launch_count(self) -> int:
         n = ct.c_int64()
         self._ck(self.L.mer_launch_count(self.h, ct.byref(n)))

@@ -74,11 +74,84 @@ struct mer_ctx {
     bool graph_dirty = true;
     LaunchShape shape{128, 0, 0, 1};
     int64_t launches = 0;
+    void* timer = nullptr;      // EventTimer while profiling
 };
 
 namespace {
 
 thread_local std::string t_err = "no error";
+
+const char* const kClassNames[KC_COUNT] = {
+    "extend_1", "shade_1_primal", "shade_1_replay", "shadow_1_primal", "shadow_1_replay",
+    "extend_2", "shade_2_primal", "shade_2_replay", "shadow_2_primal", "shadow_2_replay",
+    "resolve", "l2_loss", "scatter", "update", "update_finalize"};
+
+// CUDA-event timer installed in mer::g_timer while profiling is enabled
+struct EventTimer : KernelTimer {
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    int64_t units[KC_COUNT] = {0};
+    cudaEvent_t get() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    void before(int cls, cudaStream_t st) override {
+        Rec r{cls, get(), nullptr};
+        cudaEventRecord(r.a, st);
+        recs.push_back(r);
+    }
+    void after(int cls, cudaStream_t st) override {
+        (void)cls;
+        recs.back().b = get();
+        cudaEventRecord(recs.back().b, st);
+    }
+    void add_units(int cls, int64_t n) override { units[cls] += n; }
+    void read(mer_kernel_time* out, int max, int* n_out) {
+        double ms[KC_COUNT] = {0};
+        int64_t cnt[KC_COUNT] = {0};
+        for (Rec& r : recs) {
+            cudaEventSynchronize(r.b);
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, r.a, r.b);
+            ms[r.cls] += t;
+            cnt[r.cls]++;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+        int k = 0;
+        for (int c = 0; c < KC_COUNT; ++c) {
+            if (!cnt[c]) continue;
+            if (k < max) {
+                memset(&out[k], 0, sizeof out[k]);
+                snprintf(out[k].name, sizeof out[k].name, "%s", kClassNames[c]);
+                out[k].launches = cnt[c];
+                out[k].units = units[c];
+                out[k].total_ms = ms[c];
+            }
+            ++k;
+        }
+        for (int64_t& u : units) u = 0;
+        *n_out = std::min(k, max);
+    }
+    ~EventTimer() override {
+        for (Rec& r : recs) {
+            cudaEventDestroy(r.a);
+            if (r.b) cudaEventDestroy(r.b);
+        }
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
 
 mer_status failv(mer_ctx* c, int code, const char* fmt, va_list ap) {
     char buf[1024];
@@ -210,7 +283,23 @@ LaunchShape shape_of(mer_ctx* c) {
 int pass(mer_ctx* c, PassArgs A, int nb, int mode, int maxD) {
     cudaMemsetAsync(c->cnt, 0, CNT_ERR * sizeof(uint32_t), c->st);
     const LaunchShape L = shape_of(c);
-    return 1 + run_pass(A, nb, mode, maxD, L, c->st);
+    const int n = 1 + run_pass(A, nb, mode, maxD, L, c->st);
+    if (g_timer) {
+        // work items of this pass: rays per depth and NEE rays, read back from the pass counters
+        uint32_t h[CNT_WORDS];
+        cudaMemcpyAsync(h, c->cnt, sizeof h, cudaMemcpyDeviceToHost, c->st);
+        cudaStreamSynchronize(c->st);
+        int64_t rays = A.n_paths, sh = 0;
+        for (int k = 2; k <= maxD; ++k) rays += h[CNT_Q + k];
+        for (int k = 1; k <= maxD; ++k) sh += h[CNT_S + k];
+        const int base = nb == 1 ? KC_EXTEND1 : KC_EXTEND2;
+        const int rep = mode == MODE_REPLAY ? 1 : 0;
+        g_timer->add_units(base, rays);
+        g_timer->add_units(base + 1 + rep, rays);
+        g_timer->add_units(base + 3 + rep, sh);
+        if (mode == MODE_REPLAY) g_timer->add_units(KC_SCATTER, h[CNT_R]);
+    }
+    return n;
 }
 
 // the gradient part of one iteration for all problems (steps a1-a10)
@@ -263,6 +352,8 @@ int enqueue_gradient(mer_ctx* c) {
 }
 
 int enqueue_update(mer_ctx* c) {
+    if (g_timer)
+        for (Problem* p : c->probs) g_timer->add_units(KC_UPDATE, p->n_par);
     launch_update_ctx(c->d_segs, c->d_blk_off, (int)c->probs.size(), c->upd_blocks, c->d_pstate, c->d_partials, c->st);
     return 2;
 }
@@ -448,6 +539,7 @@ void mer_destroy(mer_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->st) cudaStreamSynchronize(c->st);
+    mer_profile_enable(c, 0);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (Problem* p : c->probs) {
         for (void* a : p->allocs) dfree(a);
@@ -925,10 +1017,13 @@ mer_status mer_iterate(mer_ctx* c, int32_t n_iters, int32_t use_graph) {
             c->gexec = nullptr;
         }
         cudaGraph_t graph = nullptr;
+        KernelTimer* saved_timer = g_timer;
+        g_timer = nullptr;   // no event timing inside a captured graph
         CK(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
         int n = enqueue_gradient(c);
         n += enqueue_update(c);
         cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+        g_timer = saved_timer;
         if (e) return fail(c, MER_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&c->gexec, graph, 0);
         cudaGraphDestroy(graph);
@@ -984,6 +1079,31 @@ mer_status mer_state_get(mer_ctx* c, int32_t pid, mer_state_view* out) {
     out->var = p->var;
     out->alpha_prev = p->ap;
     out->n = p->n_par;
+    return MER_OK;
+}
+
+mer_status mer_profile_enable(mer_ctx* c, int32_t enable) {
+    if (!c) return fail(c, MER_ERR_INVALID_ARG, "null context");
+    if (enable && !c->timer) {
+        EventTimer* t = new EventTimer();
+        c->timer = t;
+        g_timer = t;
+    } else if (!enable && c->timer) {
+        EventTimer* t = (EventTimer*)c->timer;
+        if (g_timer == t) g_timer = nullptr;
+        delete t;
+        c->timer = nullptr;
+    }
+    return MER_OK;
+}
+
+mer_status mer_profile_read(mer_ctx* c, mer_kernel_time* out, int32_t max_entries, int32_t* n_out) {
+    if (!c || !out || !n_out || max_entries < 0) return fail(c, MER_ERR_INVALID_ARG, "bad arguments");
+    if (!c->timer) return fail(c, MER_ERR_STATE, "profiling is not enabled");
+    cudaSetDevice(c->device);
+    int n = 0;
+    ((EventTimer*)c->timer)->read(out, max_entries, &n);
+    *n_out = n;
     return MER_OK;
 }
 

@@ -4,6 +4,8 @@
 
 namespace mer {
 
+KernelTimer* g_timer = nullptr;
+
 constexpr unsigned FULLM = 0xffffffffu;
 
 // sum of v over the lanes of `peers` (lanes listed in vmask all call this); every lane gets
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cn
 
 int run_scatter(const uint32_t* cnt, const uint32_t* rpos, const float* rf, int64_t rcap, const ProblemDev* probs,
                 float* grad_over, int which, int grid, cudaStream_t st) {
-    k_scatter<<<grid, 256, 0, st>>>(cnt, rpos, rf, rcap, probs, grad_over, which);
+    MER_TIMED(KC_SCATTER, st, k_scatter<<<grid, 256, 0, st>>>(cnt, rpos, rf, rcap, probs, grad_over, which));
     return 1;
 }
 
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs
 
 int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int with_fd,
            double* loss_acc, int grid, cudaStream_t st) {
-    k_l2<<<grid, 256, 0, st>>>(probs, pix_pref, n_probs, total_pix, with_fd, loss_acc);
+    MER_TIMED(KC_L2, st, k_l2<<<grid, 256, 0, st>>>(probs, pix_pref, n_probs, total_pix, with_fd, loss_acc));
     return 1;
 }
 

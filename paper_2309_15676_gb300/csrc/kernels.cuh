@@ -5,6 +5,29 @@
 
 namespace mer {
 
+// launch classes for the optional per-kernel event timing
+enum KernelClass {
+    KC_EXTEND1, KC_SHADE1_PRIMAL, KC_SHADE1_REPLAY, KC_SHADOW1_PRIMAL, KC_SHADOW1_REPLAY,
+    KC_EXTEND2, KC_SHADE2_PRIMAL, KC_SHADE2_REPLAY, KC_SHADOW2_PRIMAL, KC_SHADOW2_REPLAY,
+    KC_RESOLVE, KC_L2, KC_SCATTER, KC_UPDATE, KC_UPDATE_FIN, KC_COUNT
+};
+
+// records CUDA events around launches when installed (diagnostic mode, one thread)
+struct KernelTimer {
+    virtual void before(int cls, cudaStream_t st) = 0;
+    virtual void after(int cls, cudaStream_t st) = 0;
+    virtual void add_units(int cls, int64_t n) = 0;
+    virtual ~KernelTimer() {}
+};
+extern KernelTimer* g_timer;
+
+#define MER_TIMED(cls, st, ...)                       \
+    do {                                              \
+        if (g_timer) g_timer->before((cls), (st));    \
+        __VA_ARGS__;                                  \
+        if (g_timer) g_timer->after((cls), (st));     \
+    } while (0)
+
 struct PassArgs;
 struct LaunchShape {
     int block;        // threads per block of the wavefront kernels (<= 256)

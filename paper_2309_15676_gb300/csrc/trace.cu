@@ -856,9 +856,11 @@ static void launch_depth(const PassArgs& A, int depth, const LaunchShape& L, cud
         g_sd = persistent_grid(k_shadow<NB, MODE>, L, smem);
         last = L;
     }
-    k_extend<NB><<<g_ext, L.block, smem, st>>>(B, depth);
-    k_shade<NB, MODE><<<g_sh, L.block, 0, st>>>(B, depth);
-    k_shadow<NB, MODE><<<g_sd, L.block, smem, st>>>(B, depth);
+    const int base = NB == 1 ? KC_EXTEND1 : KC_EXTEND2;
+    const int rep = MODE == MODE_REPLAY ? 1 : 0;
+    MER_TIMED(base, st, k_extend<NB><<<g_ext, L.block, smem, st>>>(B, depth));
+    MER_TIMED(base + 1 + rep, st, k_shade<NB, MODE><<<g_sh, L.block, 0, st>>>(B, depth));
+    MER_TIMED(base + 3 + rep, st, k_shadow<NB, MODE><<<g_sd, L.block, smem, st>>>(B, depth));
 }
 
 // enqueues one full pass; returns the number of kernel launches
@@ -878,8 +880,8 @@ int run_pass(const PassArgs& A, int nb, int mode, int max_depth, const LaunchSha
 }
 
 int run_resolve(const PassArgs& A, int nb, float* img0, float* img1, int accumulate, int grid, cudaStream_t st) {
-    if (nb == 1) k_resolve<1><<<grid, 256, 0, st>>>(A, img0, img1, accumulate);
-    else k_resolve<2><<<grid, 256, 0, st>>>(A, img0, img1, accumulate);
+    if (nb == 1) MER_TIMED(KC_RESOLVE, st, k_resolve<1><<<grid, 256, 0, st>>>(A, img0, img1, accumulate));
+    else MER_TIMED(KC_RESOLVE, st, k_resolve<2><<<grid, 256, 0, st>>>(A, img0, img1, accumulate));
     return 1;
 }
 

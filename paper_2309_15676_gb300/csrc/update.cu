@@ -14,6 +14,7 @@
 #include <mutex>
 #include <vector>
 
+#include "kernels.cuh"
 #include "update.cuh"
 
 namespace mer {
@@ -251,15 +252,19 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_finalize_raw(const doubl
 cudaError_t launch_update_ctx(const UpdSeg* segs_dev, const int64_t* blk_off_dev, int n_segs, int64_t total_blocks,
                               ProbState* ps, double* partials, cudaStream_t st) {
     if (total_blocks <= 0) return cudaSuccess;
-    k_update_ctx<<<(unsigned)total_blocks, UPD_THREADS, 0, st>>>(segs_dev, blk_off_dev, n_segs, ps, partials);
-    k_update_finalize_ctx<<<n_segs, UPD_THREADS, 0, st>>>(segs_dev, blk_off_dev, ps, partials);
+    MER_TIMED(KC_UPDATE, st,
+              k_update_ctx<<<(unsigned)total_blocks, UPD_THREADS, 0, st>>>(segs_dev, blk_off_dev, n_segs, ps, partials));
+    MER_TIMED(KC_UPDATE_FIN, st, k_update_finalize_ctx<<<n_segs, UPD_THREADS, 0, st>>>(segs_dev, blk_off_dev, ps, partials));
     return cudaGetLastError();
 }
 
 cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int count_d, double n2, double* partials,
                               int64_t nblocks, double* out, cudaStream_t st) {
-    if (nblocks > 0) k_update_raw<<<(unsigned)nblocks, UPD_THREADS, 0, st>>>(S, iteration, count_f, count_d, n2, partials);
-    k_update_finalize_raw<<<1, UPD_THREADS, 0, st>>>(partials, nblocks, out);
+    if (g_timer) g_timer->add_units(KC_UPDATE, S.n);
+    if (nblocks > 0)
+        MER_TIMED(KC_UPDATE, st,
+                  k_update_raw<<<(unsigned)nblocks, UPD_THREADS, 0, st>>>(S, iteration, count_f, count_d, n2, partials));
+    MER_TIMED(KC_UPDATE_FIN, st, k_update_finalize_raw<<<1, UPD_THREADS, 0, st>>>(partials, nblocks, out));
     return cudaGetLastError();
 }
 
