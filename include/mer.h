@@ -211,6 +211,26 @@ mer_status mer_meta_step_raw(const mer_hyper* hyper, int64_t n, int32_t C, const
                              int32_t count_d, double dpi_norm2, int32_t zero_grads, double* dpi_norm2_out,
                              void* cuda_stream);
 
+/* The same update as mer_meta_step_raw, for callers that must not allocate device memory:
+ * code running while a stream is being captured into a CUDA graph, applications that reserve
+ * all device memory up front or hand it out through their own pool, and real-time loops where
+ * an allocation (and the device synchronisation that freeing implies) is not allowed.
+ * The paper has no counterpart; this is an interface variant only.
+ * Arguments, layout, results and tolerances are exactly those of mer_meta_step_raw.
+ * Scratch: the per-block partial norms go to a fixed array compiled into the library (512 KiB
+ * of device memory on every GPU that loads it, held until the process exits), so n may be at
+ * most 268,435,456 parameters; larger n fails with MER_ERR_INVALID_ARG. It calls no cudaMalloc,
+ * cudaFree or other allocating routine. The first call on a device looks up the array's device
+ * address once (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture. All calls share the one array: calls that overlap on the GPU (different
+ * streams, no ordering between them) race and give wrong norms; calls ordered on one stream are
+ * safe. Nothing in the array needs to start at zero (every call writes all the entries it reads). */
+mer_status mer_meta_step_raw_noalloc(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
+                                     const float* pi, float* pi_next, float* F, float* dF, float* m2f, float* m2d,
+                                     float* mean, float* var, float* alpha_prev, int32_t iteration, int32_t count_f,
+                                     int32_t count_d, double dpi_norm2, int32_t zero_grads, double* dpi_norm2_out,
+                                     void* cuda_stream);
+
 /* Philox4x32-10 of n counters: ctr_dev [n][4] u32, out_dev [n][4] u32, key (k0, k1). */
 mer_status mer_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr_dev, int64_t n, uint32_t* out_dev,
                       void* cuda_stream);

@@ -91,6 +91,9 @@ SIGNATURES = {
     "mer_meta_step_raw": (ct.c_int, [ct.POINTER(Hyper), ct.c_int64, ct.c_int32, _fp, _fp, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp, _vp, _vp, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_double,
                                      ct.c_int32, _vp, _vp]),
+    "mer_meta_step_raw_noalloc": (ct.c_int, [ct.POINTER(Hyper), ct.c_int64, ct.c_int32, _fp, _fp, _vp, _vp, _vp,
+                                             _vp, _vp, _vp, _vp, _vp, _vp, ct.c_int32, ct.c_int32, ct.c_int32,
+                                             ct.c_double, ct.c_int32, _vp, _vp]),
     "mer_philox": (ct.c_int, [ct.c_uint32, ct.c_uint32, _vp, ct.c_int64, _vp, _vp]),
     "mer_checkpoint_save": (ct.c_int, [_vp, _vp, ct.POINTER(ct.c_size_t)]),
     "mer_checkpoint_load": (ct.c_int, [_vp, _vp, ct.c_size_t]),

@@ -480,6 +480,13 @@ int64_t chunk_spp(mer_ctx* c, Problem* p, int spp) {
 
 }  // namespace
 
+namespace mer {
+int mer_internal_fail(int code, const char* msg) {
+    t_err = msg;
+    return code;
+}
+}  // namespace mer
+
 // =====================================================================================
 // exported entry points
 // =====================================================================================

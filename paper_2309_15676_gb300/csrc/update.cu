@@ -11,6 +11,7 @@
 // in `m2f`. Both modes write pi' into the other parameter slot, clear F and dF, and reduce
 // ||pi' - pi||^2 per problem deterministically (per-block partials, fixed-order sum).
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -268,4 +269,78 @@ cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int c
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free form of the standalone update. Its only scratch is the per-block partial
+// sums of ||pi' - pi||^2; here they live in a fixed file-scope device array instead of a
+// buffer the library allocates. Every GPU that loads the library holds this array (512 KiB)
+// until the process exits.
+// ---------------------------------------------------------------------------------------
+constexpr int64_t NOALLOC_MAX_BLOCKS = 65536;   // -> at most 65536 * UPD_CHUNK parameters
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_BLOCKS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+int64_t noalloc_max_params() { return NOALLOC_MAX_BLOCKS * UPD_CHUNK; }
+
 }  // namespace mer
+
+extern "C" mer_status mer_meta_step_raw_noalloc(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo,
+                                                const float* hi, const float* pi, float* pi_next, float* F,
+                                                float* dF, float* m2f, float* m2d, float* mean, float* var,
+                                                float* alpha_prev, int32_t iteration, int32_t count_f,
+                                                int32_t count_d, double dpi_norm2, int32_t zero_grads,
+                                                double* dpi_norm2_out, void* cuda_stream) {
+    using namespace mer;
+    if (!hyper || n < 0 || C < 1 || C > 8 || !lo || !hi || !dpi_norm2_out)
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_meta_step_raw_noalloc");
+    const bool meta = hyper->mode == MER_MODE_META;
+    if (n > 0 && (!pi || !pi_next || !F || !m2f || !mean || (meta && (!dF || !m2d || !var || !alpha_prev))))
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "missing arrays in mer_meta_step_raw_noalloc");
+    const void* ptrs[] = {pi, pi_next, F, dF, m2f, m2d, mean, var, alpha_prev};
+    for (const void* q : ptrs)
+        if (q && ((uintptr_t)q & 15u))
+            return mer_internal_fail(MER_ERR_INVALID_ARG, "mer_meta_step_raw_noalloc: arrays must be 16-byte aligned");
+    if (pi == pi_next && n > 0)
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "mer_meta_step_raw_noalloc: pi_next may not alias pi");
+    const int64_t nb = update_blocks_for(n);
+    if (nb > NOALLOC_MAX_BLOCKS)
+        return mer_internal_fail(MER_ERR_INVALID_ARG,
+                                 "mer_meta_step_raw_noalloc: n exceeds the fixed scratch (at most 268435456 parameters)");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return mer_internal_fail(MER_ERR_CUDA, "mer_meta_step_raw_noalloc: no usable current device");
+    double* scratch = nullptr;
+    {
+        // once per device, with that device current: the array's device address
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            double* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
+            if (e != cudaSuccess || !p)
+                return mer_internal_fail(MER_ERR_CUDA, "mer_meta_step_raw_noalloc: cudaGetSymbolAddress failed");
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    UpdSeg S;
+    memset(&S, 0, sizeof S);
+    S.pA = const_cast<float*>(pi);
+    S.pB = pi_next;
+    S.F = F; S.dF = dF; S.m2f = m2f; S.m2d = m2d; S.mean = mean; S.var = var; S.ap = alpha_prev;
+    S.n = n;
+    S.C = C;
+    S.zero_grads = zero_grads;
+    for (int k = 0; k < C; ++k) {
+        S.lo[k] = lo[k];
+        S.hi[k] = hi[k];
+    }
+    S.hyper = *hyper;
+    // every block writes its own partial before the finalize kernel reads it, so nothing in the
+    // shared array has to start at zero
+    const cudaError_t e = launch_update_raw(S, iteration, count_f, count_d, dpi_norm2, scratch, nb, dpi_norm2_out,
+                                            (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e));
+    return MER_OK;
+}

@@ -25,6 +25,8 @@ struct UpdSeg {
 };
 
 int64_t update_blocks_for(int64_t n);
+// records a context-free error message (thread-local) and returns code
+int mer_internal_fail(int code, const char* msg);
 cudaError_t launch_update_ctx(const UpdSeg* segs_dev, const int64_t* blk_off_dev, int n_segs, int64_t total_blocks,
                               ProbState* ps, double* partials, cudaStream_t st);
 cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int count_d, double n2, double* partials,
