@@ -257,10 +257,14 @@ mer_status mer_launch_count(mer_ctx* ctx, int64_t* launches_per_iter);
 typedef struct mer_kernel_time {
     char name[32];
     int64_t launches;
-    int64_t units;     /* work items: rays (extend/shade/shadow), records (scatter), parameters (update),
-                          paths (resolve), pixels (loss) */
-    double total_ms;   /* sum of event-measured launch durations */
+    int64_t units;      /* work items: rays (extend/shade/shadow), records (scatter), parameters (update),
+                           paths (resolve), pixels (loss) */
+    double total_ms;    /* sum of event-measured launch durations (timing mode) */
+    int64_t node_tests; /* counting mode: BVH node tests (two child boxes each) of extend/shadow */
+    int64_t prim_tests; /* counting mode: triangle and sphere tests of extend/shadow */
 } mer_kernel_time;
+/* enable: 0 off, 1 timing (events around launches), 2 counting (traversal kernels count their
+ * node and primitive tests; launches are not timed). */
 mer_status mer_profile_enable(mer_ctx* ctx, int32_t enable);
 /* Synchronises, writes up to max_entries launch classes that ran (in a fixed order) and clears them. */
 mer_status mer_profile_read(mer_ctx* ctx, mer_kernel_time* out, int32_t max_entries, int32_t* n_out);

@@ -63,7 +63,8 @@ class StateView(ct.Structure):
 
 
 class KernelTime(ct.Structure):
-    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("units", ct.c_int64), ("total_ms", ct.c_double)]
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("units", ct.c_int64), ("total_ms", ct.c_double),
+                ("node_tests", ct.c_int64), ("prim_tests", ct.c_int64)]
 
 
 # name -> (restype, argtypes); every symbol mer.h declares

@@ -244,14 +244,16 @@ class Context:
             out[name] = t
         return out
 
-    def profile(self, enable: bool = True):
-        self._ck(self.L.mer_profile_enable(self.h, int(enable)))
+    def profile(self, mode: int = 1):
+        """0 off, 1 event timing of every launch, 2 counting of traversal tests."""
+        self._ck(self.L.mer_profile_enable(self.h, int(mode)))
 
     def profile_read(self) -> dict:
         arr = (_lib.KernelTime * 32)()
         n = ct.c_int32()
         self._ck(self.L.mer_profile_read(self.h, arr, 32, ct.byref(n)))
-        return {arr[i].name.decode(): dict(launches=arr[i].launches, units=arr[i].units, ms=arr[i].total_ms)
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, units=arr[i].units, ms=arr[i].total_ms,
+                                           node_tests=arr[i].node_tests, prim_tests=arr[i].prim_tests)
                 for i in range(n.value)}
 
     def launch_count(self) -> int:

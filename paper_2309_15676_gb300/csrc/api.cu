@@ -33,6 +33,22 @@ struct Problem {
     float *dimgA = nullptr, *dimgB = nullptr;
 };
 
+// one set of wavefront buffers (a pass in flight uses one set)
+struct Wave {
+    int64_t qcap = 0, shcap = 0, rcap = 0;
+    float* qf[2] = {nullptr, nullptr};
+    uint32_t* qu[2] = {nullptr, nullptr};
+    float* hitf = nullptr;
+    int32_t* hitp = nullptr;
+    float* shf = nullptr;
+    uint32_t* shu = nullptr;
+    uint32_t* cnt = nullptr;       // pass counters + error word
+    float* lacc = nullptr;
+    float* ltot = nullptr;
+    uint32_t* rpos = nullptr;
+    float* rf = nullptr;
+};
+
 struct mer_ctx {
     int device = 0;
     cudaStream_t user = nullptr;   // caller's stream
@@ -51,19 +67,13 @@ struct mer_ctx {
     int32_t n_fd = 0;
     int64_t P_prop = 0, P_fd = 0, total_pix = 0;
     int32_t maxD_prop = 0, maxD_fd = 0, maxD = 0;
-    // wavefront buffers
-    int64_t qcap = 0, shcap = 0, rcap = 0;
-    float* qf[2] = {nullptr, nullptr};
-    uint32_t* qu[2] = {nullptr, nullptr};
-    float* hitf = nullptr;
-    int32_t* hitp = nullptr;
-    float* shf = nullptr;
-    uint32_t* shu = nullptr;
-    uint32_t* cnt = nullptr;
-    float* lacc = nullptr;
-    float* ltot = nullptr;
-    uint32_t* rpos = nullptr;
-    float* rf = nullptr;
+    // wavefront buffers: set 0 (proportional passes, API calls) and set 1 (FD-pair passes)
+    // wave sets: 0 proportional primal + replay (and API calls), 1 FD primal + replay,
+    // 2 proportional PRB radiance pass, 3 FD PRB radiance pass
+    Wave w[4];
+    cudaStream_t sx[3] = {nullptr, nullptr, nullptr};   // extra internal streams for concurrent passes
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[3] = {nullptr, nullptr, nullptr};
     // update
     UpdSeg* d_segs = nullptr;
     int64_t* d_blk_off = nullptr;
@@ -75,6 +85,8 @@ struct mer_ctx {
     LaunchShape shape{128, 0, 0, 1};
     int64_t launches = 0;
     void* timer = nullptr;      // EventTimer while profiling
+    bool counting = false;      // profiling mode 2: traversal kernels count their tests
+    unsigned long long* d_stats = nullptr;
 };
 
 namespace {
@@ -116,7 +128,7 @@ struct EventTimer : KernelTimer {
         cudaEventRecord(recs.back().b, st);
     }
     void add_units(int cls, int64_t n) override { units[cls] += n; }
-    void read(mer_kernel_time* out, int max, int* n_out) {
+    void read(mer_kernel_time* out, int max, int* n_out, const unsigned long long* stats) {
         double ms[KC_COUNT] = {0};
         int64_t cnt[KC_COUNT] = {0};
         for (Rec& r : recs) {
@@ -131,13 +143,18 @@ struct EventTimer : KernelTimer {
         recs.clear();
         int k = 0;
         for (int c = 0; c < KC_COUNT; ++c) {
-            if (!cnt[c]) continue;
+            const bool counted = stats && (stats[2 * c] || stats[2 * c + 1]);
+            if (!cnt[c] && !counted && !units[c]) continue;
             if (k < max) {
                 memset(&out[k], 0, sizeof out[k]);
                 snprintf(out[k].name, sizeof out[k].name, "%s", kClassNames[c]);
                 out[k].launches = cnt[c];
                 out[k].units = units[c];
                 out[k].total_ms = ms[c];
+                if (stats) {
+                    out[k].node_tests = (int64_t)stats[2 * c];
+                    out[k].prim_tests = (int64_t)stats[2 * c + 1];
+                }
             }
             ++k;
         }
@@ -206,44 +223,57 @@ struct Guard {
     ~Guard() { leave(c); }
 };
 
-void free_wavefront(mer_ctx* c) {
+void free_wave(Wave& w) {
     for (int i = 0; i < 2; ++i) {
-        dfree(c->qf[i]);
-        dfree(c->qu[i]);
-        c->qf[i] = nullptr;
-        c->qu[i] = nullptr;
+        dfree(w.qf[i]);
+        dfree(w.qu[i]);
     }
-    dfree(c->hitf); dfree(c->hitp); dfree(c->shf); dfree(c->shu); dfree(c->lacc); dfree(c->ltot);
-    dfree(c->rpos); dfree(c->rf);
-    c->hitf = nullptr; c->hitp = nullptr; c->shf = nullptr; c->shu = nullptr; c->lacc = nullptr;
-    c->ltot = nullptr; c->rpos = nullptr; c->rf = nullptr;
-    c->qcap = c->shcap = c->rcap = 0;
+    dfree(w.hitf); dfree(w.hitp); dfree(w.shf); dfree(w.shu); dfree(w.lacc); dfree(w.ltot);
+    dfree(w.rpos); dfree(w.rf); dfree(w.cnt);
+    w = Wave();
 }
 
+void free_wavefront(mer_ctx* c) {
+    for (Wave& w : c->w) free_wave(w);
+}
+
+mer_status alloc_wave(mer_ctx* c, Wave& w, int64_t Q, int64_t R) {
+    const int64_t S = 2 * Q;
+    for (int i = 0; i < 2; ++i) {
+        CK(c, dalloc(&w.qf[i], (size_t)(2 * QF_PER_BRANCH) * Q));
+        CK(c, dalloc(&w.qu[i], (size_t)QU_WORDS * Q));
+    }
+    CK(c, dalloc(&w.hitf, (size_t)(2 * HF_PER_BRANCH) * Q));
+    CK(c, dalloc(&w.hitp, (size_t)2 * Q));
+    CK(c, dalloc(&w.shf, (size_t)(SF_SLOT + 2 * SF_PER_SLOT) * S));
+    CK(c, dalloc(&w.shu, (size_t)(SU_REC + 2) * S));
+    CK(c, dalloc(&w.lacc, (size_t)6 * Q));
+    CK(c, dalloc(&w.ltot, (size_t)6 * Q));
+    CK(c, dalloc(&w.rpos, (size_t)R));
+    CK(c, dalloc(&w.rf, (size_t)RF_FIELDS * R));
+    CK(c, dalloc(&w.cnt, (size_t)CNT_WORDS));
+    CK(c, cudaMemset(w.cnt, 0, sizeof(uint32_t) * CNT_WORDS));
+    w.qcap = Q;
+    w.shcap = S;
+    w.rcap = R;
+    return MER_OK;
+}
+
+// four buffer sets so that independent passes can be in flight together; only sets 0 and 1
+// run replay passes and need record buffers
 mer_status ensure_wavefront(mer_ctx* c, int64_t need_paths, int maxD) {
     const int64_t want_q = std::max<int64_t>(need_paths, c->cfg.max_paths > 0 ? c->cfg.max_paths : 0);
     const int64_t want_r = 2 * want_q * std::max(1, maxD - 1);
-    if (want_q <= c->qcap && want_r <= c->rcap) return MER_OK;
+    if (want_q <= c->w[0].qcap && want_r <= c->w[0].rcap) return MER_OK;
     cudaStreamSynchronize(c->st);
+    for (cudaStream_t s : c->sx) cudaStreamSynchronize(s);
     free_wavefront(c);
     const int64_t Q = std::max<int64_t>(want_q, 1024);
-    const int64_t S = 2 * Q;
     const int64_t R = std::max<int64_t>(want_r, 1024);
-    for (int i = 0; i < 2; ++i) {
-        CK(c, dalloc(&c->qf[i], (size_t)(2 * QF_PER_BRANCH) * Q));
-        CK(c, dalloc(&c->qu[i], (size_t)QU_WORDS * Q));
+    for (int i = 0; i < 4; ++i) {
+        mer_status s = alloc_wave(c, c->w[i], Q, i < 2 ? R : 1);
+        if (s) return s;
     }
-    CK(c, dalloc(&c->hitf, (size_t)(2 * HF_PER_BRANCH) * Q));
-    CK(c, dalloc(&c->hitp, (size_t)2 * Q));
-    CK(c, dalloc(&c->shf, (size_t)(SF_SLOT + 2 * SF_PER_SLOT) * S));
-    CK(c, dalloc(&c->shu, (size_t)(SU_REC + 2) * S));
-    CK(c, dalloc(&c->lacc, (size_t)6 * Q));
-    CK(c, dalloc(&c->ltot, (size_t)6 * Q));
-    CK(c, dalloc(&c->rpos, (size_t)R));
-    CK(c, dalloc(&c->rf, (size_t)RF_FIELDS * R));
-    c->qcap = Q;
-    c->shcap = S;
-    c->rcap = R;
     c->graph_dirty = true;
     return MER_OK;
 }
@@ -251,23 +281,24 @@ mer_status ensure_wavefront(mer_ctx* c, int64_t need_paths, int maxD) {
 // grid of the simple grid-stride kernels (resolve, loss, scatter)
 int grid_for(mer_ctx* c, int block) { return c->sms * (2048 / block); }
 
-PassArgs base_args(mer_ctx* c) {
+PassArgs base_args(mer_ctx* c, const Wave& w) {
     PassArgs A;
     memset(&A, 0, sizeof A);
     A.probs = c->d_probs;
     A.pstate = c->d_pstate;
     A.inl_prob = -1;
     A.iter_override = -1;
-    A.qf[0] = c->qf[0]; A.qf[1] = c->qf[1];
-    A.qu[0] = c->qu[0]; A.qu[1] = c->qu[1];
-    A.qcap = c->qcap;
-    A.hitf = c->hitf; A.hitp = c->hitp;
-    A.shf = c->shf; A.shu = c->shu; A.shcap = c->shcap;
-    A.cnt = c->cnt;
-    A.lacc = c->lacc; A.ltot = c->ltot;
-    A.rpos = c->rpos; A.rf = c->rf; A.rcap = c->rcap;
+    A.qf[0] = w.qf[0]; A.qf[1] = w.qf[1];
+    A.qu[0] = w.qu[0]; A.qu[1] = w.qu[1];
+    A.qcap = w.qcap;
+    A.hitf = w.hitf; A.hitp = w.hitp;
+    A.shf = w.shf; A.shu = w.shu; A.shcap = w.shcap;
+    A.cnt = w.cnt;
+    A.lacc = w.lacc; A.ltot = w.ltot;
+    A.rpos = w.rpos; A.rf = w.rf; A.rcap = w.rcap;
     A.smem_nodes = c->shape.smem_nodes;
     A.smem_prob = 0;
+    A.stats = c->counting ? c->d_stats : nullptr;
     return A;
 }
 
@@ -279,16 +310,16 @@ LaunchShape shape_of(mer_ctx* c) {
     return L;
 }
 
-// zero the pass counters (not the error word) and run one pass
-int pass(mer_ctx* c, PassArgs A, int nb, int mode, int maxD) {
-    cudaMemsetAsync(c->cnt, 0, CNT_ERR * sizeof(uint32_t), c->st);
+// zero the pass counters (not the error word) and run one pass on stream st
+int pass(mer_ctx* c, cudaStream_t st, PassArgs A, int nb, int mode, int maxD) {
+    cudaMemsetAsync(A.cnt, 0, CNT_ERR * sizeof(uint32_t), st);
     const LaunchShape L = shape_of(c);
-    const int n = 1 + run_pass(A, nb, mode, maxD, L, c->st);
+    const int n = 1 + run_pass(A, nb, mode, maxD, L, st);
     if (g_timer) {
         // work items of this pass: rays per depth and NEE rays, read back from the pass counters
         uint32_t h[CNT_WORDS];
-        cudaMemcpyAsync(h, c->cnt, sizeof h, cudaMemcpyDeviceToHost, c->st);
-        cudaStreamSynchronize(c->st);
+        cudaMemcpyAsync(h, A.cnt, sizeof h, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
         int64_t rays = A.n_paths, sh = 0;
         for (int k = 2; k <= maxD; ++k) rays += h[CNT_Q + k];
         for (int k = 1; k <= maxD; ++k) sh += h[CNT_S + k];
@@ -302,52 +333,93 @@ int pass(mer_ctx* c, PassArgs A, int nb, int mode, int maxD) {
     return n;
 }
 
-// the gradient part of one iteration for all problems (steps a1-a10)
+// the gradient part of one iteration for all problems (steps a1-a10), as a graph of passes:
+//   stage 1 (concurrent): proportional primal image   [main stream, wave set 0]
+//                         FD primal image pair          [stream x0,  wave set 1]
+//                         proportional PRB radiance     [stream x1,  wave set 2]
+//                         FD PRB radiance pair          [stream x2,  wave set 3]
+//   stage 2: L2 loss and adjoint images (needs both images)
+//   stage 3 (concurrent): proportional replay + scatter into F   [main, set 0, L_total of set 2]
+//                         FD replay pair + scatter into dF       [x0,   set 1, L_total of set 3]
+// Branches fork and join through events, so inside stream capture they become parallel graph
+// branches. While per-kernel timing is on, everything runs on the main stream.
 int enqueue_gradient(mer_ctx* c) {
     int n = 0;
     const int G = grid_for(c, 256);
-    cudaMemsetAsync(c->d_loss, 0, sizeof(double) * c->probs.size(), c->st);
+    const bool have_fd = c->n_fd > 0 && c->P_fd > 0;
+    const bool split = !g_timer;
+    cudaStream_t s[4] = {c->st, split ? c->sx[0] : c->st, split ? c->sx[1] : c->st, split ? c->sx[2] : c->st};
+    cudaMemsetAsync(c->d_loss, 0, sizeof(double) * c->probs.size(), s[0]);
     n++;
-    PassArgs P = base_args(c);
-    P.entry_prob = c->d_prop_prob;
-    P.path_off = c->d_prop_off;
-    P.n_entries = (int)c->probs.size();
-    P.n_paths = c->P_prop;
-    PassArgs D = base_args(c);
-    D.entry_prob = c->d_fd_prob;
-    D.path_off = c->d_fd_off;
-    D.n_entries = c->n_fd;
-    D.n_paths = c->P_fd;
-    D.fd_kind = 1;
-    // primal images: FD pair (same counters at pi_i and pi_{i-1}) and the proportional image
-    if (c->n_fd > 0 && c->P_fd > 0) {
-        D.stream = MER_STREAM_FD_PRIMAL;
-        n += pass(c, D, 2, MODE_PRIMAL, c->maxD_fd);
-        n += run_resolve(D, 2, nullptr, nullptr, 0, G, c->st);
-    }
+    auto prop_args = [&](int wi) {
+        PassArgs A = base_args(c, c->w[wi]);
+        A.entry_prob = c->d_prop_prob;
+        A.path_off = c->d_prop_off;
+        A.n_entries = (int)c->probs.size();
+        A.n_paths = c->P_prop;
+        return A;
+    };
+    auto fd_args = [&](int wi) {
+        PassArgs A = base_args(c, c->w[wi]);
+        A.entry_prob = c->d_fd_prob;
+        A.path_off = c->d_fd_off;
+        A.n_entries = c->n_fd;
+        A.n_paths = c->P_fd;
+        A.fd_kind = 1;
+        return A;
+    };
+    auto fork = [&](int branches) {
+        if (!split) return;
+        cudaEventRecord(c->ev_fork, s[0]);
+        for (int b = 1; b < branches; ++b) cudaStreamWaitEvent(s[b], c->ev_fork, 0);
+    };
+    auto join = [&](int branches) {
+        if (!split) return;
+        for (int b = 1; b < branches; ++b) {
+            cudaEventRecord(c->ev_join[b - 1], s[b]);
+            cudaStreamWaitEvent(s[0], c->ev_join[b - 1], 0);
+        }
+    };
+    // ---- stage 1 ----
+    fork(4);
+    PassArgs P = prop_args(0);
     P.stream = MER_STREAM_PROP_PRIMAL;
-    n += pass(c, P, 1, MODE_PRIMAL, c->maxD_prop);
-    n += run_resolve(P, 1, nullptr, nullptr, 0, G, c->st);
-    // loss and adjoint images
-    n += run_l2(c->d_probs, c->d_pix_pref, (int)c->probs.size(), c->total_pix, c->n_fd > 0, c->d_loss, G, c->st);
-    // proportional gradient <F_i>: radiance pass, replay, scatter into F
-    P.stream = MER_STREAM_PROP_ADJ;
-    P.lacc = c->ltot;
-    n += pass(c, P, 1, MODE_ADJ_FWD, c->maxD_prop);
-    P.lacc = c->lacc;
-    P.ltot = c->ltot;
-    n += pass(c, P, 1, MODE_REPLAY, c->maxD_prop);
-    n += run_scatter(c->cnt, c->rpos, c->rf, c->rcap, c->d_probs, nullptr, 0, G, c->st);
-    // finite-difference gradient <dF_i> (Eq. est_triv): same for the pair, scatter into dF
-    if (c->n_fd > 0 && c->P_fd > 0) {
-        D.stream = MER_STREAM_FD_ADJ;
-        D.lacc = c->ltot;
-        n += pass(c, D, 2, MODE_ADJ_FWD, c->maxD_fd);
-        D.lacc = c->lacc;
-        D.ltot = c->ltot;
-        n += pass(c, D, 2, MODE_REPLAY, c->maxD_fd);
-        n += run_scatter(c->cnt, c->rpos, c->rf, c->rcap, c->d_probs, nullptr, 1, G, c->st);
+    n += pass(c, s[0], P, 1, MODE_PRIMAL, c->maxD_prop);
+    n += run_resolve(P, 1, nullptr, nullptr, 0, G, s[0]);
+    PassArgs PR = prop_args(2);
+    PR.stream = MER_STREAM_PROP_ADJ;
+    PR.lacc = c->w[2].ltot;                  // per-path radiance L_total of the replayed paths
+    n += pass(c, s[2], PR, 1, MODE_ADJ_FWD, c->maxD_prop);
+    if (have_fd) {
+        PassArgs D = fd_args(1);
+        D.stream = MER_STREAM_FD_PRIMAL;
+        n += pass(c, s[1], D, 2, MODE_PRIMAL, c->maxD_fd);
+        n += run_resolve(D, 2, nullptr, nullptr, 0, G, s[1]);
+        PassArgs DR = fd_args(3);
+        DR.stream = MER_STREAM_FD_ADJ;
+        DR.lacc = c->w[3].ltot;
+        n += pass(c, s[3], DR, 2, MODE_ADJ_FWD, c->maxD_fd);
     }
+    join(4);
+    // ---- stage 2: loss and adjoint images of every problem ----
+    n += run_l2(c->d_probs, c->d_pix_pref, (int)c->probs.size(), c->total_pix, have_fd, c->d_loss, G, s[0]);
+    // ---- stage 3 ----
+    fork(2);
+    // proportional gradient <F_i>: replay from the same counters, scatter into F
+    P = prop_args(0);
+    P.stream = MER_STREAM_PROP_ADJ;
+    P.ltot = c->w[2].ltot;
+    n += pass(c, s[0], P, 1, MODE_REPLAY, c->maxD_prop);
+    n += run_scatter(c->w[0].cnt, c->w[0].rpos, c->w[0].rf, c->w[0].rcap, c->d_probs, nullptr, 0, G, s[0]);
+    // finite-difference gradient <dF_i> (Eq. est_triv): the same for the pair, scatter into dF
+    if (have_fd) {
+        PassArgs D = fd_args(1);
+        D.stream = MER_STREAM_FD_ADJ;
+        D.ltot = c->w[3].ltot;
+        n += pass(c, s[1], D, 2, MODE_REPLAY, c->maxD_fd);
+        n += run_scatter(c->w[1].cnt, c->w[1].rpos, c->w[1].rf, c->w[1].rcap, c->d_probs, nullptr, 1, G, s[1]);
+    }
+    join(2);
     return n;
 }
 
@@ -359,11 +431,14 @@ int enqueue_update(mer_ctx* c) {
 }
 
 mer_status check_err_word(mer_ctx* c) {
-    uint32_t e = 0;
-    CK(c, cudaMemcpy(&e, c->cnt + CNT_ERR, sizeof e, cudaMemcpyDeviceToHost));
-    if (e) {
-        cudaMemset(c->cnt + CNT_ERR, 0, sizeof(uint32_t));
-        return fail(c, (int)e, "a kernel reported an out-of-capacity write (code %u)", e);
+    for (Wave& w : c->w) {
+        if (!w.cnt) continue;
+        uint32_t e = 0;
+        CK(c, cudaMemcpy(&e, w.cnt + CNT_ERR, sizeof e, cudaMemcpyDeviceToHost));
+        if (e) {
+            cudaMemset(w.cnt + CNT_ERR, 0, sizeof(uint32_t));
+            return fail(c, (int)e, "a kernel reported an out-of-capacity write (code %u)", e);
+        }
     }
     return MER_OK;
 }
@@ -465,7 +540,7 @@ int32_t read_cur(mer_ctx* c, Problem* p) {
 
 // single-problem pass helpers for the API calls (chunked over samples)
 PassArgs single_args(mer_ctx* c, Problem* p, uint32_t stream, uint32_t iteration, int spp) {
-    PassArgs A = base_args(c);
+    PassArgs A = base_args(c, c->w[0]);
     A.inl_prob = p->id;
     A.stream = stream;
     A.iter_override = (int32_t)iteration;
@@ -475,7 +550,7 @@ PassArgs single_args(mer_ctx* c, Problem* p, uint32_t stream, uint32_t iteration
 }
 
 int64_t chunk_spp(mer_ctx* c, Problem* p, int spp) {
-    return std::max<int64_t>(1, std::min<int64_t>(spp, c->qcap / std::max(1, p->n_pix)));
+    return std::max<int64_t>(1, std::min<int64_t>(spp, c->w[0].qcap / std::max(1, p->n_pix)));
 }
 
 }  // namespace
@@ -529,8 +604,11 @@ mer_status mer_create(const mer_config* cfg, void* cuda_stream, mer_ctx** out) {
     if (!e) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
     if (!e) e = cudaMalloc(&c->d_pstate, sizeof(ProbState) * MER_MAX_PROBLEMS);
     if (!e) e = cudaMalloc(&c->d_loss, sizeof(double) * MER_MAX_PROBLEMS);
-    if (!e) e = cudaMalloc(&c->cnt, sizeof(uint32_t) * CNT_WORDS);
-    if (!e) e = cudaMemset(c->cnt, 0, sizeof(uint32_t) * CNT_WORDS);
+    for (int i = 0; i < 3 && !e; ++i) {
+        e = cudaStreamCreateWithFlags(&c->sx[i], cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+    }
+    if (!e) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (!e) e = cudaMemset(c->d_loss, 0, sizeof(double) * MER_MAX_PROBLEMS);
     if (!e && c->shape.smem_nodes > 0) e = set_trace_smem_limits(c->shape.smem_nodes);
     if (e) {
@@ -553,11 +631,17 @@ void mer_destroy(mer_ctx* c) {
         delete p;
     }
     free_wavefront(c);
-    dfree(c->d_probs); dfree(c->d_pstate); dfree(c->d_loss); dfree(c->cnt);
+    dfree(c->d_probs); dfree(c->d_pstate); dfree(c->d_loss);
     dfree(c->d_prop_prob); dfree(c->d_prop_off); dfree(c->d_fd_prob); dfree(c->d_fd_off); dfree(c->d_pix_pref);
     dfree(c->d_segs); dfree(c->d_blk_off); dfree(c->d_partials);
+    dfree(c->d_stats);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    for (int i = 0; i < 3; ++i) {
+        if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+        if (c->sx[i]) cudaStreamDestroy(c->sx[i]);
+    }
     if (c->st) cudaStreamDestroy(c->st);
     delete c;
 }
@@ -896,7 +980,7 @@ mer_status mer_render(mer_ctx* c, int32_t pid, const float* tex, int32_t spp, ui
         A.tex_over[0] = tex;
         A.n_paths = ns * p->n_pix;
         A.sample_base = (int32_t)s0;
-        pass(c, A, 1, MODE_PRIMAL, p->max_depth);
+        pass(c, c->st, A, 1, MODE_PRIMAL, p->max_depth);
         run_resolve(A, 1, img, nullptr, s0 > 0, grid_for(c, 256), c->st);
     }
     CK(c, cudaGetLastError());
@@ -921,7 +1005,7 @@ mer_status mer_render_samples(mer_ctx* c, int32_t pid, const float* tex, int32_t
         A.tex_over[0] = tex;
         A.n_paths = ns * p->n_pix;
         A.sample_base = (int32_t)s0;
-        pass(c, A, 1, MODE_PRIMAL, p->max_depth);
+        pass(c, c->st, A, 1, MODE_PRIMAL, p->max_depth);
         run_samples_out(A, out, grid_for(c, 256), c->st);
     }
     CK(c, cudaGetLastError());
@@ -942,7 +1026,7 @@ mer_status mer_render_pair(mer_ctx* c, int32_t pid, const float* texA, const flo
         A.tex_over[1] = texB;
         A.n_paths = ns * p->n_pix;
         A.sample_base = (int32_t)s0;
-        pass(c, A, 2, MODE_PRIMAL, p->max_depth);
+        pass(c, c->st, A, 2, MODE_PRIMAL, p->max_depth);
         run_resolve(A, 2, imgA, imgB, s0 > 0, grid_for(c, 256), c->st);
     }
     CK(c, cudaGetLastError());
@@ -964,12 +1048,12 @@ static mer_status adjoint_impl(mer_ctx* c, Problem* p, int nb, const float* texA
         A.dimg_over[1] = dB;
         A.n_paths = ns * p->n_pix;
         A.sample_base = (int32_t)s0;
-        A.lacc = c->ltot;
-        pass(c, A, nb, MODE_ADJ_FWD, p->max_depth);
-        A.lacc = c->lacc;
-        A.ltot = c->ltot;
-        pass(c, A, nb, MODE_REPLAY, p->max_depth);
-        run_scatter(c->cnt, c->rpos, c->rf, c->rcap, c->d_probs, grad, 0, grid_for(c, 256), c->st);
+        A.lacc = c->w[0].ltot;
+        pass(c, c->st, A, nb, MODE_ADJ_FWD, p->max_depth);
+        A.lacc = c->w[0].lacc;
+        A.ltot = c->w[0].ltot;
+        pass(c, c->st, A, nb, MODE_REPLAY, p->max_depth);
+        run_scatter(c->w[0].cnt, c->w[0].rpos, c->w[0].rf, c->w[0].rcap, c->d_probs, grad, 0, grid_for(c, 256), c->st);
     }
     CK(c, cudaGetLastError());
     return MER_OK;
@@ -1090,7 +1174,8 @@ mer_status mer_state_get(mer_ctx* c, int32_t pid, mer_state_view* out) {
 }
 
 mer_status mer_profile_enable(mer_ctx* c, int32_t enable) {
-    if (!c) return fail(c, MER_ERR_INVALID_ARG, "null context");
+    if (!c || enable < 0 || enable > 2) return fail(c, MER_ERR_INVALID_ARG, "bad arguments");
+    cudaSetDevice(c->device);
     if (enable && !c->timer) {
         EventTimer* t = new EventTimer();
         c->timer = t;
@@ -1101,6 +1186,12 @@ mer_status mer_profile_enable(mer_ctx* c, int32_t enable) {
         delete t;
         c->timer = nullptr;
     }
+    if (enable == 2 && !c->d_stats) {
+        CK(c, dalloc(&c->d_stats, 2 * KC_COUNT));
+        CK(c, cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 2 * KC_COUNT));
+    }
+    c->counting = enable == 2;
+    c->graph_dirty = true;
     return MER_OK;
 }
 
@@ -1108,8 +1199,14 @@ mer_status mer_profile_read(mer_ctx* c, mer_kernel_time* out, int32_t max_entrie
     if (!c || !out || !n_out || max_entries < 0) return fail(c, MER_ERR_INVALID_ARG, "bad arguments");
     if (!c->timer) return fail(c, MER_ERR_STATE, "profiling is not enabled");
     cudaSetDevice(c->device);
+    unsigned long long h[2 * KC_COUNT] = {0};
+    if (c->counting && c->d_stats) {
+        CK(c, cudaStreamSynchronize(c->st));
+        CK(c, cudaMemcpy(h, c->d_stats, sizeof h, cudaMemcpyDeviceToHost));
+        CK(c, cudaMemset(c->d_stats, 0, sizeof h));
+    }
     int n = 0;
-    ((EventTimer*)c->timer)->read(out, max_entries, &n);
+    ((EventTimer*)c->timer)->read(out, max_entries, &n, c->counting ? h : nullptr);
     *n_out = n;
     return MER_OK;
 }

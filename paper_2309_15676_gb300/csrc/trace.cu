@@ -93,9 +93,15 @@ struct Hit {
 
 // closest hit (ANY = false) or any hit before tmax (ANY = true). Ties in t go to the
 // smaller primitive id, independent of traversal order.
-template <bool ANY>
+// algorithmic work of a traversal (counted only in the counting instantiation)
+struct TravCount {
+    unsigned nodes = 0;   // two-box node tests
+    unsigned prims = 0;   // triangle and sphere tests
+};
+
+template <bool ANY, bool STATS = false>
 __device__ __forceinline__ bool traverse(const ProblemDev& P, const Node* s_nodes, int smem_n, v3 o, v3 d,
-                                         float tmax, Hit& h) {
+                                         float tmax, Hit& h, TravCount& tc) {
     h.t = tmax;
     h.prim = -1;
     h.b1 = h.b2 = 0.0f;
@@ -113,6 +119,7 @@ __device__ __forceinline__ bool traverse(const ProblemDev& P, const Node* s_node
         while (true) {
             while (node >= 0) {
                 const Node n = load_node(P.nodes, s_nodes, smem_n, node);
+                if (STATS) tc.nodes++;
                 const float tfar = h.t * grow;
                 const float l0x = fmaf(n.a.x, ix, -ox), l1x = fmaf(n.a.y, ix, -ox);
                 const float l0y = fmaf(n.a.z, iy, -oy), l1y = fmaf(n.a.w, iy, -oy);
@@ -143,6 +150,7 @@ __device__ __forceinline__ bool traverse(const ProblemDev& P, const Node* s_node
             // leaf
             const int x = ~node;
             const int first = x >> 3, count = (x & 7) + 1;
+            if (STATS) tc.prims += count;
             for (int k = 0; k < count; ++k) {
                 const TriGeo T = load_tri(P.tris, first + k);
                 float t, u, v;
@@ -160,6 +168,7 @@ __device__ __forceinline__ bool traverse(const ProblemDev& P, const Node* s_node
         }
     }
     if (!ANY) h.prim = (best == 0x7fffffff) ? -1 : best;
+    if (STATS) tc.prims += P.n_sph;
     for (int i = 0; i < P.n_sph; ++i) {
         const Sphere S = P.sph[i];
         float t;
@@ -361,7 +370,16 @@ __device__ __forceinline__ int stage_nodes(const PassArgs& A, const Node*& s_nod
 // ---------------------------------------------------------------------------------
 // extend: closest hit of every queued ray (shared once per coincident pair)
 // ---------------------------------------------------------------------------------
-template <int NB>
+// adds a warp's traversal counts to stats[2*cls], stats[2*cls+1]; all lanes must call
+__device__ __forceinline__ void flush_counts(const PassArgs& A, int cls, const TravCount& tc) {
+    const unsigned nsum = __reduce_add_sync(FULL, tc.nodes), psum = __reduce_add_sync(FULL, tc.prims);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(A.stats + 2 * cls, (unsigned long long)nsum);
+        atomicAdd(A.stats + 2 * cls + 1, (unsigned long long)psum);
+    }
+}
+
+template <int NB, bool STATS>
 __global__ void __launch_bounds__(256) k_extend(PassArgs A, int depth) {
     const Node* s_nodes;
     const int n_staged = stage_nodes(A, s_nodes);
@@ -369,6 +387,7 @@ __global__ void __launch_bounds__(256) k_extend(PassArgs A, int depth) {
     const int64_t n = first ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth], A.qcap);
     const int qi = depth & 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    TravCount tc;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         uint32_t flags;
         int q;
@@ -398,13 +417,14 @@ __global__ void __launch_bounds__(256) k_extend(PassArgs A, int depth) {
             if (!(flags & (1u << b))) continue;
             if (b == 1 && (flags & FLAG_COINC)) continue;
             Hit h;
-            traverse<false>(P, s_nodes, q == A.smem_prob ? n_staged : 0, o[b], d[b], INFINITY, h);
+            traverse<false, STATS>(P, s_nodes, q == A.smem_prob ? n_staged : 0, o[b], d[b], INFINITY, h, tc);
             A.hitf[(size_t)(b * HF_PER_BRANCH + HF_T) * A.qcap + j] = h.t;
             A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B1) * A.qcap + j] = h.b1;
             A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B2) * A.qcap + j] = h.b2;
             A.hitp[(size_t)b * A.qcap + j] = h.prim;
         }
     }
+    if (STATS) flush_counts(A, NB == 1 ? KC_EXTEND1 : KC_EXTEND2, tc);
 }
 
 // ---------------------------------------------------------------------------------
@@ -754,13 +774,14 @@ __global__ void __launch_bounds__(256) k_shade(PassArgs A, int depth) {
 // ---------------------------------------------------------------------------------
 // shadow: any-hit of NEE rays; visible ones add their radiance (and NEE gradient part)
 // ---------------------------------------------------------------------------------
-template <int NB, int MODE>
+template <int NB, int MODE, bool STATS>
 __global__ void __launch_bounds__(256) k_shadow(PassArgs A, int depth) {
     const Node* s_nodes;
     const int n_staged = stage_nodes(A, s_nodes);
     const int64_t n = min((int64_t)A.cnt[CNT_S + depth], A.shcap);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const size_t C = (size_t)A.shcap;
+    TravCount tc;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const float* F = A.shf;
         const v3 o = mk(F[(SF_O + 0) * C + j], F[(SF_O + 1) * C + j], F[(SF_O + 2) * C + j]);
@@ -771,7 +792,7 @@ __global__ void __launch_bounds__(256) k_shadow(PassArgs A, int depth) {
         const int q = meta & 0xff;
         const uint32_t mask = (meta >> 8) & 3u;
         Hit h;
-        if (traverse<true>(A.probs[q], s_nodes, q == A.smem_prob ? n_staged : 0, o, d, tmax, h)) continue;
+        if (traverse<true, STATS>(A.probs[q], s_nodes, q == A.smem_prob ? n_staged : 0, o, d, tmax, h, tc)) continue;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             if (!(mask & (1u << b))) continue;
@@ -786,6 +807,7 @@ __global__ void __launch_bounds__(256) k_shadow(PassArgs A, int depth) {
             }
         }
     }
+    if (STATS) flush_counts(A, (NB == 1 ? KC_SHADOW1_PRIMAL : KC_SHADOW2_PRIMAL) + (MODE == MODE_REPLAY ? 1 : 0), tc);
 }
 
 // ---------------------------------------------------------------------------------
@@ -851,16 +873,22 @@ static void launch_depth(const PassArgs& A, int depth, const LaunchShape& L, cud
     static int g_ext = 0, g_sh = 0, g_sd = 0;
     static LaunchShape last{-1, -1, -1, -1};
     if (last.block != L.block || last.per_sm != L.per_sm || last.smem_nodes != L.smem_nodes || last.sms != L.sms) {
-        g_ext = persistent_grid(k_extend<NB>, L, smem);
+        g_ext = persistent_grid(k_extend<NB, false>, L, smem);
         g_sh = persistent_grid(k_shade<NB, MODE>, L, 0);
-        g_sd = persistent_grid(k_shadow<NB, MODE>, L, smem);
+        g_sd = persistent_grid(k_shadow<NB, MODE, false>, L, smem);
         last = L;
     }
     const int base = NB == 1 ? KC_EXTEND1 : KC_EXTEND2;
     const int rep = MODE == MODE_REPLAY ? 1 : 0;
-    MER_TIMED(base, st, k_extend<NB><<<g_ext, L.block, smem, st>>>(B, depth));
+    if (A.stats) {   // counting run: same grids, traversal work counted
+        k_extend<NB, true><<<g_ext, L.block, smem, st>>>(B, depth);
+        k_shade<NB, MODE><<<g_sh, L.block, 0, st>>>(B, depth);
+        k_shadow<NB, MODE, true><<<g_sd, L.block, smem, st>>>(B, depth);
+        return;
+    }
+    MER_TIMED(base, st, k_extend<NB, false><<<g_ext, L.block, smem, st>>>(B, depth));
     MER_TIMED(base + 1 + rep, st, k_shade<NB, MODE><<<g_sh, L.block, 0, st>>>(B, depth));
-    MER_TIMED(base + 3 + rep, st, k_shadow<NB, MODE><<<g_sd, L.block, smem, st>>>(B, depth));
+    MER_TIMED(base + 3 + rep, st, k_shadow<NB, MODE, false><<<g_sd, L.block, smem, st>>>(B, depth));
 }
 
 // enqueues one full pass; returns the number of kernel launches
@@ -892,14 +920,18 @@ int run_samples_out(const PassArgs& A, float* out, int grid, cudaStream_t st) {
 
 cudaError_t set_trace_smem_limits(int max_nodes) {
     const int bytes = max_nodes * (int)sizeof(Node);
-    cudaError_t e = cudaSuccess;
-    e = cudaFuncSetAttribute(k_extend<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
-    e = cudaFuncSetAttribute(k_extend<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
-    e = cudaFuncSetAttribute(k_shadow<1, MODE_PRIMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
-    e = cudaFuncSetAttribute(k_shadow<1, MODE_REPLAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
-    e = cudaFuncSetAttribute(k_shadow<2, MODE_PRIMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); if (e) return e;
-    e = cudaFuncSetAttribute(k_shadow<2, MODE_REPLAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const void* fns[] = {(const void*)k_extend<1, false>,          (const void*)k_extend<2, false>,
+                         (const void*)k_extend<1, true>,           (const void*)k_extend<2, true>,
+                         (const void*)k_shadow<1, MODE_PRIMAL, false>, (const void*)k_shadow<1, MODE_REPLAY, false>,
+                         (const void*)k_shadow<2, MODE_PRIMAL, false>, (const void*)k_shadow<2, MODE_REPLAY, false>,
+                         (const void*)k_shadow<1, MODE_PRIMAL, true>,  (const void*)k_shadow<1, MODE_REPLAY, true>,
+                         (const void*)k_shadow<2, MODE_PRIMAL, true>,  (const void*)k_shadow<2, MODE_REPLAY, true>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, at, bytes);
+        if (e) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace mer

@@ -64,6 +64,7 @@ struct PassArgs {
     int64_t rcap;
     int32_t smem_nodes;       // top BVH nodes of problem smem_prob staged in shared memory
     int32_t smem_prob;
+    unsigned long long* stats; // counting run: [2*class] node tests, [2*class+1] primitive tests
 };
 
 __device__ __forceinline__ int find_entry(const int64_t* off, int n, int64_t g) {
