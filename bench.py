@@ -39,6 +39,10 @@ def parse():
     ap.add_argument("--ttt-iters", type=int, default=300)
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched comparison")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 1024^2 / 205k-triangle roofline leg")
+    ap.add_argument("--only-scale", action="store_true", help="run only the scale leg (for profiling)")
+    ap.add_argument("--scale-image", type=int, default=1024, help="image side of the scale leg")
     return ap.parse_args()
 
 
@@ -228,6 +232,109 @@ def time_to_threshold(torch, w, target_img, max_iters, lrs=(0.001, 0.003, 0.01, 
     return out
 
 
+def batched_compare(torch, n_problems=64, iters=3, seed=4):
+    """64 independent problems of uneven sizes (images {64..512}^2, 1k-50k triangles, textures
+    64^2-512^2 x5, depths 3-8, 1 FD + 2 proportional spp each): one context advancing all problems
+    per graph-launched iteration vs the per-problem launch loop (one context per problem)."""
+    from paper_2309_15676_gb300 import synth
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    t_setup = time.perf_counter()
+    ws = synth.workload_batch(n_problems, seed=seed)
+    total_paths = sum(12 * w.scene["width"] * w.scene["height"] for w in ws)
+
+    def setup(ctx, w):
+        pid = ctx.add_scene(w.scene, HyperParams(lr=0.01))
+        ctx.render_target(pid, torch.from_numpy(w.target_tex).cuda(), 16)
+        ctx.set_params(pid, w.init_tex)
+        return pid
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    big = Context(0)
+    for w in ws:
+        setup(big, w)
+    singles = []
+    for w in ws:
+        c = Context(0)
+        singles.append((c, setup(c, w)))
+    setup_s = time.perf_counter() - t_setup
+    big.iterate(2, use_graph=True)
+    for c, _ in singles:
+        c.iterate(2, use_graph=True)
+    ms_batched = timed(lambda: big.iterate(1, use_graph=True), iters)
+    ms_loop_graph = timed(lambda: [c.iterate(1, use_graph=True) for c, _ in singles], iters)
+    ms_loop_plain = timed(lambda: [c.iterate(1, use_graph=False) for c, _ in singles], iters)
+    launches = big.launch_count()
+    big.close()
+    for c, _ in singles:
+        c.close()
+    out = {"problems": n_problems, "paths_per_iter": total_paths, "setup_s": setup_s,
+           "batched_graph": {"ms_per_iter": ms_batched, "iters_per_s": 1e3 / ms_batched,
+                             "problem_iters_per_s": n_problems * 1e3 / ms_batched,
+                             "paths_per_s": total_paths * 1e3 / ms_batched, "launches_per_iter": launches},
+           "per_problem_loop_plain": {"ms_per_iter": ms_loop_plain, "iters_per_s": 1e3 / ms_loop_plain,
+                                      "problem_iters_per_s": n_problems * 1e3 / ms_loop_plain},
+           "per_problem_loop_graph": {"ms_per_iter": ms_loop_graph, "iters_per_s": 1e3 / ms_loop_graph,
+                                      "problem_iters_per_s": n_problems * 1e3 / ms_loop_graph}}
+    out["speedup_vs_plain_loop"] = ms_loop_plain / ms_batched
+    return out
+
+
+def scale_profile(torch, hbm_peak, image=1024):
+    """1024^2 image, displaced sphere of 204,800 triangles, 2048^2 x 5 textures, env + 4 area lights,
+    depth 8, 4 FD + 4 proportional spp: iteration throughput and the scatter / update rooflines
+    where they move hundreds of MB per launch."""
+    from paper_2309_15676_gb300 import synth
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    w = synth.workload_sphere(image, image)
+    sc = w.scene
+    ctx = Context(0)
+    pid = ctx.add_scene(sc, HyperParams(lr=0.01))
+    ctx.render_target(pid, torch.from_numpy(w.target_tex).cuda(), 8)
+    ctx.set_params(pid, w.init_tex)
+    ctx.iterate(2, use_graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.iterate(3, use_graph=True)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    paths = ctx.stats(pid)["paths_per_iter"]
+    ctx.profile(1)
+    ctx.iterate(1, use_graph=False)
+    prof = ctx.profile_read()
+    ctx.profile(0)
+    ctx.close()
+    C, H, W = sc["tex_c"], sc["tex_h"], sc["tex_w"]
+    out = {"workload": "dsphere1024: 1024^2, 204,800 triangles, 2048^2x5 textures, depth 8, 4 FD + 4 prop spp",
+           "ms_per_iter": ms, "paths_per_iter": paths, "paths_per_s": paths * 1e3 / ms, "rooflines": []}
+    if "scatter" in prof:
+        p = prof["scatter"]
+        byts = p["units"] * (4 + 4 * (2 + C)) + p["launches"] * 2 * 4 * H * W * C
+        gbs = byts / (p["ms"] * 1e-3) / 1e9
+        out["rooflines"].append({"kernel": "scatter", "bound": "hbm", "records": p["units"], "launches": p["launches"],
+                                 "bytes": byts, "ms": p["ms"], "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": gbs / hbm_peak})
+    if "update" in prof:
+        p = prof["update"]
+        byts = 64 * p["units"]
+        gbs = byts / (p["ms"] * 1e-3) / 1e9
+        out["rooflines"].append({"kernel": "update (META, in the iteration)", "bound": "hbm", "params": p["units"],
+                                 "bytes": byts, "ms": p["ms"], "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": gbs / hbm_peak})
+    out["kernel_ms"] = {k: v["ms"] for k, v in prof.items()}
+    return out
+
+
 def update_roofline(torch, hbm_peak, n=67_108_864, reps=10):
     """Standalone fused update (META) at 67M parameters (a 256^3 x 4 volume): 64 B per parameter."""
     from paper_2309_15676_gb300.api import HyperParams, meta_step_raw
@@ -276,6 +383,9 @@ def run_mine(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hbm_peak, peak_kind, sm_max = measured_peaks()
+    if args.only_scale:
+        print(json.dumps({"scale": scale_profile(torch, hbm_peak, args.scale_image)}), flush=True)
+        return 0
 
     w = workload()
     sc = dict(w.scene)
@@ -406,6 +516,8 @@ def run_mine(args):
     ttt = None
     if rank == 0 and not args.no_ttt:
         ttt = time_to_threshold(torch, w, target_img, args.ttt_iters)
+    batched = batched_compare(torch) if (rank == 0 and not args.no_batch) else None
+    scale = scale_profile(torch, hbm_peak, args.scale_image) if (rank == 0 and not args.no_scale) else None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(w)
     if rank == 0:
@@ -421,7 +533,7 @@ def run_mine(args):
                 "kernels": kernels, "peak_source": peak_kind,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                 "gpu_launches": int(launches_per_iter * args.steps),
-                "time_to_threshold": ttt}
+                "time_to_threshold": ttt, "batched": batched, "scale": scale}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

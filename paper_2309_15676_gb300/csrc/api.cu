@@ -1036,6 +1036,7 @@ mer_status mer_render_pair(mer_ctx* c, int32_t pid, const float* texA, const flo
 static mer_status adjoint_impl(mer_ctx* c, Problem* p, int nb, const float* texA, const float* texB,
                                const float* dA, const float* dB, int32_t spp, uint32_t stream, uint32_t iteration,
                                float* grad) {
+    if ((uintptr_t)grad & 15u) return fail(c, MER_ERR_INVALID_ARG, "gradient output must be 16-byte aligned");
     Guard g(c);
     CK(c, cudaMemsetAsync(grad, 0, sizeof(float) * p->n_par, c->st));
     const int64_t ch = chunk_spp(c, p, spp);

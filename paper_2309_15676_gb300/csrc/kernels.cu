@@ -25,10 +25,52 @@ __device__ __forceinline__ float peer_sum(unsigned vmask, unsigned peers, float 
     return acc;
 }
 
+// Adds v[0..len) to the contiguous floats base[f0 ..) with the widest aligned vector
+// reductions available (float4 where 16-byte aligned, float2 where 8-byte aligned, else
+// scalar); base itself must be 16-byte aligned. Unrolled so that v stays in registers.
+__device__ __forceinline__ void red_run(float* base, int64_t f0, const float (&v)[13], int len) {
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        if (k == s && k < len) {
+            const int64_t f = f0 + k;
+            const int rem = len - k;
+            if ((f & 3) == 0 && rem >= 4) {
+                atomicAdd(reinterpret_cast<float4*>(base + f), make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]));
+                s += 4;
+            } else if ((f & 1) == 0 && rem >= 2) {
+                atomicAdd(reinterpret_cast<float2*>(base + f), make_float2(v[k], v[k + 1]));
+                s += 2;
+            } else {
+                atomicAdd(base + f, v[k]);
+                s += 1;
+            }
+        }
+    }
+}
+
+template <int CC>
+__device__ __forceinline__ void fill_rows(float (&v)[2][13], const float (&g)[MAXC], float w00, float w10, float w01,
+                                          float w11) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float wa = r ? w01 : w00, wb = r ? w11 : w10;
+#pragma unroll
+        for (int k = 0; k < 13; ++k) v[r][k] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < CC; ++c) {
+            v[r][c] = wa * g[c];
+            v[r][CC + c] = wb * g[c];   // ignored beyond the run length when the taps merged
+        }
+    }
+}
+
 // Each record {problem, texel footprint (x0, y0, fx, fy), g[C]} adds w_k g[c] to the four
-// bilinear taps (clamp-to-edge) of the problem's gradient texture. Lanes of a warp holding
-// the same footprint origin (same four taps) are merged with __match_any_sync and a
-// segmented shuffle sum, and only the group's first lane issues the atomics.
+// bilinear taps (clamp-to-edge) of the problem's HWC gradient texture. The two taps of a row
+// are adjacent texels, i.e. one run of up to 2C contiguous floats, issued as aligned vector
+// reductions (taps that clamp onto the same texel are merged first). Lanes of a warp holding
+// the same footprint origin are merged with __match_any_sync and a segmented shuffle sum;
+// only the group's first lane issues the reductions. All shuffles are warp-uniform.
 __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ rpos,
                                                  const float* __restrict__ rf, int64_t rcap,
                                                  const ProblemDev* __restrict__ probs, float* grad_over, int which) {
@@ -49,29 +91,30 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cn
 #pragma unroll
         for (int c = 0; c < MAXC; ++c) g[c] = (c < C) ? __ldcs(rf + (size_t)(RF_G + c) * rcap + i) : 0.0f;
         const int xa = max(x0, 0), xb = min(x0 + 1, W - 1), ya = max(y0, 0), yb = min(y0 + 1, H - 1);
-        float* base = grad_over ? grad_over : (which ? P.dF : P.F);
-        float* tap[4] = {base + ((size_t)ya * W + xa) * C, base + ((size_t)ya * W + xb) * C,
-                         base + ((size_t)yb * W + xa) * C, base + ((size_t)yb * W + xb) * C};
-        const float w[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
+        float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
+        const bool one_x = xa == xb, one_y = ya == yb;
+        if (one_x) { w00 += w10; w10 = 0.0f; w01 += w11; w11 = 0.0f; }
+        if (one_y) { w00 += w01; w10 += w11; w01 = 0.0f; w11 = 0.0f; }
+        // row r holds [tap xa channels..., tap xb channels...] (compile-time indices per C)
+        float v[2][13];
+        if (C == 5) fill_rows<5>(v, g, w00, w10, w01, w11);
+        else fill_rows<3>(v, g, w00, w10, w01, w11);
         const unsigned peers = __match_any_sync(vmask, pos);
-        const int gsize = __popc(peers);
-        const int maxg = (int)__reduce_max_sync(vmask, (unsigned)gsize);
-        if (maxg == 1) {
+        const int maxg = (int)__reduce_max_sync(vmask, (unsigned)__popc(peers));
+        bool issue = true;
+        if (maxg > 1) {
+            // same pos => same problem and layout; every lane runs every shuffle
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int r = 0; r < 2; ++r)
 #pragma unroll
-                for (int c = 0; c < MAXC; ++c)
-                    if (c < C) atomicAdd(tap[k] + c, w[k] * g[c]);
-        } else {
-            const bool leader = (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int c = 0; c < MAXC; ++c) {
-                    if (c >= C) continue;   // C is uniform across the group (same problem)
-                    const float s = peer_sum(vmask, peers, w[k] * g[c], maxg);
-                    if (leader) atomicAdd(tap[k] + c, s);
-                }
+                for (int k = 0; k < 10; ++k) v[r][k] = peer_sum(vmask, peers, v[r][k], maxg);
+            issue = (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
+        }
+        if (issue) {
+            float* base = grad_over ? grad_over : (which ? P.dF : P.F);
+            const int len = (one_x ? 1 : 2) * C;
+            red_run(base, ((int64_t)ya * W + xa) * C, v[0], len);
+            if (!one_y) red_run(base, ((int64_t)yb * W + xa) * C, v[1], len);
         }
     }
 }
