@@ -45,8 +45,7 @@ struct Wave {
     uint32_t* cnt = nullptr;       // pass counters + error word
     float* lacc = nullptr;
     float* ltot = nullptr;
-    uint32_t* rpos = nullptr;
-    float* rf = nullptr;
+    Record* rec = nullptr;
 };
 
 struct mer_ctx {
@@ -229,7 +228,7 @@ void free_wave(Wave& w) {
         dfree(w.qu[i]);
     }
     dfree(w.hitf); dfree(w.hitp); dfree(w.shf); dfree(w.shu); dfree(w.lacc); dfree(w.ltot);
-    dfree(w.rpos); dfree(w.rf); dfree(w.cnt);
+    dfree(w.rec); dfree(w.cnt);
     w = Wave();
 }
 
@@ -249,8 +248,7 @@ mer_status alloc_wave(mer_ctx* c, Wave& w, int64_t Q, int64_t R) {
     CK(c, dalloc(&w.shu, (size_t)(SU_REC + 2) * S));
     CK(c, dalloc(&w.lacc, (size_t)6 * Q));
     CK(c, dalloc(&w.ltot, (size_t)6 * Q));
-    CK(c, dalloc(&w.rpos, (size_t)R));
-    CK(c, dalloc(&w.rf, (size_t)RF_FIELDS * R));
+    CK(c, dalloc(&w.rec, (size_t)R));
     CK(c, dalloc(&w.cnt, (size_t)CNT_WORDS));
     CK(c, cudaMemset(w.cnt, 0, sizeof(uint32_t) * CNT_WORDS));
     w.qcap = Q;
@@ -295,7 +293,7 @@ PassArgs base_args(mer_ctx* c, const Wave& w) {
     A.shf = w.shf; A.shu = w.shu; A.shcap = w.shcap;
     A.cnt = w.cnt;
     A.lacc = w.lacc; A.ltot = w.ltot;
-    A.rpos = w.rpos; A.rf = w.rf; A.rcap = w.rcap;
+    A.rec = w.rec; A.rcap = w.rcap;
     A.smem_nodes = c->shape.smem_nodes;
     A.smem_prob = 0;
     A.stats = c->counting ? c->d_stats : nullptr;
@@ -410,14 +408,14 @@ int enqueue_gradient(mer_ctx* c) {
     P.stream = MER_STREAM_PROP_ADJ;
     P.ltot = c->w[2].ltot;
     n += pass(c, s[0], P, 1, MODE_REPLAY, c->maxD_prop);
-    n += run_scatter(c->w[0].cnt, c->w[0].rpos, c->w[0].rf, c->w[0].rcap, c->d_probs, nullptr, 0, G, s[0]);
+    n += run_scatter(c->w[0].cnt, c->w[0].rec, c->w[0].rcap, c->d_probs, (int)c->probs.size(), nullptr, 0, G, s[0]);
     // finite-difference gradient <dF_i> (Eq. est_triv): the same for the pair, scatter into dF
     if (have_fd) {
         PassArgs D = fd_args(1);
         D.stream = MER_STREAM_FD_ADJ;
         D.ltot = c->w[3].ltot;
         n += pass(c, s[1], D, 2, MODE_REPLAY, c->maxD_fd);
-        n += run_scatter(c->w[1].cnt, c->w[1].rpos, c->w[1].rf, c->w[1].rcap, c->d_probs, nullptr, 1, G, s[1]);
+        n += run_scatter(c->w[1].cnt, c->w[1].rec, c->w[1].rcap, c->d_probs, (int)c->probs.size(), nullptr, 1, G, s[1]);
     }
     join(2);
     return n;
@@ -1054,7 +1052,8 @@ static mer_status adjoint_impl(mer_ctx* c, Problem* p, int nb, const float* texA
         A.lacc = c->w[0].lacc;
         A.ltot = c->w[0].ltot;
         pass(c, c->st, A, nb, MODE_REPLAY, p->max_depth);
-        run_scatter(c->w[0].cnt, c->w[0].rpos, c->w[0].rf, c->w[0].rcap, c->d_probs, grad, 0, grid_for(c, 256), c->st);
+        run_scatter(c->w[0].cnt, c->w[0].rec, c->w[0].rcap, c->d_probs, (int)c->probs.size(), grad, 0, grid_for(c, 256),
+                    c->st);
     }
     CK(c, cudaGetLastError());
     return MER_OK;

@@ -65,63 +65,83 @@ __device__ __forceinline__ void fill_rows(float (&v)[2][13], const float (&g)[MA
     }
 }
 
-// Each record {problem, texel footprint (x0, y0, fx, fy), g[C]} adds w_k g[c] to the four
-// bilinear taps (clamp-to-edge) of the problem's HWC gradient texture. The two taps of a row
-// are adjacent texels, i.e. one run of up to 2C contiguous floats, issued as aligned vector
-// reductions (taps that clamp onto the same texel are merged first). Lanes of a warp holding
-// the same footprint origin are merged with __match_any_sync and a segmented shuffle sum;
-// only the group's first lane issues the reductions. All shuffles are warp-uniform.
-__global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ rpos,
-                                                 const float* __restrict__ rf, int64_t rcap,
-                                                 const ProblemDev* __restrict__ probs, float* grad_over, int which) {
-    const int64_t n = min((int64_t)cnt[CNT_R], rcap);
-    const int64_t nw = (n + 31) & ~(int64_t)31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
-        const bool valid = i < n;
-        const unsigned vmask = __ballot_sync(FULLM, valid);
-        if (!valid) continue;
-        const uint32_t pos = __ldcs(rpos + i);
-        const int q = pos >> 24;
-        const ProblemDev& P = probs[q];
-        const int x0 = (int)(pos & 0xfff) - 1, y0 = (int)((pos >> 12) & 0xfff) - 1;
-        const float fx = __ldcs(rf + (size_t)RF_FX * rcap + i), fy = __ldcs(rf + (size_t)RF_FY * rcap + i);
-        const int C = P.tex_c, W = P.tex_w, H = P.tex_h;
-        float g[MAXC];
+// per-problem fields the scatter needs, cached in shared memory
+struct SProb {
+    int C, W, H, pad;
+    float* F;
+    float* dF;
+};
+
+// One record: adds w_k g[c] to the four bilinear taps (clamp-to-edge) of the problem's HWC
+// gradient texture. The two taps of a row are adjacent texels, i.e. one run of up to 2C
+// contiguous floats, issued as aligned vector reductions (taps that clamp onto the same texel
+// are merged first). Lanes holding the same footprint origin are merged with __match_any_sync
+// and a segmented shuffle sum; only the group's first lane issues the reductions. Lanes whose
+// record is absent or all-zero sit out; every shuffle runs over exactly the participating lanes.
+__device__ __forceinline__ void scatter_one(bool valid, float4 a, float4 b, const SProb* sp, float* grad_over,
+                                            int which) {
+    const uint32_t pos = __float_as_uint(a.x);
+    float g[MAXC] = {a.w, b.x, b.y, b.z, b.w};
+    valid = valid && (g[0] != 0.0f || g[1] != 0.0f || g[2] != 0.0f || g[3] != 0.0f || g[4] != 0.0f);
+    const unsigned vmask = __ballot_sync(FULLM, valid);
+    if (!valid) return;
+    const SProb P = sp[pos >> 24];
+    const int C = P.C, W = P.W, H = P.H;
+    const int x0 = (int)(pos & 0xfff) - 1, y0 = (int)((pos >> 12) & 0xfff) - 1;
+    const float fx = a.y, fy = a.z;
+    const int xa = max(x0, 0), xb = min(x0 + 1, W - 1), ya = max(y0, 0), yb = min(y0 + 1, H - 1);
+    float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
+    const bool one_x = xa == xb, one_y = ya == yb;
+    if (one_x) { w00 += w10; w10 = 0.0f; w01 += w11; w11 = 0.0f; }
+    if (one_y) { w00 += w01; w10 += w11; w01 = 0.0f; w11 = 0.0f; }
+    // row r holds [tap xa channels..., tap xb channels...] (compile-time indices per C)
+    float v[2][13];
+    if (C == 5) fill_rows<5>(v, g, w00, w10, w01, w11);
+    else fill_rows<3>(v, g, w00, w10, w01, w11);
+    const unsigned peers = __match_any_sync(vmask, pos);
+    const int maxg = (int)__reduce_max_sync(vmask, (unsigned)__popc(peers));
+    bool issue = true;
+    if (maxg > 1) {
+        // same pos => same problem and layout; every participating lane runs every shuffle
 #pragma unroll
-        for (int c = 0; c < MAXC; ++c) g[c] = (c < C) ? __ldcs(rf + (size_t)(RF_G + c) * rcap + i) : 0.0f;
-        const int xa = max(x0, 0), xb = min(x0 + 1, W - 1), ya = max(y0, 0), yb = min(y0 + 1, H - 1);
-        float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
-        const bool one_x = xa == xb, one_y = ya == yb;
-        if (one_x) { w00 += w10; w10 = 0.0f; w01 += w11; w11 = 0.0f; }
-        if (one_y) { w00 += w01; w10 += w11; w01 = 0.0f; w11 = 0.0f; }
-        // row r holds [tap xa channels..., tap xb channels...] (compile-time indices per C)
-        float v[2][13];
-        if (C == 5) fill_rows<5>(v, g, w00, w10, w01, w11);
-        else fill_rows<3>(v, g, w00, w10, w01, w11);
-        const unsigned peers = __match_any_sync(vmask, pos);
-        const int maxg = (int)__reduce_max_sync(vmask, (unsigned)__popc(peers));
-        bool issue = true;
-        if (maxg > 1) {
-            // same pos => same problem and layout; every lane runs every shuffle
+        for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int k = 0; k < 10; ++k) v[r][k] = peer_sum(vmask, peers, v[r][k], maxg);
-            issue = (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
-        }
-        if (issue) {
-            float* base = grad_over ? grad_over : (which ? P.dF : P.F);
-            const int len = (one_x ? 1 : 2) * C;
-            red_run(base, ((int64_t)ya * W + xa) * C, v[0], len);
-            if (!one_y) red_run(base, ((int64_t)yb * W + xa) * C, v[1], len);
-        }
+            for (int k = 0; k < 10; ++k) v[r][k] = peer_sum(vmask, peers, v[r][k], maxg);
+        issue = (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
+    }
+    if (issue) {
+        float* base = grad_over ? grad_over : (which ? P.dF : P.F);
+        const int len = (one_x ? 1 : 2) * C;
+        red_run(base, ((int64_t)ya * W + xa) * C, v[0], len);
+        if (!one_y) red_run(base, ((int64_t)yb * W + xa) * C, v[1], len);
     }
 }
 
-int run_scatter(const uint32_t* cnt, const uint32_t* rpos, const float* rf, int64_t rcap, const ProblemDev* probs,
+// Grid-stride over records, one per lane (two 16-byte streaming loads each).
+__global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cnt, const Record* __restrict__ rec,
+                                                 int64_t rcap, const ProblemDev* __restrict__ probs, int n_probs,
+                                                 float* grad_over, int which) {
+    __shared__ SProb sp[MER_MAX_PROBLEMS];
+    for (int t = threadIdx.x; t < n_probs; t += blockDim.x) {
+        const ProblemDev& P = probs[t];
+        sp[t] = SProb{P.tex_c, P.tex_w, P.tex_h, 0, P.F, P.dF};
+    }
+    __syncthreads();
+    const int64_t n = min((int64_t)cnt[CNT_R], rcap);
+    const int64_t nw = (n + 31) & ~(int64_t)31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float4* R = reinterpret_cast<const float4*>(rec);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
+        const bool v = i < n;
+        float4 a = make_float4(0, 0, 0, 0), b = a;
+        if (v) { a = __ldcs(R + 2 * i); b = __ldcs(R + 2 * i + 1); }
+        scatter_one(v, a, b, sp, grad_over, which);
+    }
+}
+
+int run_scatter(const uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
                 float* grad_over, int which, int grid, cudaStream_t st) {
-    MER_TIMED(KC_SCATTER, st, k_scatter<<<grid, 256, 0, st>>>(cnt, rpos, rf, rcap, probs, grad_over, which));
+    MER_TIMED(KC_SCATTER, st, k_scatter<<<grid, 256, 0, st>>>(cnt, rec, rcap, probs, n_probs, grad_over, which));
     return 1;
 }
 

@@ -29,6 +29,7 @@ extern KernelTimer* g_timer;
     } while (0)
 
 struct PassArgs;
+struct Record;
 struct LaunchShape {
     int block;        // threads per block of the wavefront kernels (<= 256)
     int per_sm;       // cap on resident blocks per SM of the persistent grids (0 = occupancy)
@@ -42,7 +43,7 @@ int run_samples_out(const PassArgs& A, float* out, int grid, cudaStream_t st);
 cudaError_t set_trace_smem_limits(int max_nodes);
 
 // grad_over != nullptr: single-problem output; else each record's problem's F (which = 0) or dF (which = 1)
-int run_scatter(const uint32_t* cnt, const uint32_t* rpos, const float* rf, int64_t rcap, const ProblemDev* probs,
+int run_scatter(const uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
                 float* grad_over, int which, int grid, cudaStream_t st);
 // per-problem L2 loss and adjoint images of all problems (pix_pref: prefix of n_pix over problems)
 int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int with_fd,

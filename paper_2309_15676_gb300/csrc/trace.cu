@@ -664,15 +664,15 @@ __global__ void __launch_bounds__(256) k_shade(PassArgs A, int depth) {
                 const uint32_t r = rec_idx[b];
                 if (r >= A.rcap) { set_err(A, MER_ERR_BOUNDS); rec_idx[b] = 0xffffffffu; continue; }
                 const float sg = (b == 1) ? -1.0f : 1.0f;
-                A.rpos[r] = ((uint32_t)q << 24) | ((uint32_t)(foot[b].y0 + 1) << 12) | (uint32_t)(foot[b].x0 + 1);
-                A.rf[(size_t)RF_FX * A.rcap + r] = foot[b].fx;
-                A.rf[(size_t)RF_FY * A.rcap + r] = foot[b].fy;
+                float gv[MAXC];
 #pragma unroll
-                for (int k2 = 0; k2 < MAXC; ++k2) {
-                    float v = sg * gbase[b][k2];
-                    if (merged) v = gbase[0][k2] - gbase[NB - 1][k2];
-                    A.rf[(size_t)(RF_G + k2) * A.rcap + r] = v;
-                }
+                for (int k2 = 0; k2 < MAXC; ++k2)
+                    gv[k2] = merged ? gbase[0][k2] - gbase[NB - 1][k2] : sg * gbase[b][k2];
+                const uint32_t pos =
+                    ((uint32_t)q << 24) | ((uint32_t)(foot[b].y0 + 1) << 12) | (uint32_t)(foot[b].x0 + 1);
+                float4* dst = reinterpret_cast<float4*>(A.rec + r);
+                dst[0] = make_float4(__uint_as_float(pos), foot[b].fx, foot[b].fy, gv[0]);
+                dst[1] = make_float4(gv[1], gv[2], gv[3], gv[4]);
             }
             if (merged) rec_idx[NB - 1] = rec_idx[0];
         }
@@ -803,7 +803,7 @@ __global__ void __launch_bounds__(256) k_shadow(PassArgs A, int depth) {
                 const uint32_t r = A.shu[(SU_REC + b) * C + j];
                 if (r == 0xffffffffu) continue;
 #pragma unroll
-                for (int k = 0; k < MAXC; ++k) A.rf[(size_t)(RF_G + k) * A.rcap + r] += F[(bf + 3 + k) * C + j];
+                for (int k = 0; k < MAXC; ++k) A.rec[r].g[k] += F[(bf + 3 + k) * C + j];
             }
         }
     }

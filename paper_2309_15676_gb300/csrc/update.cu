@@ -91,65 +91,85 @@ __device__ __forceinline__ float adam_elem(const mer_hyper& h, const Coef& k, fl
 #define F4(ptr, i) (reinterpret_cast<float4*>(ptr)[i])
 #define CF4(ptr, i) (reinterpret_cast<const float4*>(ptr)[i])
 
-// processes [blk_begin*CHUNK, ...) of one segment; returns this thread's sum of squared steps
+// one float4 group of every state array
+struct Grp {
+    float4 p, F, dF, m2f, m2d, mean, var, ap;
+};
+
+__device__ __forceinline__ void load_grp(Grp& g, const UpdSeg& S, const float* pin, bool meta, int64_t v) {
+    g.p = CF4(pin, v);
+    g.F = CF4(S.F, v);
+    g.m2f = CF4(S.m2f, v);
+    g.mean = CF4(S.mean, v);
+    if (meta) {
+        g.dF = CF4(S.dF, v);
+        g.m2d = CF4(S.m2d, v);
+        g.var = CF4(S.var, v);
+        g.ap = CF4(S.ap, v);
+    } else {
+        g.dF = g.m2d = g.var = g.ap = make_float4(0, 0, 0, 0);
+    }
+}
+
+// updates one group in registers, stores it, returns the sum of squared applied steps
+__device__ __forceinline__ float proc_grp(Grp& g, const UpdSeg& S, const Coef& k, float* pout, bool meta, int64_t v) {
+    float pv[4] = {g.p.x, g.p.y, g.p.z, g.p.w}, Fv[4] = {g.F.x, g.F.y, g.F.z, g.F.w};
+    float dFv[4] = {g.dF.x, g.dF.y, g.dF.z, g.dF.w}, m2fv[4] = {g.m2f.x, g.m2f.y, g.m2f.z, g.m2f.w};
+    float m2dv[4] = {g.m2d.x, g.m2d.y, g.m2d.z, g.m2d.w}, meanv[4] = {g.mean.x, g.mean.y, g.mean.z, g.mean.w};
+    float varv[4] = {g.var.x, g.var.y, g.var.z, g.var.w}, apv[4] = {g.ap.x, g.ap.y, g.ap.z, g.ap.w};
+    float out[4];
+    float acc = 0.0f;
+    const int C = S.C;
+    const int c0 = (int)((uint32_t)(v * 4) % (uint32_t)C);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        int c = c0 + l;
+        if (c >= C) c -= C;
+        if (c >= C) c -= C;
+        float st;
+        if (meta)
+            st = meta_elem(S.hyper, k, pv[l], Fv[l], dFv[l], m2fv[l], m2dv[l], meanv[l], varv[l], apv[l], S.lo[c],
+                           S.hi[c], out[l]);
+        else
+            st = adam_elem(S.hyper, k, pv[l], Fv[l], m2fv[l], meanv[l], S.lo[c], S.hi[c], out[l]);
+        acc += st * st;
+    }
+    F4(pout, v) = make_float4(out[0], out[1], out[2], out[3]);
+    F4(S.m2f, v) = make_float4(m2fv[0], m2fv[1], m2fv[2], m2fv[3]);
+    F4(S.mean, v) = make_float4(meanv[0], meanv[1], meanv[2], meanv[3]);
+    if (meta) {
+        if (k.stepD) F4(S.m2d, v) = make_float4(m2dv[0], m2dv[1], m2dv[2], m2dv[3]);
+        F4(S.var, v) = make_float4(varv[0], varv[1], varv[2], varv[3]);
+        F4(S.ap, v) = make_float4(apv[0], apv[1], apv[2], apv[3]);
+    }
+    if (S.zero_grads) {
+        F4(S.F, v) = make_float4(0, 0, 0, 0);
+        if (meta) F4(S.dF, v) = make_float4(0, 0, 0, 0);
+    }
+    return acc;
+}
+
+// processes one block's chunk of one segment; returns this thread's sum of squared steps
+// (one float4 group of all state arrays per step keeps registers low and occupancy high)
 __device__ __forceinline__ float update_block(const UpdSeg& S, const Coef& k, int cur, int64_t local_block) {
     const float* pin = cur ? S.pB : S.pA;
     float* pout = cur ? S.pA : S.pB;
     const bool meta = S.hyper.mode == MER_MODE_META;
-    const int C = S.C;
     float acc = 0.0f;
-    const int64_t n4 = S.n >> 2;          // float4 count (n is a multiple of 4 for vector lanes)
+    const int64_t n4 = S.n >> 2;          // float4 count (the tail below handles n % 4)
     const int64_t v0 = local_block * (UPD_CHUNK >> 2);
 #pragma unroll
     for (int it = 0; it < UPD_VEC_PER_THREAD; ++it) {
         const int64_t v = v0 + (int64_t)it * UPD_THREADS + threadIdx.x;
         if (v >= n4) break;
-        const float4 p4 = CF4(pin, v);
-        const float4 F4v = CF4(S.F, v);
-        float4 m2f4 = CF4(S.m2f, v), mean4 = CF4(S.mean, v);
-        float4 dF4 = make_float4(0, 0, 0, 0), m2d4 = dF4, var4 = dF4, ap4 = dF4;
-        if (meta) {
-            dF4 = CF4(S.dF, v);
-            m2d4 = CF4(S.m2d, v);
-            var4 = CF4(S.var, v);
-            ap4 = CF4(S.ap, v);
-        }
-        float pv[4] = {p4.x, p4.y, p4.z, p4.w}, Fv[4] = {F4v.x, F4v.y, F4v.z, F4v.w};
-        float dFv[4] = {dF4.x, dF4.y, dF4.z, dF4.w}, m2fv[4] = {m2f4.x, m2f4.y, m2f4.z, m2f4.w};
-        float m2dv[4] = {m2d4.x, m2d4.y, m2d4.z, m2d4.w}, meanv[4] = {mean4.x, mean4.y, mean4.z, mean4.w};
-        float varv[4] = {var4.x, var4.y, var4.z, var4.w}, apv[4] = {ap4.x, ap4.y, ap4.z, ap4.w};
-        float out[4];
-        const int c0 = (int)((v * 4) % C);
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            int c = c0 + l;
-            if (c >= C) c -= C;
-            if (c >= C) c -= C;
-            float st;
-            if (meta)
-                st = meta_elem(S.hyper, k, pv[l], Fv[l], dFv[l], m2fv[l], m2dv[l], meanv[l], varv[l], apv[l], S.lo[c],
-                               S.hi[c], out[l]);
-            else
-                st = adam_elem(S.hyper, k, pv[l], Fv[l], m2fv[l], meanv[l], S.lo[c], S.hi[c], out[l]);
-            acc += st * st;
-        }
-        F4(pout, v) = make_float4(out[0], out[1], out[2], out[3]);
-        F4(S.m2f, v) = make_float4(m2fv[0], m2fv[1], m2fv[2], m2fv[3]);
-        F4(S.mean, v) = make_float4(meanv[0], meanv[1], meanv[2], meanv[3]);
-        if (meta) {
-            if (k.stepD) F4(S.m2d, v) = make_float4(m2dv[0], m2dv[1], m2dv[2], m2dv[3]);
-            F4(S.var, v) = make_float4(varv[0], varv[1], varv[2], varv[3]);
-            F4(S.ap, v) = make_float4(apv[0], apv[1], apv[2], apv[3]);
-        }
-        if (S.zero_grads) {
-            F4(S.F, v) = make_float4(0, 0, 0, 0);
-            if (meta) F4(S.dF, v) = make_float4(0, 0, 0, 0);
-        }
+        Grp g;
+        load_grp(g, S, pin, meta, v);
+        acc += proc_grp(g, S, k, pout, meta, v);
     }
     // scalar tail (n not a multiple of 4): first block, first threads
     if (local_block == 0 && threadIdx.x < (int)(S.n & 3)) {
         const int64_t e = (n4 << 2) + threadIdx.x;
-        const int c = (int)(e % C);
+        const int c = (int)(e % S.C);
         float m2f = S.m2f[e], mean = S.mean[e], pnew, st;
         if (meta) {
             float m2d = S.m2d[e], var = S.var[e], ap = S.ap[e];

@@ -24,8 +24,13 @@ constexpr int HF_T = 0, HF_B1 = 1, HF_B2 = 2, HF_PER_BRANCH = 3;
 constexpr int SF_O = 0, SF_D = 3, SF_TMAX = 6, SF_SLOT = 7, SF_PER_SLOT = 8;
 // shadow entry words: path id, meta (problem | slot mask << 8), record index per slot
 constexpr int SU_PATH = 0, SU_META = 1, SU_REC = 2;
-// record fields (float): fx, fy, g[5]; position word separately
-constexpr int RF_FX = 0, RF_FY = 1, RF_G = 2, RF_FIELDS = 7;
+// gradient record, 32 B (two 16-byte accesses): footprint word (problem << 24 | (y0+1) << 12 |
+// (x0+1)), bilinear fractions, and the derivative g[5] w.r.t. the fetched channels
+struct __align__(16) Record {
+    uint32_t pos;
+    float fx, fy;
+    float g[5];
+};
 
 constexpr uint32_t FLAG_A = 1u, FLAG_B = 2u, FLAG_COINC = 4u;
 
@@ -59,8 +64,7 @@ struct PassArgs {
     uint32_t* cnt;
     float* lacc;              // [NB*3][qcap] radiance accumulated by this pass
     const float* ltot;        // [NB*3][qcap] radiance of the ADJ_FWD pass (REPLAY)
-    uint32_t* rpos;
-    float* rf;
+    Record* rec;
     int64_t rcap;
     int32_t smem_nodes;       // top BVH nodes of problem smem_prob staged in shared memory
     int32_t smem_prob;
