@@ -93,8 +93,8 @@ namespace {
 thread_local std::string t_err = "no error";
 
 const char* const kClassNames[KC_COUNT] = {
-    "extend_1", "shade_1_primal", "shade_1_replay", "shadow_1_primal", "shadow_1_replay",
-    "extend_2", "shade_2_primal", "shade_2_replay", "shadow_2_primal", "shadow_2_replay",
+    "trace_1_primal", "trace_1_replay", "shade_1_primal", "shade_1_replay",
+    "trace_2_primal", "trace_2_replay", "shade_2_primal", "shade_2_replay",
     "resolve", "l2_loss", "scatter", "update", "update_finalize"};
 
 // CUDA-event timer installed in mer::g_timer while profiling is enabled
@@ -321,11 +321,9 @@ int pass(mer_ctx* c, cudaStream_t st, PassArgs A, int nb, int mode, int maxD) {
         int64_t rays = A.n_paths, sh = 0;
         for (int k = 2; k <= maxD; ++k) rays += h[CNT_Q + k];
         for (int k = 1; k <= maxD; ++k) sh += h[CNT_S + k];
-        const int base = nb == 1 ? KC_EXTEND1 : KC_EXTEND2;
         const int rep = mode == MODE_REPLAY ? 1 : 0;
-        g_timer->add_units(base, rays);
-        g_timer->add_units(base + 1 + rep, rays);
-        g_timer->add_units(base + 3 + rep, sh);
+        g_timer->add_units((nb == 1 ? KC_TRACE1_PRIMAL : KC_TRACE2_PRIMAL) + rep, rays + sh);
+        g_timer->add_units((nb == 1 ? KC_SHADE1_PRIMAL : KC_SHADE2_PRIMAL) + rep, rays);
         if (mode == MODE_REPLAY) g_timer->add_units(KC_SCATTER, h[CNT_R]);
     }
     return n;

@@ -117,7 +117,8 @@ __device__ __forceinline__ void scatter_one(bool valid, float4 a, float4 b, cons
     }
 }
 
-// Grid-stride over records, one per lane (two 16-byte streaming loads each).
+// Persistent grid-stride over records, one per lane (two 16-byte streaming loads each); the
+// next record is loaded while the current one is scattered.
 __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cnt, const Record* __restrict__ rec,
                                                  int64_t rcap, const ProblemDev* __restrict__ probs, int n_probs,
                                                  float* grad_over, int which) {
@@ -131,16 +132,31 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cn
     const int64_t nw = (n + 31) & ~(int64_t)31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float4* R = reinterpret_cast<const float4*>(rec);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
-        const bool v = i < n;
-        float4 a = make_float4(0, 0, 0, 0), b = a;
-        if (v) { a = __ldcs(R + 2 * i); b = __ldcs(R + 2 * i + 1); }
-        scatter_one(v, a, b, sp, grad_over, which);
+    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float4 a = make_float4(0, 0, 0, 0), b = a;
+    if (start < n) { a = __ldcs(R + 2 * start); b = __ldcs(R + 2 * start + 1); }
+    for (int64_t i = start; i < nw; i += stride) {
+        const int64_t j = i + stride;
+        float4 na = make_float4(0, 0, 0, 0), nb = na;
+        if (j < n) { na = __ldcs(R + 2 * j); nb = __ldcs(R + 2 * j + 1); }
+        scatter_one(i < n, a, b, sp, grad_over, which);
+        a = na;
+        b = nb;
     }
 }
 
 int run_scatter(const uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
                 float* grad_over, int which, int grid, cudaStream_t st) {
+    // resident blocks only (the loop is persistent): occupancy x multiprocessors, at most `grid`
+    static int resident = 0;
+    if (!resident) {
+        int occ = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scatter, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+        resident = occ * sms;
+    }
+    grid = grid < resident ? grid : resident;
     MER_TIMED(KC_SCATTER, st, k_scatter<<<grid, 256, 0, st>>>(cnt, rec, rcap, probs, n_probs, grad_over, which));
     return 1;
 }

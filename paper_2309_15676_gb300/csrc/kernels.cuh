@@ -7,8 +7,8 @@ namespace mer {
 
 // launch classes for the optional per-kernel event timing
 enum KernelClass {
-    KC_EXTEND1, KC_SHADE1_PRIMAL, KC_SHADE1_REPLAY, KC_SHADOW1_PRIMAL, KC_SHADOW1_REPLAY,
-    KC_EXTEND2, KC_SHADE2_PRIMAL, KC_SHADE2_REPLAY, KC_SHADOW2_PRIMAL, KC_SHADOW2_REPLAY,
+    KC_TRACE1_PRIMAL, KC_TRACE1_REPLAY, KC_SHADE1_PRIMAL, KC_SHADE1_REPLAY,
+    KC_TRACE2_PRIMAL, KC_TRACE2_REPLAY, KC_SHADE2_PRIMAL, KC_SHADE2_REPLAY,
     KC_RESOLVE, KC_L2, KC_SCATTER, KC_UPDATE, KC_UPDATE_FIN, KC_COUNT
 };
 

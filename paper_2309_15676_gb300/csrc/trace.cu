@@ -379,52 +379,46 @@ __device__ __forceinline__ void flush_counts(const PassArgs& A, int cls, const T
     }
 }
 
+// closest hit of path-queue entry j of depth `depth` (once per coincident pair)
 template <int NB, bool STATS>
-__global__ void __launch_bounds__(256) k_extend(PassArgs A, int depth) {
-    const Node* s_nodes;
-    const int n_staged = stage_nodes(A, s_nodes);
+__device__ __forceinline__ void extend_item(const PassArgs& A, const Node* s_nodes, int n_staged, int depth, int64_t j,
+                                            TravCount& tc) {
     const bool first = depth == 1;
-    const int64_t n = first ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth], A.qcap);
     const int qi = depth & 1;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    TravCount tc;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        uint32_t flags;
-        int q;
-        v3 o[NB], d[NB];
-        if (first) {
-            const PathId id = decode_path(A, j);
-            q = id.q;
-            const ProblemDev& P = A.probs[q];
-            flags = (NB == 2) ? (FLAG_A | FLAG_B | FLAG_COINC) : FLAG_A;
-            if (A.fd_kind && A.iter_override < 0 && A.pstate[q].iteration == 0) flags = 0;
-            const uint4 r = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, 0, 0);
-            camera_ray(P, id.pixel, u01(r.x), u01(r.y), o[0], d[0]);
-            if (NB == 2) { o[NB - 1] = o[0]; d[NB - 1] = d[0]; }
-        } else {
-            flags = A.qu[qi][QU_FLAGS * A.qcap + j];
-            q = (flags >> 8) & 0xff;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const float* f = A.qf[qi] + (size_t)(b * QF_PER_BRANCH) * A.qcap + j;
-                o[b] = mk(f[(QF_O + 0) * A.qcap], f[(QF_O + 1) * A.qcap], f[(QF_O + 2) * A.qcap]);
-                d[b] = mk(f[(QF_D + 0) * A.qcap], f[(QF_D + 1) * A.qcap], f[(QF_D + 2) * A.qcap]);
-            }
-        }
+    uint32_t flags;
+    int q;
+    v3 o[NB], d[NB];
+    if (first) {
+        const PathId id = decode_path(A, j);
+        q = id.q;
         const ProblemDev& P = A.probs[q];
+        flags = (NB == 2) ? (FLAG_A | FLAG_B | FLAG_COINC) : FLAG_A;
+        if (A.fd_kind && A.iter_override < 0 && A.pstate[q].iteration == 0) flags = 0;
+        const uint4 r = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, 0, 0);
+        camera_ray(P, id.pixel, u01(r.x), u01(r.y), o[0], d[0]);
+        if (NB == 2) { o[NB - 1] = o[0]; d[NB - 1] = d[0]; }
+    } else {
+        flags = A.qu[qi][QU_FLAGS * A.qcap + j];
+        q = (flags >> 8) & 0xff;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            if (!(flags & (1u << b))) continue;
-            if (b == 1 && (flags & FLAG_COINC)) continue;
-            Hit h;
-            traverse<false, STATS>(P, s_nodes, q == A.smem_prob ? n_staged : 0, o[b], d[b], INFINITY, h, tc);
-            A.hitf[(size_t)(b * HF_PER_BRANCH + HF_T) * A.qcap + j] = h.t;
-            A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B1) * A.qcap + j] = h.b1;
-            A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B2) * A.qcap + j] = h.b2;
-            A.hitp[(size_t)b * A.qcap + j] = h.prim;
+            const float* f = A.qf[qi] + (size_t)(b * QF_PER_BRANCH) * A.qcap + j;
+            o[b] = mk(f[(QF_O + 0) * A.qcap], f[(QF_O + 1) * A.qcap], f[(QF_O + 2) * A.qcap]);
+            d[b] = mk(f[(QF_D + 0) * A.qcap], f[(QF_D + 1) * A.qcap], f[(QF_D + 2) * A.qcap]);
         }
     }
-    if (STATS) flush_counts(A, NB == 1 ? KC_EXTEND1 : KC_EXTEND2, tc);
+    const ProblemDev& P = A.probs[q];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        if (!(flags & (1u << b))) continue;
+        if (b == 1 && (flags & FLAG_COINC)) continue;
+        Hit h;
+        traverse<false, STATS>(P, s_nodes, q == A.smem_prob ? n_staged : 0, o[b], d[b], INFINITY, h, tc);
+        A.hitf[(size_t)(b * HF_PER_BRANCH + HF_T) * A.qcap + j] = h.t;
+        A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B1) * A.qcap + j] = h.b1;
+        A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B2) * A.qcap + j] = h.b2;
+        A.hitp[(size_t)b * A.qcap + j] = h.prim;
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -771,43 +765,63 @@ __global__ void __launch_bounds__(256) k_shade(PassArgs A, int depth) {
     }
 }
 
-// ---------------------------------------------------------------------------------
-// shadow: any-hit of NEE rays; visible ones add their radiance (and NEE gradient part)
-// ---------------------------------------------------------------------------------
+// any-hit of shadow entry j; if the light is visible, add the NEE radiance to the path's
+// accumulator and (replay) the NEE part of the gradient to its record
 template <int NB, int MODE, bool STATS>
-__global__ void __launch_bounds__(256) k_shadow(PassArgs A, int depth) {
-    const Node* s_nodes;
-    const int n_staged = stage_nodes(A, s_nodes);
-    const int64_t n = min((int64_t)A.cnt[CNT_S + depth], A.shcap);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+__device__ __forceinline__ void shadow_item(const PassArgs& A, const Node* s_nodes, int n_staged, int64_t j,
+                                            TravCount& tc) {
     const size_t C = (size_t)A.shcap;
-    TravCount tc;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const float* F = A.shf;
-        const v3 o = mk(F[(SF_O + 0) * C + j], F[(SF_O + 1) * C + j], F[(SF_O + 2) * C + j]);
-        const v3 d = mk(F[(SF_D + 0) * C + j], F[(SF_D + 1) * C + j], F[(SF_D + 2) * C + j]);
-        const float tmax = F[SF_TMAX * C + j];
-        const uint32_t g = A.shu[SU_PATH * C + j];
-        const uint32_t meta = A.shu[SU_META * C + j];
-        const int q = meta & 0xff;
-        const uint32_t mask = (meta >> 8) & 3u;
-        Hit h;
-        if (traverse<true, STATS>(A.probs[q], s_nodes, q == A.smem_prob ? n_staged : 0, o, d, tmax, h, tc)) continue;
+    const float* F = A.shf;
+    const v3 o = mk(F[(SF_O + 0) * C + j], F[(SF_O + 1) * C + j], F[(SF_O + 2) * C + j]);
+    const v3 d = mk(F[(SF_D + 0) * C + j], F[(SF_D + 1) * C + j], F[(SF_D + 2) * C + j]);
+    const float tmax = F[SF_TMAX * C + j];
+    const uint32_t g = A.shu[SU_PATH * C + j];
+    const uint32_t meta = A.shu[SU_META * C + j];
+    const int q = meta & 0xff;
+    const uint32_t mask = (meta >> 8) & 3u;
+    Hit h;
+    if (traverse<true, STATS>(A.probs[q], s_nodes, q == A.smem_prob ? n_staged : 0, o, d, tmax, h, tc)) return;
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            if (!(mask & (1u << b))) continue;
-            const size_t bf = SF_SLOT + (size_t)b * SF_PER_SLOT;
+    for (int b = 0; b < NB; ++b) {
+        if (!(mask & (1u << b))) continue;
+        const size_t bf = SF_SLOT + (size_t)b * SF_PER_SLOT;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) A.lacc[(size_t)(b * 3 + c) * A.qcap + g] += F[(bf + c) * C + j];
-            if (MODE == MODE_REPLAY) {
-                const uint32_t r = A.shu[(SU_REC + b) * C + j];
-                if (r == 0xffffffffu) continue;
+        for (int c = 0; c < 3; ++c) A.lacc[(size_t)(b * 3 + c) * A.qcap + g] += F[(bf + c) * C + j];
+        if (MODE == MODE_REPLAY) {
+            const uint32_t r = A.shu[(SU_REC + b) * C + j];
+            if (r == 0xffffffffu) continue;
 #pragma unroll
-                for (int k = 0; k < MAXC; ++k) A.rec[r].g[k] += F[(bf + 3 + k) * C + j];
-            }
+            for (int k = 0; k < MAXC; ++k) A.rec[r].g[k] += F[(bf + 3 + k) * C + j];
         }
     }
-    if (STATS) flush_counts(A, (NB == 1 ? KC_SHADOW1_PRIMAL : KC_SHADOW2_PRIMAL) + (MODE == MODE_REPLAY ? 1 : 0), tc);
+}
+
+// ---------------------------------------------------------------------------------
+// trace: one launch consumes two independent queues that shade(depth_ext - 1) produced —
+// the continuation rays of depth depth_ext (closest hit) and the NEE shadow rays of depth
+// depth_sh = depth_ext - 1 (any hit). The first launch of a pass has no shadow rays; the
+// last one has no continuation rays.
+// ---------------------------------------------------------------------------------
+template <int NB, int MODE, bool STATS>
+__global__ void __launch_bounds__(256) k_trace(PassArgs A, int depth_ext, int depth_sh) {
+    const Node* s_nodes;
+    const int n_staged = stage_nodes(A, s_nodes);
+    const int64_t n_ext = depth_ext == 1 ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth_ext], A.qcap);
+    const int64_t n_sh = depth_sh > 0 ? min((int64_t)A.cnt[CNT_S + depth_sh], A.shcap) : 0;
+    const int64_t n = n_ext + n_sh;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    TravCount tc_e, tc_s;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        if (j < n_ext) extend_item<NB, STATS>(A, s_nodes, n_staged, depth_ext, j, tc_e);
+        else shadow_item<NB, MODE, STATS>(A, s_nodes, n_staged, j - n_ext, tc_s);
+    }
+    if (STATS) {
+        const int cls = (NB == 1 ? KC_TRACE1_PRIMAL : KC_TRACE2_PRIMAL) + (MODE == MODE_REPLAY ? 1 : 0);
+        TravCount t;
+        t.nodes = tc_e.nodes + tc_s.nodes;
+        t.prims = tc_e.prims + tc_s.prims;
+        flush_counts(A, cls, t);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -866,45 +880,53 @@ static int persistent_grid(K kernel, const LaunchShape& L, size_t smem) {
 }
 
 template <int NB, int MODE>
-static void launch_depth(const PassArgs& A, int depth, const LaunchShape& L, cudaStream_t st) {
-    const size_t smem = (size_t)L.smem_nodes * sizeof(Node);
-    PassArgs B = A;
-    B.smem_nodes = L.smem_nodes;
-    static int g_ext = 0, g_sh = 0, g_sd = 0;
-    static LaunchShape last{-1, -1, -1, -1};
-    if (last.block != L.block || last.per_sm != L.per_sm || last.smem_nodes != L.smem_nodes || last.sms != L.sms) {
-        g_ext = persistent_grid(k_extend<NB, false>, L, smem);
-        g_sh = persistent_grid(k_shade<NB, MODE>, L, 0);
-        g_sd = persistent_grid(k_shadow<NB, MODE, false>, L, smem);
+struct PassLauncher {
+    int g_trace = 0, g_shade = 0;
+    LaunchShape last{-1, -1, -1, -1};
+
+    void grids(const LaunchShape& L, size_t smem) {
+        if (last.block == L.block && last.per_sm == L.per_sm && last.smem_nodes == L.smem_nodes && last.sms == L.sms)
+            return;
+        g_trace = persistent_grid(k_trace<NB, MODE, false>, L, smem);
+        g_shade = persistent_grid(k_shade<NB, MODE>, L, 0);
         last = L;
     }
-    const int base = NB == 1 ? KC_EXTEND1 : KC_EXTEND2;
-    const int rep = MODE == MODE_REPLAY ? 1 : 0;
-    if (A.stats) {   // counting run: same grids, traversal work counted
-        k_extend<NB, true><<<g_ext, L.block, smem, st>>>(B, depth);
-        k_shade<NB, MODE><<<g_sh, L.block, 0, st>>>(B, depth);
-        k_shadow<NB, MODE, true><<<g_sd, L.block, smem, st>>>(B, depth);
-        return;
+
+    void trace(const PassArgs& B, int de, int ds, const LaunchShape& L, size_t smem, cudaStream_t st) {
+        const int cls = (NB == 1 ? KC_TRACE1_PRIMAL : KC_TRACE2_PRIMAL) + (MODE == MODE_REPLAY ? 1 : 0);
+        if (B.stats) k_trace<NB, MODE, true><<<g_trace, L.block, smem, st>>>(B, de, ds);
+        else MER_TIMED(cls, st, k_trace<NB, MODE, false><<<g_trace, L.block, smem, st>>>(B, de, ds));
     }
-    MER_TIMED(base, st, k_extend<NB, false><<<g_ext, L.block, smem, st>>>(B, depth));
-    MER_TIMED(base + 1 + rep, st, k_shade<NB, MODE><<<g_sh, L.block, 0, st>>>(B, depth));
-    MER_TIMED(base + 3 + rep, st, k_shadow<NB, MODE, false><<<g_sd, L.block, smem, st>>>(B, depth));
-}
+
+    void shade(const PassArgs& B, int depth, const LaunchShape& L, cudaStream_t st) {
+        const int cls = (NB == 1 ? KC_SHADE1_PRIMAL : KC_SHADE2_PRIMAL) + (MODE == MODE_REPLAY ? 1 : 0);
+        if (B.stats) k_shade<NB, MODE><<<g_shade, L.block, 0, st>>>(B, depth);
+        else MER_TIMED(cls, st, k_shade<NB, MODE><<<g_shade, L.block, 0, st>>>(B, depth));
+    }
+
+    // trace(1) shade(1) trace(2, 1) shade(2) ... shade(D) trace(-, D): 2D + 1 launches
+    int run(const PassArgs& A, int max_depth, const LaunchShape& L, cudaStream_t st) {
+        const size_t smem = (size_t)L.smem_nodes * sizeof(Node);
+        PassArgs B = A;
+        B.smem_nodes = L.smem_nodes;
+        grids(L, smem);
+        for (int depth = 1; depth <= max_depth; ++depth) {
+            trace(B, depth, depth - 1, L, smem, st);
+            shade(B, depth, L, st);
+        }
+        trace(B, max_depth + 1, max_depth, L, smem, st);
+        return 2 * max_depth + 1;
+    }
+};
 
 // enqueues one full pass; returns the number of kernel launches
 int run_pass(const PassArgs& A, int nb, int mode, int max_depth, const LaunchShape& L, cudaStream_t st) {
-    int launches = 0;
-    for (int depth = 1; depth <= max_depth; ++depth) {
-        if (nb == 1) {
-            if (mode == MODE_REPLAY) launch_depth<1, MODE_REPLAY>(A, depth, L, st);
-            else launch_depth<1, MODE_PRIMAL>(A, depth, L, st);
-        } else {
-            if (mode == MODE_REPLAY) launch_depth<2, MODE_REPLAY>(A, depth, L, st);
-            else launch_depth<2, MODE_PRIMAL>(A, depth, L, st);
-        }
-        launches += 3;
-    }
-    return launches;
+    static PassLauncher<1, MODE_PRIMAL> p1;
+    static PassLauncher<1, MODE_REPLAY> r1;
+    static PassLauncher<2, MODE_PRIMAL> p2;
+    static PassLauncher<2, MODE_REPLAY> r2;
+    if (nb == 1) return mode == MODE_REPLAY ? r1.run(A, max_depth, L, st) : p1.run(A, max_depth, L, st);
+    return mode == MODE_REPLAY ? r2.run(A, max_depth, L, st) : p2.run(A, max_depth, L, st);
 }
 
 int run_resolve(const PassArgs& A, int nb, float* img0, float* img1, int accumulate, int grid, cudaStream_t st) {
@@ -921,12 +943,10 @@ int run_samples_out(const PassArgs& A, float* out, int grid, cudaStream_t st) {
 cudaError_t set_trace_smem_limits(int max_nodes) {
     const int bytes = max_nodes * (int)sizeof(Node);
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    const void* fns[] = {(const void*)k_extend<1, false>,          (const void*)k_extend<2, false>,
-                         (const void*)k_extend<1, true>,           (const void*)k_extend<2, true>,
-                         (const void*)k_shadow<1, MODE_PRIMAL, false>, (const void*)k_shadow<1, MODE_REPLAY, false>,
-                         (const void*)k_shadow<2, MODE_PRIMAL, false>, (const void*)k_shadow<2, MODE_REPLAY, false>,
-                         (const void*)k_shadow<1, MODE_PRIMAL, true>,  (const void*)k_shadow<1, MODE_REPLAY, true>,
-                         (const void*)k_shadow<2, MODE_PRIMAL, true>,  (const void*)k_shadow<2, MODE_REPLAY, true>};
+    const void* fns[] = {(const void*)k_trace<1, MODE_PRIMAL, false>, (const void*)k_trace<1, MODE_REPLAY, false>,
+                         (const void*)k_trace<2, MODE_PRIMAL, false>, (const void*)k_trace<2, MODE_REPLAY, false>,
+                         (const void*)k_trace<1, MODE_PRIMAL, true>,  (const void*)k_trace<1, MODE_REPLAY, true>,
+                         (const void*)k_trace<2, MODE_PRIMAL, true>,  (const void*)k_trace<2, MODE_REPLAY, true>};
     for (const void* f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, at, bytes);
         if (e) return e;
