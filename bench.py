@@ -189,12 +189,13 @@ def eval_loss(torch, ctx, pid, target, spp=64):
 
 def time_to_threshold(torch, w, target_img, max_iters, lrs=(0.001, 0.003, 0.01, 0.03), frac=0.05):
     """Iterations and GPU time (iterations only, evaluation excluded) until the 64-spp eval loss
-    drops below `frac` of its initial value: meta-estimator (1 FD + 2 proportional spp) vs Adam on
-    3 fresh proportional spp (equal spp per iteration), each at its best learning rate of the grid.
-    Evaluated every 2 iterations for the first 50, then every 10."""
+    drops below `frac` of its initial value: meta-estimator (the workload's 1 FD + n proportional
+    spp) vs Adam on n+1 fresh proportional spp (equal spp per iteration), each at its best learning
+    rate of the grid. Evaluated every 2 iterations for the first 50, then every 10."""
     from paper_2309_15676_gb300.api import Context, HyperParams, MODE_ADAM, MODE_META
     out = {}
-    for name, mode, spp_prop, spp_fd in (("meta", MODE_META, 2, 1), ("adam", MODE_ADAM, 3, 0)):
+    pp, pf = w.scene["spp_prop"], w.scene["spp_fd"]
+    for name, mode, spp_prop, spp_fd in (("meta", MODE_META, pp, pf), ("adam", MODE_ADAM, pp + pf, 0)):
         best, runs = None, []
         for lr in lrs:
             sc = dict(w.scene)
@@ -515,7 +516,17 @@ def run_mine(args):
     cpu = None
     ttt = None
     if rank == 0 and not args.no_ttt:
-        ttt = time_to_threshold(torch, w, target_img, args.ttt_iters)
+        ttt = {"spiral256 (learning rate tuned per method)":
+               time_to_threshold(torch, w, target_img, args.ttt_iters)}
+        # config 1 as stated: 64x64 box, 32x32 RGB albedo, depth 3, 1 FD + 1 proportional spp, lr 0.01,
+        # 50 iterations (Adam on 2 fresh spp)
+        from paper_2309_15676_gb300 import synth as _s
+        wb = _s.workload_box()
+        cb = Context(local, max_paths=1 << 20)
+        pb = cb.add_scene(wb.scene, HyperParams())
+        tb = cb.render(pb, torch.from_numpy(wb.target_tex).cuda(), spp=256, stream=4, iteration=0).clone()
+        cb.close()
+        ttt["box64 (config 1: lr 0.01, 50 iterations)"] = time_to_threshold(torch, wb, tb, 50, lrs=(0.01,))
     batched = batched_compare(torch) if (rank == 0 and not args.no_batch) else None
     scale = scale_profile(torch, hbm_peak, args.scale_image) if (rank == 0 and not args.no_scale) else None
     if rank == 0 and not args.no_cpu:
