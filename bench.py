@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-scale", action="store_true", help="skip the 1024^2 / 205k-triangle roofline leg")
     ap.add_argument("--only-scale", action="store_true", help="run only the scale leg (for profiling)")
     ap.add_argument("--scale-image", type=int, default=1024, help="image side of the scale leg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -400,6 +401,8 @@ def run_mine(args):
     assert paths_per_iter == PATHS_PER_PIXEL * npix
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
+    # launch shapes picked by the library's autotuner on this workload (state restored afterwards)
+    tuned = ctx.autotune(3) if not args.no_autotune else "defaults"
     # warm-up (captures the iteration graph)
     ctx.iterate(max(args.warmup, 3), use_graph=True)
     torch.cuda.synchronize()
@@ -543,7 +546,7 @@ def run_mine(args):
                 "roofline": roof, "rooflines": rooflines + ([upd67] if upd67 else []),
                 "kernels": kernels, "peak_source": peak_kind,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-                "gpu_launches": int(launches_per_iter * args.steps),
+                "gpu_launches": int(launches_per_iter * args.steps), "launch_shapes": tuned,
                 "time_to_threshold": ttt, "batched": batched, "scale": scale}
         print(json.dumps(line), flush=True)
     if dist:
