@@ -290,6 +290,28 @@ def batched_compare(torch, n_problems=64, iters=3, seed=4):
     return out
 
 
+def touched_texels(ctx, pid):
+    """Texels that receive gradient in one gradient step: (proportional F, finite-difference dF).
+    Runs a1-a10 once, reads both gradient textures, then applies the update (which clears them);
+    callers rewind the state afterwards."""
+    ctx.gradient_step()
+    F, dF = ctx.grads(pid)
+    t = (int((F != 0).any(-1).sum()), int((dF != 0).any(-1).sum()))
+    ctx.update_step()
+    return t
+
+
+def scatter_roofline(p, touched, C, hbm_peak):
+    """Algorithmic bytes of the scatter: every record read once (32 B) plus one read-modify-write of
+    each touched texel's C floats per launch (the proportional and the finite-difference launch)."""
+    byts = p["units"] * 32 + 2 * 4 * C * (touched[0] + touched[1]) * (p["launches"] // 2)
+    gbs = byts / (p["ms"] * 1e-3) / 1e9
+    return {"kernel": "scatter", "bound": "hbm", "records_per_launch": p["units"] / p["launches"],
+            "touched_texels": list(touched), "bytes_per_launch": byts / p["launches"],
+            "ms": p["ms"] / p["launches"], "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": gbs / hbm_peak}
+
+
 def scale_profile(torch, hbm_peak, image=1024):
     """1024^2 image, displaced sphere of 204,800 triangles, 2048^2 x 5 textures, env + 4 area lights,
     depth 8, 4 FD + 4 proportional spp: iteration throughput and the scatter / update rooflines
@@ -315,20 +337,16 @@ def scale_profile(torch, hbm_peak, image=1024):
     ctx.iterate(1, use_graph=False)
     prof = ctx.profile_read()
     ctx.profile(0)
+    touched = touched_texels(ctx, pid)
     ctx.close()
     C, H, W = sc["tex_c"], sc["tex_h"], sc["tex_w"]
     out = {"workload": "dsphere1024: 1024^2, 204,800 triangles, 2048^2x5 textures, depth 8, 4 FD + 4 prop spp",
            "ms_per_iter": ms, "paths_per_iter": paths, "paths_per_s": paths * 1e3 / ms, "rooflines": []}
     if "scatter" in prof:
-        p = prof["scatter"]
-        byts = p["units"] * (4 + 4 * (2 + C)) + p["launches"] * 2 * 4 * H * W * C
-        gbs = byts / (p["ms"] * 1e-3) / 1e9
-        out["rooflines"].append({"kernel": "scatter", "bound": "hbm", "records": p["units"], "launches": p["launches"],
-                                 "bytes": byts, "ms": p["ms"], "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                                 "frac": gbs / hbm_peak})
+        out["rooflines"].append(scatter_roofline(prof["scatter"], touched, C, hbm_peak))
     if "update" in prof:
         p = prof["update"]
-        byts = 64 * p["units"]
+        byts = 56 * p["units"]      # F and dF are cleared by the gradient step, not here
         gbs = byts / (p["ms"] * 1e-3) / 1e9
         out["rooflines"].append({"kernel": "update (META, in the iteration)", "bound": "hbm", "params": p["units"],
                                  "bytes": byts, "ms": p["ms"], "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -447,6 +465,8 @@ def run_mine(args):
     counts = ctx.profile_read()
     ctx.profile(0)
     ctx.checkpoint_load(blob)
+    touched = touched_texels(ctx, pid)
+    ctx.checkpoint_load(blob)
     tot = sum(v["ms"] for v in prof.values())
     kernels = {k: {"launches_per_iter": v["launches"] / n_prof, "ms_per_iter": v["ms"] / n_prof,
                    "share": v["ms"] / tot, "units_per_iter": v["units"] / n_prof} for k, v in prof.items()}
@@ -455,18 +475,10 @@ def run_mine(args):
     # ---- rooflines ----
     rooflines = []
     if "scatter" in prof:
-        p = prof["scatter"]
-        rec_bytes = 4 + 4 * (2 + sc["tex_c"])
-        per_launch_units = p["units"] / p["launches"]
-        byts = per_launch_units * rec_bytes + 2 * 4 * sc["tex_h"] * sc["tex_w"] * sc["tex_c"]
-        avg_ms = p["ms"] / p["launches"]
-        gbs = byts / (avg_ms * 1e-3) / 1e9
-        rooflines.append({"kernel": "scatter", "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                          "frac": gbs / hbm_peak, "bytes_per_launch": byts, "records_per_launch": per_launch_units,
-                          "ms": avg_ms})
+        rooflines.append(scatter_roofline(prof["scatter"], touched, sc["tex_c"], hbm_peak))
     if "update" in prof:
         p = prof["update"]
-        byts = 64 * p["units"] / p["launches"]
+        byts = 56 * p["units"] / p["launches"]      # no clearing of F, dF in the iteration
         avg_ms = p["ms"] / p["launches"]
         gbs = byts / (avg_ms * 1e-3) / 1e9
         rooflines.append({"kernel": "update", "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",

@@ -175,12 +175,14 @@ mer_status mer_render_pair(mer_ctx* ctx, int32_t pid, const float* texA_dev, con
                            int32_t spp, uint32_t stream, uint32_t iteration, float* imgA_dev, float* imgB_dev);
 
 /* Steps a1-a10 of one iteration for every problem: the proportional gradient <F_i> and (META
- * problems, iteration >= 1) the FD gradient <dF_i>, accumulated into the context's F and dF. */
+ * problems, iteration >= 1) the FD gradient <dF_i>, accumulated into the context's F and dF,
+ * each cleared right before its scatter (after the call they hold this step's gradients). */
 mer_status mer_gradient_step(mer_ctx* ctx);
 /* Copy a problem's current F and dF (texture-shaped) out (host: synchronous). */
 mer_status mer_grads_get(mer_ctx* ctx, int32_t pid, float* F_out, float* dF_out, int32_t on_device);
 /* Step a11 for every problem: the fused meta-estimator (or Adam) update, pi_{i+1} written over
- * pi_{i-1}, F and dF zeroed, ||pi_{i+1} - pi_i||^2 reduced, iteration advanced. */
+ * pi_{i-1}, ||pi_{i+1} - pi_i||^2 reduced, iteration advanced. F and dF are left as they are
+ * (the next gradient step clears them). */
 mer_status mer_update_step(mer_ctx* ctx);
 /* n_iters full iterations (gradient + update) of all problems; use_graph = 1 replays one
  * captured CUDA graph per iteration (captured on first use). */

@@ -95,7 +95,7 @@ thread_local std::string t_err = "no error";
 const char* const kClassNames[KC_COUNT] = {
     "trace_1_primal", "trace_1_replay", "shade_1_primal", "shade_1_replay",
     "trace_2_primal", "trace_2_replay", "shade_2_primal", "shade_2_replay",
-    "resolve", "l2_loss", "scatter", "update", "update_finalize"};
+    "resolve", "l2_loss", "zero_grads", "scatter", "update", "update_finalize"};
 
 // CUDA-event timer installed in mer::g_timer while profiling is enabled
 struct EventTimer : KernelTimer {
@@ -406,6 +406,10 @@ int enqueue_gradient(mer_ctx* c) {
     P.stream = MER_STREAM_PROP_ADJ;
     P.ltot = c->w[2].ltot;
     n += pass(c, s[0], P, 1, MODE_REPLAY, c->maxD_prop);
+    // F is cleared right before its scatter, so that the reductions find its lines in L2
+    n += run_zero_grads(c->d_probs, (int)c->probs.size(), 0, G, s[0]);
+    if (g_timer)
+        for (Problem* p : c->probs) g_timer->add_units(KC_ZERO, p->n_par);
     n += run_scatter(c->w[0].cnt, c->w[0].rec, c->w[0].rcap, c->d_probs, (int)c->probs.size(), nullptr, 0, G, s[0]);
     // finite-difference gradient <dF_i> (Eq. est_triv): the same for the pair, scatter into dF
     if (have_fd) {
@@ -413,6 +417,9 @@ int enqueue_gradient(mer_ctx* c) {
         D.stream = MER_STREAM_FD_ADJ;
         D.ltot = c->w[3].ltot;
         n += pass(c, s[1], D, 2, MODE_REPLAY, c->maxD_fd);
+        n += run_zero_grads(c->d_probs, (int)c->probs.size(), 1, G, s[1]);
+        if (g_timer)
+            for (Problem* p : c->probs) g_timer->add_units(KC_ZERO, p->n_par);
         n += run_scatter(c->w[1].cnt, c->w[1].rec, c->w[1].rcap, c->d_probs, (int)c->probs.size(), nullptr, 1, G, s[1]);
     }
     join(2);
@@ -433,7 +440,8 @@ mer_status check_err_word(mer_ctx* c) {
         CK(c, cudaMemcpy(&e, w.cnt + CNT_ERR, sizeof e, cudaMemcpyDeviceToHost));
         if (e) {
             cudaMemset(w.cnt + CNT_ERR, 0, sizeof(uint32_t));
-            return fail(c, (int)e, "a kernel reported an out-of-capacity write (code %u)", e);
+            return fail(c, (int)e, "a kernel reported %s (code %u)",
+                        e == MER_ERR_TIMEOUT ? "a bounded wait that ran out" : "an out-of-capacity write", e);
         }
     }
     return MER_OK;
@@ -916,7 +924,7 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     S.n = p->n_par;
     S.C = p->C;
     S.prob = p->id;
-    S.zero_grads = 1;
+    S.zero_grads = 0;        // the gradient step clears F and dF right before their scatters
     for (int k = 0; k < 8; ++k) {
         S.lo[k] = p->lo[k];
         S.hi[k] = p->hi[k];

@@ -25,44 +25,10 @@ __device__ __forceinline__ float peer_sum(unsigned vmask, unsigned peers, float 
     return acc;
 }
 
-// Adds v[0..len) to the contiguous floats base[f0 ..) with the widest aligned vector
-// reductions available (float4 where 16-byte aligned, float2 where 8-byte aligned, else
-// scalar); base itself must be 16-byte aligned. Unrolled so that v stays in registers.
-__device__ __forceinline__ void red_run(float* base, int64_t f0, const float (&v)[13], int len) {
-    int s = 0;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-        if (k == s && k < len) {
-            const int64_t f = f0 + k;
-            const int rem = len - k;
-            if ((f & 3) == 0 && rem >= 4) {
-                atomicAdd(reinterpret_cast<float4*>(base + f), make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]));
-                s += 4;
-            } else if ((f & 1) == 0 && rem >= 2) {
-                atomicAdd(reinterpret_cast<float2*>(base + f), make_float2(v[k], v[k + 1]));
-                s += 2;
-            } else {
-                atomicAdd(base + f, v[k]);
-                s += 1;
-            }
-        }
-    }
-}
-
-template <int CC>
-__device__ __forceinline__ void fill_rows(float (&v)[2][13], const float (&g)[MAXC], float w00, float w10, float w01,
-                                          float w11) {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const float wa = r ? w01 : w00, wb = r ? w11 : w10;
-#pragma unroll
-        for (int k = 0; k < 13; ++k) v[r][k] = 0.0f;
-#pragma unroll
-        for (int c = 0; c < CC; ++c) {
-            v[r][c] = wa * g[c];
-            v[r][CC + c] = wb * g[c];   // ignored beyond the run length when the taps merged
-        }
-    }
+// Fire-and-forget reduction: no value comes back, so the issuing warp never waits on the L2
+// (the vector atomicAdd overloads return the old value and compile to waiting atomics)
+__device__ __forceinline__ void red_add(float* p, float a) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(a) : "memory");
 }
 
 // per-problem fields the scatter needs, cached in shared memory
@@ -72,92 +38,282 @@ struct SProb {
     float* dF;
 };
 
-// One record: adds w_k g[c] to the four bilinear taps (clamp-to-edge) of the problem's HWC
-// gradient texture. The two taps of a row are adjacent texels, i.e. one run of up to 2C
-// contiguous floats, issued as aligned vector reductions (taps that clamp onto the same texel
-// are merged first). Lanes holding the same footprint origin are merged with __match_any_sync
-// and a segmented shuffle sum; only the group's first lane issues the reductions. Lanes whose
-// record is absent or all-zero sit out; every shuffle runs over exactly the participating lanes.
-__device__ __forceinline__ void scatter_one(bool valid, float4 a, float4 b, const SProb* sp, float* grad_over,
-                                            int which) {
-    const uint32_t pos = __float_as_uint(a.x);
-    float g[MAXC] = {a.w, b.x, b.y, b.z, b.w};
-    valid = valid && (g[0] != 0.0f || g[1] != 0.0f || g[2] != 0.0f || g[3] != 0.0f || g[4] != 0.0f);
-    const unsigned vmask = __ballot_sync(FULLM, valid);
-    if (!valid) return;
-    const SProb P = sp[pos >> 24];
-    const int C = P.C, W = P.W, H = P.H;
-    const int x0 = (int)(pos & 0xfff) - 1, y0 = (int)((pos >> 12) & 0xfff) - 1;
-    const float fx = a.y, fy = a.z;
-    const int xa = max(x0, 0), xb = min(x0 + 1, W - 1), ya = max(y0, 0), yb = min(y0 + 1, H - 1);
-    float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
-    const bool one_x = xa == xb, one_y = ya == yb;
-    if (one_x) { w00 += w10; w10 = 0.0f; w01 += w11; w11 = 0.0f; }
-    if (one_y) { w00 += w01; w10 += w11; w01 = 0.0f; w11 = 0.0f; }
-    // row r holds [tap xa channels..., tap xb channels...] (compile-time indices per C)
-    float v[2][13];
-    if (C == 5) fill_rows<5>(v, g, w00, w10, w01, w11);
-    else fill_rows<3>(v, g, w00, w10, w01, w11);
-    const unsigned peers = __match_any_sync(vmask, pos);
-    const int maxg = (int)__reduce_max_sync(vmask, (unsigned)__popc(peers));
-    bool issue = true;
-    if (maxg > 1) {
-        // same pos => same problem and layout; every participating lane runs every shuffle
+template <int CC>
+__device__ __forceinline__ void fill_row(float (&v)[10], const float (&g)[MAXC], float wa, float wb) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int k = 0; k < 10; ++k) v[r][k] = peer_sum(vmask, peers, v[r][k], maxg);
-        issue = (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
-    }
-    if (issue) {
-        float* base = grad_over ? grad_over : (which ? P.dF : P.F);
-        const int len = (one_x ? 1 : 2) * C;
-        red_run(base, ((int64_t)ya * W + xa) * C, v[0], len);
-        if (!one_y) red_run(base, ((int64_t)yb * W + xa) * C, v[1], len);
+    for (int c = 0; c < CC; ++c) {
+        v[c] = wa * g[c];
+        v[CC + c] = wb * g[c];   // ignored beyond the run length when the taps merged
     }
 }
 
-// Persistent grid-stride over records, one per lane (two 16-byte streaming loads each); the
-// next record is loaded while the current one is scattered.
-__global__ void __launch_bounds__(256) k_scatter(const uint32_t* __restrict__ cnt, const Record* __restrict__ rec,
-                                                 int64_t rcap, const ProblemDev* __restrict__ probs, int n_probs,
-                                                 float* grad_over, int which) {
-    __shared__ SProb sp[MER_MAX_PROBLEMS];
+// ---- staging: per-warp bulk-copy (TMA) ring of records and per-record reduction rows ----
+
+constexpr int SC_THREADS = 256;
+constexpr int SC_WARPS = SC_THREADS / 32;
+constexpr int SC_STAGES = 3;                        // chunks in flight per warp
+constexpr int SC_CHUNK = 32;                        // records per chunk (one per lane in phase 1)
+constexpr int SC_ROWS = 2 * SC_CHUNK;               // bilinear rows of a chunk
+constexpr uint32_t SC_WAIT_POLLS = 1u << 20;        // bound on the polls of one stage barrier
+constexpr uint64_t SC_WAIT_NS = 200000000ull;       // and on its wall time (0.2 s)
+constexpr uint32_t SC_SUSPEND_NS = 1000;            // suspend hint of one poll
+
+// one non-empty bilinear row of a chunk: where its run starts, how long it is, where its values are
+struct __align__(16) RowEnt {
+    float* addr;
+    int len;                            // C or 2C floats
+    int vidx;                           // index of its first value in WarpArea::vals
+};
+
+struct __align__(16) WarpArea {
+    Record ring[SC_STAGES][SC_CHUNK];   // records, filled by bulk copies
+    float vals[SC_CHUNK * 20];          // weighted row values of each record: row 0 then row 1
+    RowEnt rows[SC_ROWS];               // the chunk's non-empty rows, compacted
+};
+constexpr size_t SC_HEAD = 256;         // stage barriers, then the warp areas, then the problem table
+
+size_t scatter_smem(int n_probs) { return SC_HEAD + sizeof(WarpArea) * SC_WARPS + sizeof(SProb) * (size_t)n_probs; }
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// one elected lane: arm the stage barrier with the byte count, then start the bulk copy that
+// completes it (source and destination 16-byte aligned, size a multiple of 16). The records are
+// read once: the copy marks their lines evict-first so that they do not push the gradient
+// texture out of L2.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(SC_SUSPEND_NS)
+        : "memory");
+    return done != 0;
+}
+
+// polls the barrier phase with the given parity; false once SC_WAIT_NS have passed (or after
+// SC_WAIT_POLLS polls) without the phase completing. The clock is read only after a first
+// unsuccessful poll.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    if (mbar_try(a, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t k = 0; k < SC_WAIT_POLLS; ++k) {
+        if (mbar_try(a, parity)) return true;
+        if ((k & 15u) == 15u && global_ns() - t0 > SC_WAIT_NS) return false;
+    }
+    return false;
+}
+
+// Phase 1, one record per lane: the bilinear footprint (clamp-to-edge) of the record's texel
+// window becomes two rows of up to 2C contiguous floats (taps xa, xb of texel rows ya, yb;
+// taps that clamp onto the same texel are merged first) holding w_k g[c]. Lanes holding the same
+// footprint origin are merged with __match_any_sync and a segmented shuffle sum over both rows,
+// run by every participating lane; the group's first lane keeps the rows. Lanes whose record is
+// absent or all-zero sit out. The values go to the warp's area and the non-empty rows to a
+// compacted list (ballot + prefix count); returns the number of rows, the same on every lane.
+__device__ __forceinline__ int stage_record(bool valid, float4 a, float4 b, const SProb* sp, float* grad_over,
+                                            int which, WarpArea& WA, int lane) {
+    const uint32_t pos = __float_as_uint(a.x);
+    const float g[MAXC] = {a.w, b.x, b.y, b.z, b.w};
+    valid = valid && (g[0] != 0.0f || g[1] != 0.0f || g[2] != 0.0f || g[3] != 0.0f || g[4] != 0.0f);
+    const unsigned vmask = __ballot_sync(FULLM, valid);
+    bool r0 = false, r1 = false;
+    int off0 = 0, off1 = 0, len = 0;
+    float* base = nullptr;
+    float v0[10], v1[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v0[k] = v1[k] = 0.0f;
+    if (valid) {
+        const SProb P = sp[pos >> 24];
+        const int C = P.C, W = P.W, H = P.H;
+        const int x0 = (int)(pos & 0xfff) - 1, y0 = (int)((pos >> 12) & 0xfff) - 1;
+        const float fx = a.y, fy = a.z;
+        const int xa = max(x0, 0), xb = min(x0 + 1, W - 1), ya = max(y0, 0), yb = min(y0 + 1, H - 1);
+        float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
+        const bool one_x = xa == xb, one_y = ya == yb;
+        if (one_x) { w00 += w10; w10 = 0.0f; w01 += w11; w11 = 0.0f; }
+        if (one_y) { w00 += w01; w10 += w11; w01 = 0.0f; w11 = 0.0f; }
+        if (C == 5) { fill_row<5>(v0, g, w00, w10); fill_row<5>(v1, g, w01, w11); }
+        else { fill_row<3>(v0, g, w00, w10); fill_row<3>(v1, g, w01, w11); }
+        len = (one_x ? 1 : 2) * C;
+        // texture extents are below 4096 per side and C <= 5: offsets fit in 32 bits
+        off0 = (ya * W + xa) * C;
+        off1 = (yb * W + xa) * C;
+        base = grad_over ? grad_over : (which ? P.dF : P.F);
+        r0 = true;
+        r1 = !one_y;
+        // same pos => same problem and layout; every lane of vmask runs every shuffle
+        const unsigned peers = __match_any_sync(vmask, pos);
+        const int maxg = (int)__reduce_max_sync(vmask, (unsigned)__popc(peers));
+        if (maxg > 1) {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) {
+                v0[k] = peer_sum(vmask, peers, v0[k], maxg);
+                v1[k] = peer_sum(vmask, peers, v1[k], maxg);
+            }
+            if (lane != __ffs(peers) - 1) r0 = r1 = false;
+        }
+    }
+    const unsigned m0 = __ballot_sync(FULLM, r0), m1 = __ballot_sync(FULLM, r1);
+    const unsigned below = (1u << lane) - 1u;
+    const int n0 = __popc(m0);
+    if (r0) WA.rows[__popc(m0 & below)] = RowEnt{base + off0, len, 20 * lane};
+    if (r1) WA.rows[n0 + __popc(m1 & below)] = RowEnt{base + off1, len, 20 * lane + 10};
+    if (r0) {
+        float4* d = reinterpret_cast<float4*>(WA.vals + 20 * lane);
+        d[0] = make_float4(v0[0], v0[1], v0[2], v0[3]);
+        d[1] = make_float4(v0[4], v0[5], v0[6], v0[7]);
+        d[2] = make_float4(v0[8], v0[9], v1[0], v1[1]);
+        d[3] = make_float4(v1[2], v1[3], v1[4], v1[5]);
+        d[4] = make_float4(v1[6], v1[7], v1[8], v1[9]);
+    }
+    return n0 + __popc(m1);
+}
+
+// Phase 2, ten lanes per row and three rows per step over the compacted rows: each reduction
+// instruction adds up to three contiguous runs of 2C floats, which the load/store unit packs into
+// one request per 32-byte sector (about two per row) instead of one per vector reduction and lane.
+__device__ __forceinline__ void reduce_rows(const WarpArea& WA, int lane, int nrows) {
+    const int slot = lane / 10, e = lane - 10 * slot;
+    for (int q = slot; q - slot < nrows; q += 3) {
+        if (slot < 3 && q < nrows) {
+            const RowEnt R = WA.rows[q];
+            if (e < R.len) red_add(R.addr + e, WA.vals[R.vidx + e]);
+        }
+    }
+}
+
+// Persistent over chunks of 32 records: warp w of the grid takes chunks w, w + total_warps, ...
+// Lane 0 keeps SC_STAGES bulk copies (1 KB each) in flight into the warp's shared-memory ring;
+// every lane reads its record once the stage's barrier completes, the ring slot is refilled with
+// the chunk SC_STAGES ahead, and the chunk is staged (phase 1) and reduced (phase 2) while the
+// copies are in flight. A barrier that does not complete within its bound stops the warp,
+// records MER_ERR_TIMEOUT in the error word and waits (bounded) for its copies still in flight.
+__global__ void __launch_bounds__(SC_THREADS) k_scatter(uint32_t* __restrict__ cnt, const Record* __restrict__ rec,
+                                                        int64_t rcap, const ProblemDev* __restrict__ probs,
+                                                        int n_probs, float* grad_over, int which) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
+    WarpArea* areas = reinterpret_cast<WarpArea*>(sm + SC_HEAD);
+    SProb* sp = reinterpret_cast<SProb*>(sm + SC_HEAD + sizeof(WarpArea) * SC_WARPS);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    WarpArea& WA = areas[wib];
+    uint64_t* bar = bars + wib * SC_STAGES;
     for (int t = threadIdx.x; t < n_probs; t += blockDim.x) {
         const ProblemDev& P = probs[t];
         sp[t] = SProb{P.tex_c, P.tex_w, P.tex_h, 0, P.F, P.dF};
     }
+    if (lane == 0)
+        for (int s = 0; s < SC_STAGES; ++s) mbar_init(&bar[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
+
     const int64_t n = min((int64_t)cnt[CNT_R], rcap);
-    const int64_t nw = (n + 31) & ~(int64_t)31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const float4* R = reinterpret_cast<const float4*>(rec);
-    const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float4 a = make_float4(0, 0, 0, 0), b = a;
-    if (start < n) { a = __ldcs(R + 2 * start); b = __ldcs(R + 2 * start + 1); }
-    for (int64_t i = start; i < nw; i += stride) {
-        const int64_t j = i + stride;
-        float4 na = make_float4(0, 0, 0, 0), nb = na;
-        if (j < n) { na = __ldcs(R + 2 * j); nb = __ldcs(R + 2 * j + 1); }
-        scatter_one(i < n, a, b, sp, grad_over, which);
-        a = na;
-        b = nb;
+    const int64_t nchunks = (n + SC_CHUNK - 1) / SC_CHUNK;
+    const int64_t gw = (int64_t)blockIdx.x * SC_WARPS + wib, tw = (int64_t)gridDim.x * SC_WARPS;
+    const int64_t my = nchunks > gw ? (nchunks - gw + tw - 1) / tw : 0;   // chunks of this warp
+    auto issue = [&](int64_t k) {
+        const int64_t first = (gw + k * tw) * SC_CHUNK;
+        const uint32_t cnt_k = (uint32_t)min((int64_t)SC_CHUNK, n - first);
+        bulk_load(WA.ring[k % SC_STAGES], rec + first, cnt_k * (uint32_t)sizeof(Record), &bar[k % SC_STAGES]);
+    };
+    if (lane == 0)
+        for (int64_t k = 0; k < min(my, (int64_t)SC_STAGES); ++k) issue(k);
+    for (int64_t k = 0; k < my; ++k) {
+        const int s = (int)(k % SC_STAGES);
+        const bool ok = mbar_wait(&bar[s], (uint32_t)(k / SC_STAGES) & 1u);
+        if (!__all_sync(FULLM, ok)) {
+            if (lane == 0) {
+                atomicCAS(&cnt[CNT_ERR], 0u, (uint32_t)MER_ERR_TIMEOUT);
+                for (int64_t q = k; q < min(my, k + SC_STAGES); ++q)
+                    mbar_wait(&bar[q % SC_STAGES], (uint32_t)(q / SC_STAGES) & 1u);
+            }
+            __syncwarp();
+            return;
+        }
+        const bool valid = (gw + k * tw) * SC_CHUNK + lane < n;
+        float4 a = make_float4(0, 0, 0, 0), b = a;
+        if (valid) {
+            const float4* r = reinterpret_cast<const float4*>(&WA.ring[s][lane]);
+            a = r[0];
+            b = r[1];
+        }
+        __syncwarp();
+        if (lane == 0 && k + SC_STAGES < my) {
+            // the generic-proxy reads of this slot are ordered before the async-proxy refill
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + SC_STAGES);
+        }
+        const int nrows = stage_record(valid, a, b, sp, grad_over, which, WA, lane);
+        __syncwarp();
+        reduce_rows(WA, lane, nrows);
+        __syncwarp();   // the rows are read before the next chunk overwrites them
     }
 }
 
-int run_scatter(const uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
+// float4 stores over each problem's F or dF (16-byte aligned allocations; scalar tail)
+__global__ void k_zero_grads(const ProblemDev* __restrict__ probs, int n_probs, int which) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int q = 0; q < n_probs; ++q) {
+        float* g = which ? probs[q].dF : probs[q].F;
+        const int64_t n = probs[q].n_par, n4 = n >> 2;
+        float4* g4 = reinterpret_cast<float4*>(g);
+        for (int64_t i = t0; i < n4; i += stride) g4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int64_t i = 4 * n4 + t0; i < n; i += stride) g[i] = 0.0f;
+    }
+}
+
+int run_zero_grads(const ProblemDev* probs, int n_probs, int which, int grid, cudaStream_t st) {
+    MER_TIMED(KC_ZERO, st, k_zero_grads<<<grid, 256, 0, st>>>(probs, n_probs, which));
+    return 1;
+}
+
+int run_scatter(uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
                 float* grad_over, int which, int grid, cudaStream_t st) {
-    // resident blocks only (the loop is persistent): occupancy x multiprocessors, at most `grid`
-    static int resident = 0;
-    if (!resident) {
+    // resident blocks only (the loop is persistent): occupancy x multiprocessors, at most `grid`;
+    // the shared-memory size depends on the number of problems, so the occupancy is kept per count
+    static int resident[MER_MAX_PROBLEMS + 1] = {0};
+    static bool attr = false;
+    const size_t smem = scatter_smem(n_probs);
+    if (!attr) {
+        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem(MER_MAX_PROBLEMS));
+        attr = true;
+    }
+    if (!resident[n_probs]) {
         int occ = 0, dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scatter, 256, 0) != cudaSuccess || occ < 1) occ = 1;
-        resident = occ * sms;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scatter, SC_THREADS, smem) != cudaSuccess || occ < 1)
+            occ = 1;
+        resident[n_probs] = occ * sms;
     }
-    grid = grid < resident ? grid : resident;
-    MER_TIMED(KC_SCATTER, st, k_scatter<<<grid, 256, 0, st>>>(cnt, rec, rcap, probs, n_probs, grad_over, which));
+    grid = grid < resident[n_probs] ? grid : resident[n_probs];
+    MER_TIMED(KC_SCATTER, st,
+              k_scatter<<<grid, SC_THREADS, smem, st>>>(cnt, rec, rcap, probs, n_probs, grad_over, which));
     return 1;
 }
 

@@ -9,7 +9,7 @@ namespace mer {
 enum KernelClass {
     KC_TRACE1_PRIMAL, KC_TRACE1_REPLAY, KC_SHADE1_PRIMAL, KC_SHADE1_REPLAY,
     KC_TRACE2_PRIMAL, KC_TRACE2_REPLAY, KC_SHADE2_PRIMAL, KC_SHADE2_REPLAY,
-    KC_RESOLVE, KC_L2, KC_SCATTER, KC_UPDATE, KC_UPDATE_FIN, KC_COUNT
+    KC_RESOLVE, KC_L2, KC_ZERO, KC_SCATTER, KC_UPDATE, KC_UPDATE_FIN, KC_COUNT
 };
 
 // records CUDA events around launches when installed (diagnostic mode, one thread)
@@ -43,7 +43,9 @@ int run_samples_out(const PassArgs& A, float* out, int grid, cudaStream_t st);
 cudaError_t set_trace_smem_limits(int max_nodes);
 
 // grad_over != nullptr: single-problem output; else each record's problem's F (which = 0) or dF (which = 1)
-int run_scatter(const uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
+// Clears F (which = 0) or dF (which = 1) of every problem in the table.
+int run_zero_grads(const ProblemDev* probs, int n_probs, int which, int grid, cudaStream_t st);
+int run_scatter(uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
                 float* grad_over, int which, int grid, cudaStream_t st);
 // per-problem L2 loss and adjoint images of all problems (pix_pref: prefix of n_pix over problems)
 int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int with_fd,
