@@ -159,3 +159,135 @@ def test_exposition_toy_converges(method):
         else:
             lam, _ = meta.adam_update(lam, F, ad, h, lo=np.array([0.05]), hi=np.array([10.0]))
     assert abs(lam[0] - 0.5) < 0.05, lam
+
+
+# ---- variants (module docstring of oracle.meta) ----
+
+def test_per_element_uniform_steps_equal_global():
+    """With every |pi_i - pi_{i-1}| equal to c, dF/|dpi_e| = sqrt(n) dF/||dpi|| and
+    |dpi_e|^2 = ||dpi||^2 / n, so Var[<dF>] and every result coincide with the global norm."""
+    rng = np.random.default_rng(21)
+    n, c = 12, 0.003
+    h = meta.Hyper(lr=0.01)
+    F0, F1, dF1 = rng.normal(size=n), rng.normal(size=n), rng.normal(size=n) * 0.1
+    pi0 = rng.uniform(0.3, 0.7, n)
+    sg, sp = meta.MetaState.zeros((n,)), meta.MetaState.zeros((n,))
+    # iteration 0 without FD, identical for both; then force a uniform previous step of size c
+    meta.meta_update(pi0, F0, np.zeros(n), sg, h, 0.0)
+    meta.meta_update(pi0, F0, np.zeros(n), sp, h, 0.0, flags=meta.PER_ELEMENT, pi_prev=pi0)
+    sign = np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0)
+    pi1 = pi0 + sign * c
+    a, _, al_a = meta.meta_update(pi1, F1, dF1, sg, h, n * c * c)
+    b, _, al_b = meta.meta_update(pi1, F1, dF1, sp, h, n * c * c, flags=meta.PER_ELEMENT, pi_prev=pi0)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-15) and np.allclose(al_a, al_b, rtol=1e-12)
+    assert np.allclose(sp.m2d, n * sg.m2d, rtol=1e-12)
+
+
+def test_per_element_zero_step_keeps_var_d():
+    """An element whose own previous step was zero keeps Var_D and adds Var[<dF>] = 0."""
+    rng = np.random.default_rng(22)
+    n = 6
+    h = meta.Hyper()
+    st = meta.MetaState.zeros((n,))
+    st.iteration, st.count_f, st.count_d = 3, 3, 2
+    st.m2f[:] = 1.0
+    st.m2d[:] = 0.5
+    st.alpha_prev[:] = 0.4
+    pi_prev = rng.uniform(0.3, 0.7, n)
+    pi = pi_prev.copy()
+    pi[1::2] += 0.01                     # odd elements moved, even elements did not
+    dF = rng.normal(size=n)
+    var0 = st.var.copy()
+    meta.meta_update(pi, rng.normal(size=n), dF, st, h, float(np.sum((pi - pi_prev) ** 2)),
+                     flags=meta.PER_ELEMENT, pi_prev=pi_prev)
+    assert np.all(st.m2d[0::2] == 0.5) and np.all(st.m2d[1::2] != 0.5)
+    # even elements: var went through var += 0, then the varmeta recurrence only
+    a = st.alpha_prev[0::2]
+    m2f = st.m2f[0::2]
+    assert np.allclose(st.var[0::2], a * a * var0[0::2] + (1 - a) ** 2 * m2f, rtol=1e-12)
+
+
+def test_no_clip_iteration_zero_closed_form():
+    """Without Eq. alpha_clip_2 the first alpha is m2f / (m2f + 1e-30) (the carried variance
+    is 0), so <F_0>_M = alpha * 0 + (1 - alpha) F = (1e-30 / (F^2 + 1e-30)) F and the step is
+    its (vanishing) multiple; with the clip alpha_0 = 0 and <F_0>_M = F."""
+    F = np.array([0.5, -2.0, 1e-3])
+    h = meta.Hyper(lr=0.1)
+    st = meta.MetaState.zeros((3,))
+    _, _, al = meta.meta_update(np.full(3, 0.5), F, np.zeros(3), st, h, 0.0, flags=meta.NO_CLIP)
+    assert np.allclose(al, F * F / (F * F + 1e-30), rtol=1e-15)
+    assert np.allclose(st.mean, (1e-30 / (F * F + 1e-30)) * F, rtol=1e-12)
+    st2 = meta.MetaState.zeros((3,))
+    _, _, al2 = meta.meta_update(np.full(3, 0.5), F, np.zeros(3), st2, h, 0.0)
+    assert np.all(al2 == 0.0) and np.allclose(st2.mean, F)
+
+
+def test_centred_two_samples_weighted_variance():
+    """Start-up-corrected EMAs of x1, x2 weight them w1 = beta / (1 + beta), w2 = 1 / (1 + beta);
+    the centred variance m2 - mu^2 is then w1 w2 (x1 - x2)^2."""
+    beta = 0.7
+    h = meta.Hyper(beta_f=beta)
+    x1, x2 = np.array([0.3, -1.0]), np.array([1.1, 2.0])
+    st = meta.MetaState.zeros((2,))
+    pi = np.full(2, 0.5)
+    meta.meta_update(pi, x1, np.zeros(2), st, h, 0.0, flags=meta.CENTRED)
+    meta.meta_update(pi, x2, np.zeros(2), st, h, 0.0, flags=meta.CENTRED)
+    w1, w2 = beta / (1 + beta), 1 / (1 + beta)
+    assert np.allclose(st.mu_f, w1 * x1 + w2 * x2, rtol=1e-12)
+    assert np.allclose(st.m2f - st.mu_f ** 2, w1 * w2 * (x1 - x2) ** 2, rtol=1e-10)
+
+
+def test_growing_beta_weights_become_uniform():
+    """With decays b_k = max(beta, k/(k+1)) the recurrence equals sum_k w_k x_k^2 with
+    w_k = (1 - b_k) prod_{j>k} b_j / (1 - prod_j b_j); once k/(k+1) > beta the weights of the
+    later samples are all 1/(n+1) of the mass, i.e. equal."""
+    beta, n = 0.75, 12
+    h = meta.Hyper(beta_f=beta)
+    rng = np.random.default_rng(5)
+    xs = rng.normal(size=(n, 1))
+    st = meta.MetaState.zeros((1,))
+    for k in range(n):
+        meta.meta_update(np.full(1, 0.5), xs[k], np.zeros(1), st, h, 0.0, flags=meta.GROWING_BETA)
+    b = np.array([max(beta, k / (k + 1.0)) for k in range(n)])
+    w = np.array([(1 - b[k]) * np.prod(b[k + 1:]) for k in range(n)]) / (1 - np.prod(b))
+    assert np.isclose(w.sum(), 1.0)
+    assert np.allclose(st.m2f, np.sum(w[:, None] * xs ** 2, axis=0), rtol=1e-12)
+    K = int(np.argmax(np.arange(n) / (np.arange(n) + 1.0) > beta))
+    assert K > 0 and np.allclose(w[K - 1:], w[-1], rtol=1e-12)
+
+
+def test_naive_adam_reduces_to_adam_on_meta_estimate():
+    """At iteration 0 <F_0>_M = F (alpha_0 = 0), so the naive coupling's first step is Adam's
+    first step on F; afterwards it is Adam run on the sequence of <F_i>_M."""
+    rng = np.random.default_rng(9)
+    n = 5
+    h = meta.Hyper(lr=0.05)
+    pi = rng.uniform(0.3, 0.7, n)
+    st = meta.MetaState.zeros((n,))
+    ad = meta.AdamState.zeros((n,))
+    F0 = rng.normal(size=n)
+    a, n2, _ = meta.meta_update(pi, F0, np.zeros(n), st, h, 0.0, flags=meta.NAIVE_ADAM)
+    b, _ = meta.adam_update(pi, F0, ad, h)
+    assert np.allclose(a, b, rtol=1e-13)
+    F1, dF1 = rng.normal(size=n), rng.normal(size=n) * 0.1
+    a2, _, _ = meta.meta_update(a, F1, dF1, st, h, n2, flags=meta.NAIVE_ADAM)
+    b2, _ = meta.adam_update(b, st.mean, ad, h)
+    assert np.allclose(a2, b2, rtol=1e-13)
+
+
+def test_uncorrelated_variance_samples():
+    """The variances follow F_var, dF_var only: with F_var = F and dF_var = dF the variant is the
+    default; with other F_var, m2f is that of a default run on F_var while <F>_M still uses F."""
+    rng = np.random.default_rng(13)
+    n = 7
+    h = meta.Hyper()
+    pi = rng.uniform(0.3, 0.7, n)
+    F, Fv = rng.normal(size=n), rng.normal(size=n)
+    s0, s1, s2 = (meta.MetaState.zeros((n,)) for _ in range(3))
+    a, _, _ = meta.meta_update(pi, F, np.zeros(n), s0, h, 0.0)
+    b, _, _ = meta.meta_update(pi, F, np.zeros(n), s1, h, 0.0, flags=meta.UNCORRELATED, F_var=F, dF_var=np.zeros(n))
+    assert np.array_equal(a, b)
+    meta.meta_update(pi, F, np.zeros(n), s2, h, 0.0, flags=meta.UNCORRELATED, F_var=Fv, dF_var=np.zeros(n))
+    s3 = meta.MetaState.zeros((n,))
+    meta.meta_update(pi, Fv, np.zeros(n), s3, h, 0.0)
+    assert np.allclose(s2.m2f, s3.m2f) and np.allclose(s2.mean, F)
