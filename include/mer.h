@@ -56,6 +56,9 @@ typedef int mer_status;
 #define MER_STREAM_FD_ADJ 3u      /* adjoint pair of the FD sample */
 #define MER_STREAM_TARGET 4u      /* target rendering */
 #define MER_STREAM_EVAL 5u        /* loss evaluation renders */
+/* MER_META_UNCORRELATED draws its independent variance samples from the four gradient streams
+ * shifted by this offset (streams 8..11) */
+#define MER_STREAM_VAR_OFFSET 8u
 
 #define MER_MAX_CHANNELS 5
 #define MER_MAX_DEPTH 16
@@ -64,6 +67,26 @@ typedef int mer_status;
 /* Hyper-parameters of one problem's optimiser. Defaults (mer_hyper_default):
  * lr 0.01, beta_f 0.99, beta_d 0.9 (Sec. 4.1 "large beta_F", Sec. 4.2 "small beta_D"),
  * eps 1e-8 and eps_alpha 1e-30 (appendix pseudocode), beta1 0.9 / beta2 0.999 (Adam). */
+/* Variants of the META update (bits of mer_hyper.flags; 0 = the method as stated):
+ *  PER_ELEMENT   the step size of Sec. 4.2 read per element, |pi_i - pi_{i-1}| (the appendix
+ *                loop writes sqrt(dpi_i^2)), instead of the Euclidean norm of the problem's
+ *                step; an element whose own step was zero keeps Var_D and adds Var[<dF>] = 0
+ *  NO_CLIP       Eq. alpha_clip_2 not applied (ablation "alpha clipping", Sec. 6)
+ *  CENTRED       non-zero-centred variances max(m2 - mu^2, 0), mu a start-up-corrected EMA of
+ *                the sample beside each Moment2 (ablation "zero-centred EMAs", Sec. 6)
+ *  GROWING_BETA  beta_F of the k-th Var[<F>] step grown as max(beta_F, k/(k+1)), start-up
+ *                correction (1 - beta_k) / (1 - prod_{j<=k} beta_j) (appendix A)
+ *  NAIVE_ADAM    <F_i>_M fed to Adam's moments (beta1, beta2, bias-corrected) instead of the
+ *                update rule of Sec. 5 (the naive coupling Sec. 5 argues against)
+ *  UNCORRELATED  Var[<F>] and Var[<dF>]_D stepped with independent samples F_var, dF_var of
+ *                the same estimators (ablation "sample reuse", Sec. 6); <F_i>_M still uses F, dF */
+#define MER_META_PER_ELEMENT 1
+#define MER_META_NO_CLIP 2
+#define MER_META_CENTRED 4
+#define MER_META_GROWING_BETA 8
+#define MER_META_NAIVE_ADAM 16
+#define MER_META_UNCORRELATED 32
+
 typedef struct mer_hyper {
     int32_t mode;      /* MER_MODE_META or MER_MODE_ADAM */
     float lr;          /* eta */
@@ -73,6 +96,7 @@ typedef struct mer_hyper {
     float eps_alpha;   /* added to the alpha denominator (appendix pseudocode) */
     float beta1;       /* Adam first moment */
     float beta2;       /* Adam second moment */
+    int32_t flags;     /* MER_META_* variant bits (META mode only; 0 = as stated) */
 } mer_hyper;
 
 /* Scene of one problem. All arrays are HOST arrays, copied by mer_scene_add (the caller
@@ -194,6 +218,9 @@ mer_status mer_stats(mer_ctx* ctx, int32_t pid, mer_iter_stats* out);
  * inspection and tests: pi_cur, pi_prev, F, dF, m2f, m2d, mean, var, alpha_prev. */
 typedef struct mer_state_view {
     float *pi_cur, *pi_prev, *F, *dF, *m2f, *m2d, *mean, *var, *alpha_prev;
+    /* variant state, NULL unless the problem's flags need it: CENTRED first moments, NAIVE_ADAM
+     * moments, UNCORRELATED variance samples */
+    float *mu_f, *mu_d, *adam_m, *adam_v, *F_var, *dF_var;
     int64_t n;                /* parameters of the problem (H*W*C) */
 } mer_state_view;
 mer_status mer_state_get(mer_ctx* ctx, int32_t pid, mer_state_view* out);
@@ -206,12 +233,35 @@ mer_status mer_state_get(mer_ctx* ctx, int32_t pid, mer_state_view* out);
  * and the update dpi = -lr*mean/(sqrt(var)+eps), clamped channel-wise (channel = index % C) to
  * [lo[c], hi[c]]. ADAM mode uses mean/var as Adam's m/v and iteration+1 as its step count.
  * zero_grads = 1 clears F and dF. *dpi_norm2_out (device double) receives ||pi_next - pi||^2.
+ * Variant flags without arrays of their own work here (PER_ELEMENT, with pi_next holding pi_{i-1}
+ * on entry; NO_CLIP; GROWING_BETA); CENTRED, NAIVE_ADAM and UNCORRELATED are rejected
+ * (MER_ERR_INVALID_ARG): use mer_meta_step_raw_ex.
  * Uses library-owned per-device scratch for the deterministic norm reduction. */
 mer_status mer_meta_step_raw(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
                              const float* pi, float* pi_next, float* F, float* dF, float* m2f, float* m2d,
                              float* mean, float* var, float* alpha_prev, int32_t iteration, int32_t count_f,
                              int32_t count_d, double dpi_norm2, int32_t zero_grads, double* dpi_norm2_out,
                              void* cuda_stream);
+
+/* Device arrays of the standalone update (n floats each, 16-byte aligned). pi_next may not alias
+ * pi; with MER_META_PER_ELEMENT it holds pi_{i-1} on entry (as the context's second parameter
+ * slot does). The variant arrays are read only when their flag is set and may be NULL otherwise:
+ * mu_f, mu_d (CENTRED, start at 0), adam_m, adam_v (NAIVE_ADAM, start at 0), F_var, dF_var
+ * (UNCORRELATED, this iteration's independent samples). */
+typedef struct mer_update_arrays {
+    const float* pi;
+    float *pi_next, *F, *dF, *m2f, *m2d, *mean, *var, *alpha_prev;
+    float *mu_f, *mu_d, *adam_m, *adam_v;
+    const float *F_var, *dF_var;
+} mer_update_arrays;
+
+/* mer_meta_step_raw with every variant of hyper->flags: arrays as described above, scalars as
+ * in mer_meta_step_raw (ADAM mode ignores the flags). Rejects (MER_ERR_INVALID_ARG) a flag whose
+ * arrays are missing. */
+mer_status mer_meta_step_raw_ex(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
+                                const mer_update_arrays* arrays, int32_t iteration, int32_t count_f,
+                                int32_t count_d, double dpi_norm2, int32_t zero_grads, double* dpi_norm2_out,
+                                void* cuda_stream);
 
 /* The same update as mer_meta_step_raw, for callers that must not allocate device memory:
  * code running while a stream is being captured into a CUDA graph, applications that reserve

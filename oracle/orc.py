@@ -216,22 +216,25 @@ def bsdf_sample(mtype, th, n, wo, ul, u1, u2):
 # one iteration's gradient estimates (Sec. 3, Eq. est_def and est_triv)
 # ---------------------------------------------------------------------------
 
-def prop_gradient(sc: Scene, tex, target, spp, iteration):
+def prop_gradient(sc: Scene, tex, target, spp, iteration, stream_offset=0):
     """<F_i>: L2-loss gradient with an independent primal image (stream PROP_PRIMAL) for the
-    adjoint weights and the PRB adjoint on stream PROP_ADJ. Returns (grad, loss, image)."""
-    img = render_image(sc, tex, spp, iteration, ST_PROP_PRIMAL)
+    adjoint weights and the PRB adjoint on stream PROP_ADJ. Returns (grad, loss, image).
+    stream_offset shifts both streams (the independent variance samples of the uncorrelated
+    variant use offset 8)."""
+    img = render_image(sc, tex, spp, iteration, ST_PROP_PRIMAL + stream_offset)
     loss, dimg = l2_loss(img, target)
-    g = adjoint_image(sc, tex, spp, iteration, ST_PROP_ADJ, dimg)
+    g = adjoint_image(sc, tex, spp, iteration, ST_PROP_ADJ + stream_offset, dimg)
     return g, loss, img
 
 
-def fd_gradient(sc: Scene, tex_cur, tex_prev, target, spp, iteration):
+def fd_gradient(sc: Scene, tex_cur, tex_prev, target, spp, iteration, stream_offset=0):
     """<dF_i> = <F_i>(u) - <F_{i-1}>(u): both terms use the same counters (streams FD_PRIMAL
-    for the adjoint weights and FD_ADJ for the adjoint) at pi_i and pi_{i-1}."""
-    img_c = render_image(sc, tex_cur, spp, iteration, ST_FD_PRIMAL)
-    img_p = render_image(sc, tex_prev, spp, iteration, ST_FD_PRIMAL)
+    for the adjoint weights and FD_ADJ for the adjoint) at pi_i and pi_{i-1}; stream_offset
+    shifts both streams as in prop_gradient."""
+    img_c = render_image(sc, tex_cur, spp, iteration, ST_FD_PRIMAL + stream_offset)
+    img_p = render_image(sc, tex_prev, spp, iteration, ST_FD_PRIMAL + stream_offset)
     _, d_c = l2_loss(img_c, target)
     _, d_p = l2_loss(img_p, target)
-    g_c = adjoint_image(sc, tex_cur, spp, iteration, ST_FD_ADJ, d_c)
-    g_p = adjoint_image(sc, tex_prev, spp, iteration, ST_FD_ADJ, d_p)
+    g_c = adjoint_image(sc, tex_cur, spp, iteration, ST_FD_ADJ + stream_offset, d_c)
+    g_p = adjoint_image(sc, tex_prev, spp, iteration, ST_FD_ADJ + stream_offset, d_p)
     return g_c - g_p

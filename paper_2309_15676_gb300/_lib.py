@@ -26,7 +26,7 @@ _vp = ct.c_void_p
 
 class Hyper(ct.Structure):
     _fields_ = [("mode", ct.c_int32), ("lr", _f), ("beta_f", _f), ("beta_d", _f), ("eps", _f),
-                ("eps_alpha", _f), ("beta1", _f), ("beta2", _f)]
+                ("eps_alpha", _f), ("beta1", _f), ("beta2", _f), ("flags", ct.c_int32)]
 
 
 class SceneDesc(ct.Structure):
@@ -58,8 +58,14 @@ class IterStats(ct.Structure):
 
 
 class StateView(ct.Structure):
-    _fields_ = [(n, _fp) for n in ("pi_cur", "pi_prev", "F", "dF", "m2f", "m2d", "mean", "var", "alpha_prev")] + \
+    _fields_ = [(n, _fp) for n in ("pi_cur", "pi_prev", "F", "dF", "m2f", "m2d", "mean", "var", "alpha_prev",
+                                   "mu_f", "mu_d", "adam_m", "adam_v", "F_var", "dF_var")] + \
                [("n", ct.c_int64)]
+
+
+class UpdateArrays(ct.Structure):
+    _fields_ = [(n, _vp) for n in ("pi", "pi_next", "F", "dF", "m2f", "m2d", "mean", "var", "alpha_prev",
+                                   "mu_f", "mu_d", "adam_m", "adam_v", "F_var", "dF_var")]
 
 
 class KernelTime(ct.Structure):
@@ -92,6 +98,8 @@ SIGNATURES = {
     "mer_meta_step_raw": (ct.c_int, [ct.POINTER(Hyper), ct.c_int64, ct.c_int32, _fp, _fp, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp, _vp, _vp, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_double,
                                      ct.c_int32, _vp, _vp]),
+    "mer_meta_step_raw_ex": (ct.c_int, [ct.POINTER(Hyper), ct.c_int64, ct.c_int32, _fp, _fp, ct.POINTER(UpdateArrays),
+                                        ct.c_int32, ct.c_int32, ct.c_int32, ct.c_double, ct.c_int32, _vp, _vp]),
     "mer_meta_step_raw_noalloc": (ct.c_int, [ct.POINTER(Hyper), ct.c_int64, ct.c_int32, _fp, _fp, _vp, _vp, _vp,
                                              _vp, _vp, _vp, _vp, _vp, _vp, ct.c_int32, ct.c_int32, ct.c_int32,
                                              ct.c_double, ct.c_int32, _vp, _vp]),

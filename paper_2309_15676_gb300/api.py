@@ -33,10 +33,20 @@ class HyperParams:
     eps_alpha: float = 1e-30
     beta1: float = 0.9
     beta2: float = 0.999
+    flags: int = 0            # MER_META_* variant bits (META_* constants below)
 
     def to_c(self) -> _lib.Hyper:
         return _lib.Hyper(self.mode, self.lr, self.beta_f, self.beta_d, self.eps, self.eps_alpha, self.beta1,
-                          self.beta2)
+                          self.beta2, self.flags)
+
+
+# variant bits of HyperParams.flags (the header's MER_META_* values)
+META_PER_ELEMENT = 1
+META_NO_CLIP = 2
+META_CENTRED = 4
+META_GROWING_BETA = 8
+META_NAIVE_ADAM = 16
+META_UNCORRELATED = 32
 
 
 def _ptr(t):
@@ -237,9 +247,12 @@ class Context:
         v = _lib.StateView()
         self._ck(self.L.mer_state_get(self.h, pid, ct.byref(v)))
         out = {}
-        for name in ("pi_cur", "pi_prev", "F", "dF", "m2f", "m2d", "mean", "var", "alpha_prev"):
-            t = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
+        for name in ("pi_cur", "pi_prev", "F", "dF", "m2f", "m2d", "mean", "var", "alpha_prev",
+                     "mu_f", "mu_d", "adam_m", "adam_v", "F_var", "dF_var"):
             addr = ct.cast(getattr(v, name), ct.c_void_p).value
+            if not addr:
+                continue            # variant state the problem's flags do not allocate
+            t = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
             _memcpy_d2d(t, addr, v.n * 4)
             out[name] = t
         return out
@@ -298,6 +311,24 @@ def meta_step_raw(hyper: HyperParams, pi, pi_next, F, dF, m2f, m2d, mean, var, a
     check(L.mer_meta_step_raw(ct.byref(h), pi.numel(), C, lo_a, hi_a, _ptr(pi), _ptr(pi_next), _ptr(F), _ptr(dF),
                               _ptr(m2f), _ptr(m2d), _ptr(mean), _ptr(var), _ptr(alpha_prev), iteration, count_f,
                               count_d, float(dpi_norm2), int(zero_grads), _ptr(out), _cur_stream(dev)))
+    return out
+
+
+def meta_step_raw_ex(hyper: HyperParams, arrays: dict, C, lo, hi, iteration, count_f, count_d, dpi_norm2,
+                     zero_grads=True, out=None):
+    """mer_meta_step_raw_ex on torch device tensors (dict keys as in mer_update_arrays; absent keys
+    are NULL); returns the device tensor holding ||dpi||^2."""
+    L = _lib.load()
+    dev = arrays["pi"].device
+    out = out if out is not None else torch.zeros(1, device=dev, dtype=torch.float64)
+    lo_a = (ct.c_float * 8)(*([float(x) for x in lo] + [0.0] * (8 - len(lo))))
+    hi_a = (ct.c_float * 8)(*([float(x) for x in hi] + [0.0] * (8 - len(hi))))
+    A = _lib.UpdateArrays()
+    for name, _ in _lib.UpdateArrays._fields_:
+        setattr(A, name, _ptr(arrays.get(name)))
+    h = hyper.to_c()
+    check(L.mer_meta_step_raw_ex(ct.byref(h), arrays["pi"].numel(), C, lo_a, hi_a, ct.byref(A), iteration, count_f,
+                                 count_d, float(dpi_norm2), int(zero_grads), _ptr(out), _cur_stream(dev)))
     return out
 
 

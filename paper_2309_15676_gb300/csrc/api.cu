@@ -29,6 +29,8 @@ struct Problem {
     std::vector<void*> allocs;
     float *pslot[2] = {nullptr, nullptr}, *F = nullptr, *dF = nullptr, *m2f = nullptr, *m2d = nullptr;
     float *mean = nullptr, *var = nullptr, *ap = nullptr;
+    // variant state (MER_META_* flags), NULL unless needed
+    float *mu_f = nullptr, *mu_d = nullptr, *am = nullptr, *av = nullptr, *Fv = nullptr, *dFv = nullptr;
     float *target = nullptr, *img = nullptr, *dimg = nullptr, *imgA = nullptr, *imgB = nullptr;
     float *dimgA = nullptr, *dimgB = nullptr;
 };
@@ -60,6 +62,7 @@ struct mer_ctx {
     ProblemDev* d_probs = nullptr;
     ProbState* d_pstate = nullptr;
     double* d_loss = nullptr;
+    bool any_uncorrelated = false;   // some problem uses MER_META_UNCORRELATED
     // pass tables
     int32_t *d_prop_prob = nullptr, *d_fd_prob = nullptr;
     int64_t *d_prop_off = nullptr, *d_fd_off = nullptr, *d_pix_pref = nullptr;
@@ -344,14 +347,13 @@ int enqueue_gradient(mer_ctx* c) {
     const int G = grid_for(c, 256);
     const bool have_fd = c->n_fd > 0 && c->P_fd > 0;
     const bool split = !g_timer;
+    const int NP = (int)c->probs.size();
     cudaStream_t s[4] = {c->st, split ? c->sx[0] : c->st, split ? c->sx[1] : c->st, split ? c->sx[2] : c->st};
-    cudaMemsetAsync(c->d_loss, 0, sizeof(double) * c->probs.size(), s[0]);
-    n++;
     auto prop_args = [&](int wi) {
         PassArgs A = base_args(c, c->w[wi]);
         A.entry_prob = c->d_prop_prob;
         A.path_off = c->d_prop_off;
-        A.n_entries = (int)c->probs.size();
+        A.n_entries = NP;
         A.n_paths = c->P_prop;
         return A;
     };
@@ -376,53 +378,63 @@ int enqueue_gradient(mer_ctx* c) {
             cudaStreamWaitEvent(s[0], c->ev_join[b - 1], 0);
         }
     };
-    // ---- stage 1 ----
-    fork(4);
-    PassArgs P = prop_args(0);
-    P.stream = MER_STREAM_PROP_PRIMAL;
-    n += pass(c, s[0], P, 1, MODE_PRIMAL, c->maxD_prop);
-    n += run_resolve(P, 1, nullptr, nullptr, 0, G, s[0]);
-    PassArgs PR = prop_args(2);
-    PR.stream = MER_STREAM_PROP_ADJ;
-    PR.lacc = c->w[2].ltot;                  // per-path radiance L_total of the replayed paths
-    n += pass(c, s[2], PR, 1, MODE_ADJ_FWD, c->maxD_prop);
-    if (have_fd) {
-        PassArgs D = fd_args(1);
-        D.stream = MER_STREAM_FD_PRIMAL;
-        n += pass(c, s[1], D, 2, MODE_PRIMAL, c->maxD_fd);
-        n += run_resolve(D, 2, nullptr, nullptr, 0, G, s[1]);
-        PassArgs DR = fd_args(3);
-        DR.stream = MER_STREAM_FD_ADJ;
-        DR.lacc = c->w[3].ltot;
-        n += pass(c, s[3], DR, 2, MODE_ADJ_FWD, c->maxD_fd);
-    }
-    join(4);
-    // ---- stage 2: loss and adjoint images of every problem ----
-    n += run_l2(c->d_probs, c->d_pix_pref, (int)c->probs.size(), c->total_pix, have_fd, c->d_loss, G, s[0]);
-    // ---- stage 3 ----
-    fork(2);
-    // proportional gradient <F_i>: replay from the same counters, scatter into F
-    P = prop_args(0);
-    P.stream = MER_STREAM_PROP_ADJ;
-    P.ltot = c->w[2].ltot;
-    n += pass(c, s[0], P, 1, MODE_REPLAY, c->maxD_prop);
-    // F is cleared right before its scatter, so that the reductions find its lines in L2
-    n += run_zero_grads(c->d_probs, (int)c->probs.size(), 0, G, s[0]);
-    if (g_timer)
-        for (Problem* p : c->probs) g_timer->add_units(KC_ZERO, p->n_par);
-    n += run_scatter(c->w[0].cnt, c->w[0].rec, c->w[0].rcap, c->d_probs, (int)c->probs.size(), nullptr, 0, G, s[0]);
-    // finite-difference gradient <dF_i> (Eq. est_triv): the same for the pair, scatter into dF
-    if (have_fd) {
-        PassArgs D = fd_args(1);
-        D.stream = MER_STREAM_FD_ADJ;
-        D.ltot = c->w[3].ltot;
-        n += pass(c, s[1], D, 2, MODE_REPLAY, c->maxD_fd);
-        n += run_zero_grads(c->d_probs, (int)c->probs.size(), 1, G, s[1]);
+    auto zero = [&](int which, cudaStream_t st) {
+        n += run_zero_grads(c->d_probs, NP, which, G, st);
         if (g_timer)
             for (Problem* p : c->probs) g_timer->add_units(KC_ZERO, p->n_par);
-        n += run_scatter(c->w[1].cnt, c->w[1].rec, c->w[1].rcap, c->d_probs, (int)c->probs.size(), nullptr, 1, G, s[1]);
-    }
-    join(2);
+    };
+    // One gradient evaluation: proportional samples into gradient texture wF and FD samples into
+    // wD, drawn from the four gradient streams shifted by soff, loss accumulated into `loss`.
+    auto evaluate = [&](uint32_t soff, int wF, int wD, double* loss) {
+        cudaMemsetAsync(loss, 0, sizeof(double) * NP, s[0]);
+        n++;
+        // ---- stage 1 ----
+        fork(4);
+        PassArgs P = prop_args(0);
+        P.stream = MER_STREAM_PROP_PRIMAL + soff;
+        n += pass(c, s[0], P, 1, MODE_PRIMAL, c->maxD_prop);
+        n += run_resolve(P, 1, nullptr, nullptr, 0, G, s[0]);
+        PassArgs PR = prop_args(2);
+        PR.stream = MER_STREAM_PROP_ADJ + soff;
+        PR.lacc = c->w[2].ltot;                  // per-path radiance L_total of the replayed paths
+        n += pass(c, s[2], PR, 1, MODE_ADJ_FWD, c->maxD_prop);
+        if (have_fd) {
+            PassArgs D = fd_args(1);
+            D.stream = MER_STREAM_FD_PRIMAL + soff;
+            n += pass(c, s[1], D, 2, MODE_PRIMAL, c->maxD_fd);
+            n += run_resolve(D, 2, nullptr, nullptr, 0, G, s[1]);
+            PassArgs DR = fd_args(3);
+            DR.stream = MER_STREAM_FD_ADJ + soff;
+            DR.lacc = c->w[3].ltot;
+            n += pass(c, s[3], DR, 2, MODE_ADJ_FWD, c->maxD_fd);
+        }
+        join(4);
+        // ---- stage 2: loss and adjoint images of every problem ----
+        n += run_l2(c->d_probs, c->d_pix_pref, NP, c->total_pix, have_fd, loss, G, s[0]);
+        // ---- stage 3 ----
+        fork(2);
+        // proportional gradient <F_i>: replay from the same counters, scatter into F (the
+        // texture is cleared right before its scatter, so that the reductions find it in L2)
+        P = prop_args(0);
+        P.stream = MER_STREAM_PROP_ADJ + soff;
+        P.ltot = c->w[2].ltot;
+        n += pass(c, s[0], P, 1, MODE_REPLAY, c->maxD_prop);
+        zero(wF, s[0]);
+        n += run_scatter(c->w[0].cnt, c->w[0].rec, c->w[0].rcap, c->d_probs, NP, nullptr, wF, G, s[0]);
+        // finite-difference gradient <dF_i> (Eq. est_triv): the same for the pair, scatter into dF
+        if (have_fd) {
+            PassArgs D = fd_args(1);
+            D.stream = MER_STREAM_FD_ADJ + soff;
+            D.ltot = c->w[3].ltot;
+            n += pass(c, s[1], D, 2, MODE_REPLAY, c->maxD_fd);
+            zero(wD, s[1]);
+            n += run_scatter(c->w[1].cnt, c->w[1].rec, c->w[1].rcap, c->d_probs, NP, nullptr, wD, G, s[1]);
+        }
+        join(2);
+    };
+    evaluate(0u, 0, 1, c->d_loss);
+    // MER_META_UNCORRELATED: a second, independent evaluation (own streams) for the variances
+    if (c->any_uncorrelated) evaluate(MER_STREAM_VAR_OFFSET, 2, 3, c->d_loss + MER_MAX_PROBLEMS);
     return n;
 }
 
@@ -456,8 +468,10 @@ mer_status rebuild_tables(mer_ctx* c) {
     std::vector<UpdSeg> segs(n);
     std::vector<int64_t> blk_off(n + 1, 0);
     c->maxD_prop = c->maxD_fd = 0;
+    c->any_uncorrelated = false;
     for (int i = 0; i < n; ++i) {
         Problem* p = c->probs[i];
+        if (p->meta && (p->hyper.flags & MER_META_UNCORRELATED)) c->any_uncorrelated = true;
         pd[i] = p->dev;
         prop_prob[i] = i;
         prop_off[i + 1] = prop_off[i] + (int64_t)p->n_pix * p->spp_prop;
@@ -516,6 +530,8 @@ mer_status reset_state(mer_ctx* c, Problem* p) {
     CK(c, cudaMemsetAsync(p->mean, 0, nb, c->st));
     CK(c, cudaMemsetAsync(p->var, 0, nb, c->st));
     run_fill(p->ap, p->n_par, -INFINITY, c->st);
+    for (float* a : {p->mu_f, p->mu_d, p->am, p->av, p->Fv, p->dFv})
+        if (a) CK(c, cudaMemsetAsync(a, 0, nb, c->st));
     ProbState ps{};
     CK(c, cudaMemcpyAsync(c->d_pstate + p->id, &ps, sizeof ps, cudaMemcpyHostToDevice, c->st));
     CK(c, cudaStreamSynchronize(c->st));
@@ -581,6 +597,7 @@ mer_status mer_hyper_default(mer_hyper* h) {
     h->eps_alpha = 1e-30f;
     h->beta1 = 0.9f;
     h->beta2 = 0.999f;
+    h->flags = 0;
     return MER_OK;
 }
 
@@ -607,13 +624,13 @@ mer_status mer_create(const mer_config* cfg, void* cuda_stream, mer_ctx** out) {
     if (!e) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
     if (!e) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
     if (!e) e = cudaMalloc(&c->d_pstate, sizeof(ProbState) * MER_MAX_PROBLEMS);
-    if (!e) e = cudaMalloc(&c->d_loss, sizeof(double) * MER_MAX_PROBLEMS);
+    if (!e) e = cudaMalloc(&c->d_loss, sizeof(double) * 2 * MER_MAX_PROBLEMS);   // loss, variance-sample loss
     for (int i = 0; i < 3 && !e; ++i) {
         e = cudaStreamCreateWithFlags(&c->sx[i], cudaStreamNonBlocking);
         if (!e) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
     }
     if (!e) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (!e) e = cudaMemset(c->d_loss, 0, sizeof(double) * MER_MAX_PROBLEMS);
+    if (!e) e = cudaMemset(c->d_loss, 0, sizeof(double) * 2 * MER_MAX_PROBLEMS);
     if (!e && c->shape.smem_nodes > 0) e = set_trace_smem_limits(c->shape.smem_nodes);
     if (e) {
         fail(nullptr, MER_ERR_CUDA, "context setup failed: %s", cudaGetErrorString(e));
@@ -685,7 +702,15 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     Problem* p = new Problem();
     p->id = (int32_t)c->probs.size();
     p->hyper = d->hyper;
-    if (p->hyper.lr == 0.0f && p->hyper.beta_f == 0.0f) mer_hyper_default(&p->hyper);
+    if (p->hyper.lr == 0.0f && p->hyper.beta_f == 0.0f) {   // all-zero hyper: defaults (flags kept)
+        const int32_t fl = p->hyper.flags;
+        mer_hyper_default(&p->hyper);
+        p->hyper.flags = fl;
+    }
+    if (p->hyper.flags & ~63) {
+        delete p;
+        return fail(c, MER_ERR_INVALID_ARG, "unknown MER_META_* flag bits");
+    }
     p->meta = p->hyper.mode == MER_MODE_META;
     p->max_depth = d->max_depth;
     p->spp_prop = d->spp_prop;
@@ -887,6 +912,19 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     AK(alloc(&p->mean, np));
     AK(alloc(&p->var, np));
     AK(alloc(&p->ap, np));
+    const int vfl = p->meta ? p->hyper.flags : 0;
+    if (vfl & MER_META_CENTRED) {
+        AK(alloc(&p->mu_f, np));
+        AK(alloc(&p->mu_d, np));
+    }
+    if (vfl & MER_META_NAIVE_ADAM) {
+        AK(alloc(&p->am, np));
+        AK(alloc(&p->av, np));
+    }
+    if (vfl & MER_META_UNCORRELATED) {
+        AK(alloc(&p->Fv, np));
+        AK(alloc(&p->dFv, np));
+    }
     AK(alloc(&p->target, npx));
     AK(alloc(&p->img, npx));
     AK(alloc(&p->dimg, npx));
@@ -903,6 +941,8 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     D.pslot[1] = p->pslot[1];
     D.F = p->F;
     D.dF = p->dF;
+    D.Fv = p->Fv;
+    D.dFv = p->dFv;
     D.target = p->target;
     D.img = p->img;
     D.dimg = p->dimg;
@@ -921,6 +961,12 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     S.mean = p->mean;
     S.var = p->var;
     S.ap = p->ap;
+    S.mu_f = p->mu_f;
+    S.mu_d = p->mu_d;
+    S.am = p->am;
+    S.av = p->av;
+    S.Fv = p->Fv;
+    S.dFv = p->dFv;
     S.n = p->n_par;
     S.C = p->C;
     S.prob = p->id;
@@ -1175,6 +1221,12 @@ mer_status mer_state_get(mer_ctx* c, int32_t pid, mer_state_view* out) {
     out->mean = p->mean;
     out->var = p->var;
     out->alpha_prev = p->ap;
+    out->mu_f = p->mu_f;
+    out->mu_d = p->mu_d;
+    out->adam_m = p->am;
+    out->adam_v = p->av;
+    out->F_var = p->Fv;
+    out->dF_var = p->dFv;
     out->n = p->n_par;
     return MER_OK;
 }
@@ -1242,20 +1294,42 @@ mer_status mer_meta_step_raw(const mer_hyper* hyper, int64_t n, int32_t C, const
                              const float* pi, float* pi_next, float* F, float* dF, float* m2f, float* m2d, float* mean,
                              float* var, float* alpha_prev, int32_t iteration, int32_t count_f, int32_t count_d,
                              double dpi_norm2, int32_t zero_grads, double* out, void* stream) {
-    if (!hyper || n < 0 || C < 1 || C > 8 || !lo || !hi || !out)
+    mer_update_arrays A;
+    memset(&A, 0, sizeof A);
+    A.pi = pi; A.pi_next = pi_next; A.F = F; A.dF = dF; A.m2f = m2f; A.m2d = m2d; A.mean = mean; A.var = var;
+    A.alpha_prev = alpha_prev;
+    return mer_meta_step_raw_ex(hyper, n, C, lo, hi, &A, iteration, count_f, count_d, dpi_norm2, zero_grads, out,
+                                stream);
+}
+
+mer_status mer_meta_step_raw_ex(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
+                                const mer_update_arrays* arrays, int32_t iteration, int32_t count_f,
+                                int32_t count_d, double dpi_norm2, int32_t zero_grads, double* out, void* stream) {
+    if (!hyper || !arrays || n < 0 || C < 1 || C > 8 || !lo || !hi || !out)
         return fail(nullptr, MER_ERR_INVALID_ARG, "bad arguments to mer_meta_step_raw");
+    const mer_update_arrays& A = *arrays;
     const bool meta = hyper->mode == MER_MODE_META;
-    if (n > 0 && (!pi || !pi_next || !F || !m2f || !mean || (meta && (!dF || !m2d || !var || !alpha_prev))))
+    const int fl = meta ? hyper->flags : 0;
+    if (n > 0 && (!A.pi || !A.pi_next || !A.F || !A.m2f || !A.mean ||
+                  (meta && (!A.dF || !A.m2d || !A.var || !A.alpha_prev))))
         return fail(nullptr, MER_ERR_INVALID_ARG, "missing arrays in mer_meta_step_raw");
-    const void* ptrs[] = {pi, pi_next, F, dF, m2f, m2d, mean, var, alpha_prev};
+    if (n > 0 && (((fl & MER_META_CENTRED) && (!A.mu_f || !A.mu_d)) ||
+                  ((fl & MER_META_NAIVE_ADAM) && (!A.adam_m || !A.adam_v)) ||
+                  ((fl & MER_META_UNCORRELATED) && (!A.F_var || !A.dF_var))))
+        return fail(nullptr, MER_ERR_INVALID_ARG, "mer_meta_step_raw: the flags need variant arrays that are missing");
+    const void* ptrs[] = {A.pi, A.pi_next, A.F, A.dF, A.m2f, A.m2d, A.mean, A.var, A.alpha_prev,
+                          A.mu_f, A.mu_d, A.adam_m, A.adam_v, A.F_var, A.dF_var};
     for (const void* q : ptrs)
         if (q && ((uintptr_t)q & 15u)) return fail(nullptr, MER_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
-    if (pi == pi_next && n > 0) return fail(nullptr, MER_ERR_INVALID_ARG, "pi_next may not alias pi");
+    if (A.pi == A.pi_next && n > 0) return fail(nullptr, MER_ERR_INVALID_ARG, "pi_next may not alias pi");
     UpdSeg S;
     memset(&S, 0, sizeof S);
-    S.pA = const_cast<float*>(pi);
-    S.pB = pi_next;
-    S.F = F; S.dF = dF; S.m2f = m2f; S.m2d = m2d; S.mean = mean; S.var = var; S.ap = alpha_prev;
+    S.pA = const_cast<float*>(A.pi);
+    S.pB = A.pi_next;
+    S.F = A.F; S.dF = A.dF; S.m2f = A.m2f; S.m2d = A.m2d; S.mean = A.mean; S.var = A.var; S.ap = A.alpha_prev;
+    if (fl & MER_META_CENTRED) { S.mu_f = A.mu_f; S.mu_d = A.mu_d; }
+    if (fl & MER_META_NAIVE_ADAM) { S.am = A.adam_m; S.av = A.adam_v; }
+    if (fl & MER_META_UNCORRELATED) { S.Fv = A.F_var; S.dFv = A.dF_var; }
     S.n = n;
     S.C = C;
     S.zero_grads = zero_grads;
@@ -1293,12 +1367,20 @@ mer_status mer_meta_step_raw(const mer_hyper* hyper, int64_t n, int32_t C, const
 }
 
 // --------------------------------------------------------------------------------------
-// checkpoint: per problem ProbState + the nine parameter-shaped arrays
+// checkpoint: per problem ProbState + the nine parameter-shaped arrays (+ the variant state
+// its flags allocate)
 // --------------------------------------------------------------------------------------
+static std::vector<float*> ckpt_arrays(Problem* p) {
+    std::vector<float*> v = {p->pslot[0], p->pslot[1], p->F, p->dF, p->m2f, p->m2d, p->mean, p->var, p->ap};
+    for (float* a : {p->mu_f, p->mu_d, p->am, p->av, p->Fv, p->dFv})
+        if (a) v.push_back(a);
+    return v;
+}
+
 mer_status mer_checkpoint_save(mer_ctx* c, void* buf, size_t* len) {
     if (!c || !len) return fail(c, MER_ERR_INVALID_ARG, "null argument");
     size_t need = sizeof(uint64_t) * 2;
-    for (Problem* p : c->probs) need += sizeof(ProbState) + 9 * sizeof(float) * (size_t)p->n_par;
+    for (Problem* p : c->probs) need += sizeof(ProbState) + ckpt_arrays(p).size() * sizeof(float) * (size_t)p->n_par;
     if (!buf) {
         *len = need;
         return MER_OK;
@@ -1312,8 +1394,7 @@ mer_status mer_checkpoint_save(mer_ctx* c, void* buf, size_t* len) {
     for (Problem* p : c->probs) {
         CK(c, cudaMemcpyAsync(w, c->d_pstate + p->id, sizeof(ProbState), cudaMemcpyDeviceToHost, c->st));
         w += sizeof(ProbState);
-        float* arrs[9] = {p->pslot[0], p->pslot[1], p->F, p->dF, p->m2f, p->m2d, p->mean, p->var, p->ap};
-        for (float* a : arrs) {
+        for (float* a : ckpt_arrays(p)) {
             CK(c, cudaMemcpyAsync(w, a, sizeof(float) * p->n_par, cudaMemcpyDeviceToHost, c->st));
             w += sizeof(float) * p->n_par;
         }
@@ -1326,7 +1407,7 @@ mer_status mer_checkpoint_save(mer_ctx* c, void* buf, size_t* len) {
 mer_status mer_checkpoint_load(mer_ctx* c, const void* buf, size_t len) {
     if (!c || !buf) return fail(c, MER_ERR_INVALID_ARG, "null argument");
     size_t need = sizeof(uint64_t) * 2;
-    for (Problem* p : c->probs) need += sizeof(ProbState) + 9 * sizeof(float) * (size_t)p->n_par;
+    for (Problem* p : c->probs) need += sizeof(ProbState) + ckpt_arrays(p).size() * sizeof(float) * (size_t)p->n_par;
     uint64_t hdr[2];
     if (len < sizeof hdr) return fail(c, MER_ERR_INVALID_ARG, "checkpoint too short");
     memcpy(hdr, buf, sizeof hdr);
@@ -1337,8 +1418,7 @@ mer_status mer_checkpoint_load(mer_ctx* c, const void* buf, size_t len) {
     for (Problem* p : c->probs) {
         CK(c, cudaMemcpyAsync(c->d_pstate + p->id, r, sizeof(ProbState), cudaMemcpyHostToDevice, c->st));
         r += sizeof(ProbState);
-        float* arrs[9] = {p->pslot[0], p->pslot[1], p->F, p->dF, p->m2f, p->m2d, p->mean, p->var, p->ap};
-        for (float* a : arrs) {
+        for (float* a : ckpt_arrays(p)) {
             CK(c, cudaMemcpyAsync(a, r, sizeof(float) * p->n_par, cudaMemcpyHostToDevice, c->st));
             r += sizeof(float) * p->n_par;
         }

@@ -31,12 +31,18 @@ __device__ __forceinline__ void red_add(float* p, float a) {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(a) : "memory");
 }
 
-// per-problem fields the scatter needs, cached in shared memory
+// per-problem fields the scatter needs, cached in shared memory: the layout and the gradient
+// texture this launch adds to (NULL: the problem has none and its records are skipped)
 struct SProb {
     int C, W, H, pad;
-    float* F;
-    float* dF;
+    float* tgt;
+    float* pad2;
 };
+
+// gradient texture `which` of a problem: 0 F, 1 dF, 2 F_var, 3 dF_var
+__device__ __forceinline__ float* grad_target(const ProblemDev& P, int which) {
+    return which == 0 ? P.F : which == 1 ? P.dF : which == 2 ? P.Fv : P.dFv;
+}
 
 template <int CC>
 __device__ __forceinline__ void fill_row(float (&v)[10], const float (&g)[MAXC], float wa, float wb) {
@@ -161,9 +167,9 @@ __device__ __forceinline__ int stage_record(bool valid, float4 a, float4 b, cons
         // texture extents are below 4096 per side and C <= 5: offsets fit in 32 bits
         off0 = (ya * W + xa) * C;
         off1 = (yb * W + xa) * C;
-        base = grad_over ? grad_over : (which ? P.dF : P.F);
-        r0 = true;
-        r1 = !one_y;
+        base = grad_over ? grad_over : P.tgt;
+        r0 = base != nullptr;
+        r1 = r0 && !one_y;
         // same pos => same problem and layout; every lane of vmask runs every shuffle
         const unsigned peers = __match_any_sync(vmask, pos);
         const int maxg = (int)__reduce_max_sync(vmask, (unsigned)__popc(peers));
@@ -223,7 +229,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scatter(uint32_t* __restrict__ c
     uint64_t* bar = bars + wib * SC_STAGES;
     for (int t = threadIdx.x; t < n_probs; t += blockDim.x) {
         const ProblemDev& P = probs[t];
-        sp[t] = SProb{P.tex_c, P.tex_w, P.tex_h, 0, P.F, P.dF};
+        sp[t] = SProb{P.tex_c, P.tex_w, P.tex_h, 0, grad_target(P, which), nullptr};
     }
     if (lane == 0)
         for (int s = 0; s < SC_STAGES; ++s) mbar_init(&bar[s]);
@@ -273,12 +279,14 @@ __global__ void __launch_bounds__(SC_THREADS) k_scatter(uint32_t* __restrict__ c
     }
 }
 
-// float4 stores over each problem's F or dF (16-byte aligned allocations; scalar tail)
+// float4 stores over each problem's gradient texture `which` (16-byte aligned allocations;
+// scalar tail; problems without one are skipped)
 __global__ void k_zero_grads(const ProblemDev* __restrict__ probs, int n_probs, int which) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int q = 0; q < n_probs; ++q) {
-        float* g = which ? probs[q].dF : probs[q].F;
+        float* g = grad_target(probs[q], which);
+        if (!g) continue;
         const int64_t n = probs[q].n_par, n4 = n >> 2;
         float4* g4 = reinterpret_cast<float4*>(g);
         for (int64_t i = t0; i < n4; i += stride) g4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);

@@ -139,6 +139,8 @@ struct ProblemDev {
     float* pslot[2];
     float* F;
     float* dF;
+    float* Fv;                 // MER_META_UNCORRELATED: independent samples of F and dF (else NULL)
+    float* dFv;
     // per-pixel arrays [n_pix][3]
     const float* target;
     float* img;                // proportional primal image

@@ -8,8 +8,10 @@
 //   mean = a mean + (1-a) F ; var = a^2 var + (1-a)^2 m2f
 //   pi' = clamp(pi - lr mean / (sqrt(var) + eps))                 (update rule of Sec. 5)
 // ADAM mode (Sec. 5, Eqs. adam_moment, adam_ema_startup, adam_step) keeps m in `mean` and v
-// in `m2f`. Both modes write pi' into the other parameter slot, clear F and dF, and reduce
-// ||pi' - pi||^2 per problem deterministically (per-block partials, fixed-order sum).
+// in `m2f`. Both modes write pi' into the other parameter slot, optionally clear F and dF, and
+// reduce ||pi' - pi||^2 per problem deterministically (per-block partials, fixed-order sum).
+// META segments with MER_META_* variant flags take a scalar path (meta_elem_var) through the
+// same blocks; the method as stated keeps the float4 path.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -31,17 +33,37 @@ struct Coef {
     int stepD;
 };
 
+// prod_{j<=k} max(beta, j/(j+1)) in closed form: beta^min(k+1, K) * (k >= K ? K/(k+1) : 1),
+// K the first j with j/(j+1) > beta
+__device__ __forceinline__ double growing_prod(double beta, int k) {
+    long long K = (long long)floor(beta / (1.0 - beta));
+    if (K < 0) K = 0;
+    while (K > 0 && (double)(K - 1) / (double)K > beta) --K;
+    while ((double)K / (double)(K + 1) <= beta) ++K;
+    const long long reps = (long long)k + 1 < K ? (long long)k + 1 : K;
+    double p = pow(beta, (double)reps);
+    if ((long long)k >= K) p *= (double)K / (double)(k + 1);
+    return p;
+}
+
 __device__ __forceinline__ Coef make_coef(const UpdSeg& S, int iteration, int count_f, int count_d, double n2) {
     Coef k;
     const mer_hyper& h = S.hyper;
     if (h.mode == MER_MODE_META) {
         const double bf = (double)h.beta_f, bd = (double)h.beta_d;
-        k.cF = (float)((1.0 - bf) / (1.0 - pow(bf, (double)(count_f + 1))));
+        if (h.flags & MER_META_GROWING_BETA) {
+            const double b = fmax(bf, (double)count_f / (double)(count_f + 1));
+            k.cF = (float)((1.0 - b) / (1.0 - growing_prod(bf, count_f)));
+        } else {
+            k.cF = (float)((1.0 - bf) / (1.0 - pow(bf, (double)(count_f + 1))));
+        }
         k.stepD = (iteration >= 1 && n2 > 0.0) ? 1 : 0;
         k.cD = k.stepD ? (float)((1.0 - bd) / (1.0 - pow(bd, (double)(count_d + 1)))) : 0.0f;
         k.norm2 = (float)n2;
         k.inv_norm = k.stepD ? (float)(1.0 / sqrt(n2)) : 0.0f;
-        k.c1 = k.c2 = 0.0f;
+        const double t = (double)(iteration + 1);   // NAIVE_ADAM bias corrections
+        k.c1 = (float)(1.0 / (1.0 - pow((double)h.beta1, t)));
+        k.c2 = (float)(1.0 / (1.0 - pow((double)h.beta2, t)));
     } else {
         const double t = (double)(iteration + 1);
         k.c1 = (float)(1.0 / (1.0 - pow((double)h.beta1, t)));
@@ -84,6 +106,76 @@ __device__ __forceinline__ float adam_elem(const mer_hyper& h, const Coef& k, fl
     m = h.beta1 * m + (1.0f - h.beta1) * F;
     v = h.beta2 * v + (1.0f - h.beta2) * F * F;
     const float step = -h.lr * (m * k.c1) / (sqrtf(v * k.c2) + h.eps);
+    pnew = clampf(p + step, lo, hi);
+    return pnew - p;
+}
+
+// one element of META mode with variant flags (see the header); pprev = pi_{i-1} (PER_ELEMENT);
+// every state array is read and written through the segment at index e; returns the applied step
+__device__ __forceinline__ float meta_elem_var(const UpdSeg& S, const Coef& k, int64_t e, float p, float pprev,
+                                               float lo, float hi, float& pnew) {
+    const mer_hyper& h = S.hyper;
+    const int fl = h.flags;
+    const float F = S.F[e];
+    const float xF = (fl & MER_META_UNCORRELATED) ? S.Fv[e] : F;
+    float m2f = S.m2f[e] + k.cF * (xF * xF - S.m2f[e]);
+    S.m2f[e] = m2f;
+    float varf = m2f;
+    if (fl & MER_META_CENTRED) {
+        const float mu = S.mu_f[e] + k.cF * (xF - S.mu_f[e]);
+        S.mu_f[e] = mu;
+        varf = fmaxf(m2f - mu * mu, 0.0f);
+    }
+    float mean = S.mean[e], var = S.var[e];
+    if (k.stepD) {
+        const float dF = S.dF[e];
+        const float xD = (fl & MER_META_UNCORRELATED) ? S.dFv[e] : dF;
+        float d2, x;
+        bool live = true;
+        if (fl & MER_META_PER_ELEMENT) {
+            const float d = p - pprev;
+            d2 = d * d;
+            live = d2 > 0.0f;
+            x = live ? xD / fabsf(d) : 0.0f;
+        } else {
+            d2 = k.norm2;
+            x = xD * k.inv_norm;
+        }
+        float m2d = S.m2d[e];
+        if (live) {
+            m2d = m2d + k.cD * (x * x - m2d);
+            S.m2d[e] = m2d;
+        }
+        float vdd = m2d;
+        if (fl & MER_META_CENTRED) {
+            float mu = S.mu_d[e];
+            if (live) {
+                mu = mu + k.cD * (x - mu);
+                S.mu_d[e] = mu;
+            }
+            vdd = fmaxf(m2d - mu * mu, 0.0f);
+        }
+        mean = mean + dF;
+        var = var + vdd * d2;
+    }
+    float a = varf / (varf + var + h.eps_alpha);
+    if (!(fl & MER_META_NO_CLIP)) a = fminf(a, 1.0f / (2.0f - S.ap[e]));
+    S.ap[e] = a;
+    const float b = 1.0f - a;
+    mean = a * mean + b * F;
+    var = a * a * var + b * b * varf;
+    S.mean[e] = mean;
+    S.var[e] = var;
+    float step;
+    if (fl & MER_META_NAIVE_ADAM) {
+        const float m = h.beta1 * S.am[e] + (1.0f - h.beta1) * mean;
+        const float v = h.beta2 * S.av[e] + (1.0f - h.beta2) * mean * mean;
+        S.am[e] = m;
+        S.av[e] = v;
+        step = -h.lr * (m * k.c1) / (sqrtf(v * k.c2) + h.eps);
+    } else {
+        step = -h.lr * mean / (sqrtf(var) + h.eps);
+    }
     pnew = clampf(p + step, lo, hi);
     return pnew - p;
 }
@@ -156,6 +248,25 @@ __device__ __forceinline__ float update_block(const UpdSeg& S, const Coef& k, in
     float* pout = cur ? S.pA : S.pB;
     const bool meta = S.hyper.mode == MER_MODE_META;
     float acc = 0.0f;
+    if (meta && S.hyper.flags) {
+        // variants: one element per thread and step over the block's chunk (pout still holds
+        // pi_{i-1} when its element is read)
+        const int64_t e0 = local_block * UPD_CHUNK;
+        for (int it = 0; it < UPD_VEC_PER_THREAD * 4; ++it) {
+            const int64_t e = e0 + (int64_t)it * UPD_THREADS + threadIdx.x;
+            if (e >= S.n) break;
+            const int c = (int)((uint64_t)e % (uint64_t)S.C);
+            float pnew;
+            const float st = meta_elem_var(S, k, e, pin[e], pout[e], S.lo[c], S.hi[c], pnew);
+            pout[e] = pnew;
+            if (S.zero_grads) {
+                S.F[e] = 0.0f;
+                S.dF[e] = 0.0f;
+            }
+            acc += st * st;
+        }
+        return acc;
+    }
     const int64_t n4 = S.n >> 2;          // float4 count (the tail below handles n % 4)
     const int64_t v0 = local_block * (UPD_CHUNK >> 2);
 #pragma unroll
@@ -318,6 +429,9 @@ extern "C" mer_status mer_meta_step_raw_noalloc(const mer_hyper* hyper, int64_t 
     const bool meta = hyper->mode == MER_MODE_META;
     if (n > 0 && (!pi || !pi_next || !F || !m2f || !mean || (meta && (!dF || !m2d || !var || !alpha_prev))))
         return mer_internal_fail(MER_ERR_INVALID_ARG, "missing arrays in mer_meta_step_raw_noalloc");
+    if (meta && (hyper->flags & (MER_META_CENTRED | MER_META_NAIVE_ADAM | MER_META_UNCORRELATED)))
+        return mer_internal_fail(MER_ERR_INVALID_ARG,
+                                 "mer_meta_step_raw_noalloc: these flags need variant arrays (use mer_meta_step_raw_ex)");
     const void* ptrs[] = {pi, pi_next, F, dF, m2f, m2d, mean, var, alpha_prev};
     for (const void* q : ptrs)
         if (q && ((uintptr_t)q & 15u))

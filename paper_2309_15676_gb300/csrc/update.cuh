@@ -16,6 +16,13 @@ struct UpdSeg {
     float* mean;         // META: <F>_M;            ADAM: m
     float* var;          // META: Var[<F>_M]
     float* ap;           // META: alpha_{i-1}
+    // variant state (MER_META_* flags; NULL when the flag is off)
+    float* mu_f;         // CENTRED: EMA of the Var[<F>] samples
+    float* mu_d;         // CENTRED: EMA of the Var[<dF>]_D samples
+    float* am;           // NAIVE_ADAM: Adam's m over <F>_M
+    float* av;           // NAIVE_ADAM: Adam's v over <F>_M
+    const float* Fv;     // UNCORRELATED: independent samples for Var[<F>]
+    const float* dFv;    // UNCORRELATED: independent samples for Var[<dF>]_D
     int64_t n;
     int32_t C;
     int32_t prob;        // problem index (context form)
