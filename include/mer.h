@@ -60,6 +60,14 @@ typedef int mer_status;
  * shifted by this offset (streams 8..11) */
 #define MER_STREAM_VAR_OFFSET 8u
 
+/* Image loss of step a7 (N pixels, 3 channels, target T, image I):
+ *  L2    L = 1/(3N) sum (I - T)^2,               dL/dI = 2 (I - T) / (3N)
+ *  MRSE  L = 1/(3N) sum (I - T)^2 / (T^2 + 0.01), dL/dI = 2 (I - T) / ((T^2 + 0.01) 3N)
+ *        (the relative loss of Sec. 6's setup, normalised by the target only, so that the
+ *        adjoint stays linear in the independent primal image) */
+#define MER_LOSS_L2 0
+#define MER_LOSS_MRSE 1
+
 #define MER_MAX_CHANNELS 5
 #define MER_MAX_DEPTH 16
 #define MER_MAX_PROBLEMS 256
@@ -129,6 +137,7 @@ typedef struct mer_scene_desc {
     int32_t max_depth;        /* path segments (1 = emitters only, 2 = direct light) */
     int32_t spp_prop, spp_fd; /* samples per pixel and iteration */
     uint32_t seed, key_id;    /* Philox key */
+    int32_t loss;             /* MER_LOSS_* image loss of step a7 (0 = L2) */
     mer_hyper hyper;
 } mer_scene_desc;
 

@@ -820,6 +820,21 @@ double orc_l2_loss(int64_t n_pix, const double* img, const double* target, doubl
     return acc * inv;
 }
 
+/* Relative squared error of the experiments' setup (Sec. 6), normalised by the target alone:
+ * L = 1/(3N) sum (I - T)^2 / (T^2 + 0.01), dL/dI = 2 (I - T) / ((T^2 + 0.01) 3N). */
+double orc_mrse_loss(int64_t n_pix, const double* img, const double* target, double* dimg)
+{
+    double acc = 0.0;
+    double inv = 1.0 / (3.0 * (double)n_pix);
+    for (int64_t i = 0; i < 3 * n_pix; ++i) {
+        double r = img[i] - target[i];
+        double w = 1.0 / (target[i] * target[i] + 0.01);
+        acc += r * r * w;
+        if (dimg) dimg[i] = 2.0 * r * w * inv;
+    }
+    return acc * inv;
+}
+
 /* n Philox evaluations: ctr [n][4], out [n][4] */
 void orc_philox_batch(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out)
 {

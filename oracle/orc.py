@@ -62,6 +62,8 @@ def lib():
         L.orc_bsdf_sample.restype = ct.c_int
         L.orc_l2_loss.argtypes = [ct.c_int64, _f64p, _f64p, _f64p]
         L.orc_l2_loss.restype = ct.c_double
+        L.orc_mrse_loss.argtypes = [ct.c_int64, _f64p, _f64p, _f64p]
+        L.orc_mrse_loss.restype = ct.c_double
         _lib = L
     return _lib
 
@@ -193,6 +195,22 @@ def l2_loss(img, target):
     return loss, d
 
 
+LOSS_L2, LOSS_MRSE = 0, 1
+
+
+def mrse_loss(img, target):
+    """Relative squared error (Sec. 6 setup) and its adjoint image; see orc_mrse_loss."""
+    img = np.ascontiguousarray(img, np.float64)
+    target = np.ascontiguousarray(target, np.float64)
+    d = np.zeros_like(img)
+    loss = lib().orc_mrse_loss(img.size // 3, _p(img, _f64p), _p(target, _f64p), _p(d, _f64p))
+    return loss, d
+
+
+def image_loss(img, target, kind=LOSS_L2):
+    return mrse_loss(img, target) if kind == LOSS_MRSE else l2_loss(img, target)
+
+
 def bsdf(mtype, th, n, wo, wi):
     th = np.ascontiguousarray(th, np.float64)
     n, wo, wi = (np.ascontiguousarray(x, np.float64) for x in (n, wo, wi))
@@ -216,25 +234,25 @@ def bsdf_sample(mtype, th, n, wo, ul, u1, u2):
 # one iteration's gradient estimates (Sec. 3, Eq. est_def and est_triv)
 # ---------------------------------------------------------------------------
 
-def prop_gradient(sc: Scene, tex, target, spp, iteration, stream_offset=0):
-    """<F_i>: L2-loss gradient with an independent primal image (stream PROP_PRIMAL) for the
+def prop_gradient(sc: Scene, tex, target, spp, iteration, stream_offset=0, loss_kind=0):
+    """<F_i>: image-loss gradient (L2, or MRSE with loss_kind 1) with an independent primal image (stream PROP_PRIMAL) for the
     adjoint weights and the PRB adjoint on stream PROP_ADJ. Returns (grad, loss, image).
     stream_offset shifts both streams (the independent variance samples of the uncorrelated
     variant use offset 8)."""
     img = render_image(sc, tex, spp, iteration, ST_PROP_PRIMAL + stream_offset)
-    loss, dimg = l2_loss(img, target)
+    loss, dimg = image_loss(img, target, loss_kind)
     g = adjoint_image(sc, tex, spp, iteration, ST_PROP_ADJ + stream_offset, dimg)
     return g, loss, img
 
 
-def fd_gradient(sc: Scene, tex_cur, tex_prev, target, spp, iteration, stream_offset=0):
+def fd_gradient(sc: Scene, tex_cur, tex_prev, target, spp, iteration, stream_offset=0, loss_kind=0):
     """<dF_i> = <F_i>(u) - <F_{i-1}>(u): both terms use the same counters (streams FD_PRIMAL
     for the adjoint weights and FD_ADJ for the adjoint) at pi_i and pi_{i-1}; stream_offset
     shifts both streams as in prop_gradient."""
     img_c = render_image(sc, tex_cur, spp, iteration, ST_FD_PRIMAL + stream_offset)
     img_p = render_image(sc, tex_prev, spp, iteration, ST_FD_PRIMAL + stream_offset)
-    _, d_c = l2_loss(img_c, target)
-    _, d_p = l2_loss(img_p, target)
+    _, d_c = image_loss(img_c, target, loss_kind)
+    _, d_p = image_loss(img_p, target, loss_kind)
     g_c = adjoint_image(sc, tex_cur, spp, iteration, ST_FD_ADJ + stream_offset, d_c)
     g_p = adjoint_image(sc, tex_prev, spp, iteration, ST_FD_ADJ + stream_offset, d_p)
     return g_c - g_p

@@ -43,6 +43,7 @@ class SceneDesc(ct.Structure):
         ("clamp_lo", _f * 8), ("clamp_hi", _f * 8),
         ("max_depth", ct.c_int32), ("spp_prop", ct.c_int32), ("spp_fd", ct.c_int32),
         ("seed", ct.c_uint32), ("key_id", ct.c_uint32),
+        ("loss", ct.c_int32),
         ("hyper", Hyper),
     ]
 

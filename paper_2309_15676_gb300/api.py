@@ -40,6 +40,10 @@ class HyperParams:
                           self.beta2, self.flags)
 
 
+# image losses (scene key "loss"; the header's MER_LOSS_* values)
+LOSS_L2 = 0
+LOSS_MRSE = 1
+
 # variant bits of HyperParams.flags (the header's MER_META_* values)
 META_PER_ELEMENT = 1
 META_NO_CLIP = 2
@@ -116,6 +120,7 @@ def scene_desc(scene: dict, hyper: HyperParams) -> tuple[_lib.SceneDesc, _Arr]:
     d.max_depth = int(scene["max_depth"])
     d.spp_prop, d.spp_fd = int(scene["spp_prop"]), int(scene["spp_fd"])
     d.seed, d.key_id = int(scene["seed"]) & 0xFFFFFFFF, int(scene["key_id"]) & 0xFFFFFFFF
+    d.loss = int(scene.get("loss", LOSS_L2))
     d.hyper = hyper.to_c()
     return d, A
 

@@ -682,6 +682,7 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
         return fail(c, MER_ERR_INVALID_ARG, "texture must be C in {3,5}, 1..4094 texels per side");
     if (d->max_depth < 1 || d->max_depth > MER_MAX_DEPTH) return fail(c, MER_ERR_INVALID_ARG, "max_depth out of range");
     if (d->spp_prop < 1 || d->spp_fd < 0) return fail(c, MER_ERR_INVALID_ARG, "bad spp");
+    if (d->loss != MER_LOSS_L2 && d->loss != MER_LOSS_MRSE) return fail(c, MER_ERR_INVALID_ARG, "bad loss");
     for (int i = 0; i < d->n_mats; ++i) {
         if (d->mat_type[i] != 0 && d->mat_type[i] != 1) return fail(c, MER_ERR_INVALID_ARG, "bad material type");
         if (d->mat_type[i] == 1 && d->mat_textured[i] && d->tex_c != 5)
@@ -901,6 +902,7 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     D.spp_fd = p->spp_fd;
     D.seed = d->seed;
     D.key_id = d->key_id;
+    D.loss_kind = d->loss;
     // ---- optimiser state and images ----
     const size_t np = (size_t)p->n_par, npx = (size_t)p->n_pix * 3;
     AK(alloc(&p->pslot[0], np));

@@ -325,9 +325,10 @@ int run_scatter(uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev
     return 1;
 }
 
-// L2 loss L = 1/(3N) sum (I - T)^2 and its adjoint image dL/dI = 2 (I - T) / (3N), for the
-// proportional image (loss accumulated per problem in FP64) and, with_fd, the two images of the
-// FD pair. Pixels of all problems are enumerated through the prefix pix_pref.
+// Image loss (step a7) and its adjoint image, per problem: L2, L = 1/(3N) sum (I - T)^2 with
+// dL/dI = 2 (I - T) / (3N), or MRSE, each term divided by (T^2 + 0.01), for the proportional
+// image (loss accumulated per problem in FP64) and, with_fd, the two images of the FD pair.
+// Pixels of all problems are enumerated through the prefix pix_pref.
 __global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs, const int64_t* __restrict__ pix_pref,
                                             int n_probs, int64_t total_pix, int with_fd, double* loss_acc) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -341,16 +342,18 @@ __global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs
             const ProblemDev& P = probs[q];
             const int64_t lp = p - pix_pref[q];
             const float sc = 2.0f / (3.0f * (float)P.n_pix);
+            const bool rel = P.loss_kind == MER_LOSS_MRSE;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int64_t k = lp * 3 + c;
                 const float t = P.target[k];
+                const float w = rel ? 1.0f / (t * t + 0.01f) : 1.0f;
                 const float r = P.img[k] - t;
-                P.dimg[k] = sc * r;
-                l += (double)r * (double)r;
+                P.dimg[k] = sc * r * w;
+                l += (double)r * (double)r * (double)w;
                 if (with_fd && P.imgA) {
-                    P.dimgA[k] = sc * (P.imgA[k] - t);
-                    P.dimgB[k] = sc * (P.imgB[k] - t);
+                    P.dimgA[k] = sc * (P.imgA[k] - t) * w;
+                    P.dimgB[k] = sc * (P.imgB[k] - t) * w;
                 }
             }
         }

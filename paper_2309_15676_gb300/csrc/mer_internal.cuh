@@ -139,6 +139,7 @@ struct ProblemDev {
     float* pslot[2];
     float* F;
     float* dF;
+    int32_t loss_kind;         // MER_LOSS_*
     float* Fv;                 // MER_META_UNCORRELATED: independent samples of F and dF (else NULL)
     float* dFv;
     // per-pixel arrays [n_pix][3]

@@ -84,3 +84,24 @@ def test_streams_and_iterations_decorrelate(oracle_lib):
     a2 = orc.render_image(sc, tex, 1, 0, orc.ST_PROP_PRIMAL)
     assert np.array_equal(a, a2)
     assert not np.allclose(a, b) and not np.allclose(a, c)
+
+
+def test_mrse_loss_constant_target_and_fd(oracle_lib):
+    """MRSE with a constant target c is the L2 loss divided by c^2 + 0.01 (loss and adjoint); its
+    adjoint image is the derivative of the loss (central differences on a tiny image)."""
+    rng = np.random.default_rng(31)
+    img = rng.uniform(0, 2, (3, 4, 3))
+    c = 0.7
+    tgt = np.full_like(img, c)
+    l2, d2 = orc.l2_loss(img, tgt)
+    lm, dm = orc.mrse_loss(img, tgt)
+    assert np.isclose(lm, l2 / (c * c + 0.01), rtol=1e-14) and np.allclose(dm, d2 / (c * c + 0.01), rtol=1e-14)
+    tgt = rng.uniform(0, 1, img.shape)
+    _, dm = orc.mrse_loss(img, tgt)
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 2, 1), (2, 3, 2)]:
+        a, b = img.copy(), img.copy()
+        a[idx] += h
+        b[idx] -= h
+        fd = (orc.mrse_loss(a, tgt)[0] - orc.mrse_loss(b, tgt)[0]) / (2 * h)
+        assert abs(fd - dm[idx]) <= 1e-7 * abs(dm[idx]) + 1e-12
