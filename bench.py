@@ -290,6 +290,10 @@ def batched_compare(torch, n_problems=64, iters=3, seed=4):
     return out
 
 
+NODE_FLOPS = 97.0    # one four-wide node test: 4 slab tests of 6 FMA + 12 min/max, plus the bound's scaling
+PRIM_FLOPS = 45.0    # one Moller-Trumbore triangle test
+
+
 def touched_texels(ctx, pid):
     """Texels that receive gradient in one gradient step: (proportional F, finite-difference dF).
     Runs a1-a10 once, reads both gradient textures, then applies the update (which clears them);
@@ -485,13 +489,13 @@ def run_mine(args):
                           "frac": gbs / hbm_peak, "bytes_per_launch": byts, "ms": avg_ms,
                           "note": "327,680 params (21 MB) stay L2-resident at this size"})
     upd67 = update_roofline(torch, hbm_peak) if rank == 0 else None
-    # dominant kernel: BVH traversal on the FP32 pipes; algorithmic work = node tests x 49 FP32 ops
-    # (12 FMA = 24, 24 min/max, 1 mul) + primitive tests x 45 (Moller-Trumbore), measured by the
+    # dominant kernel: BVH traversal on the FP32 pipes; algorithmic work = four-box node tests x 97
+    # FP32 ops (24 FMA = 48, 48 min/max, 1 mul) + primitive tests x 45 (Moller-Trumbore), measured by the
     # counting run; peak = 152 SMs x 128 FP32 lanes x 2 x max SM clock
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     dk = prof[dom]
     ck = counts.get(dom, {})
-    flops = 49.0 * ck.get("node_tests", 0) + 45.0 * ck.get("prim_tests", 0)
+    flops = NODE_FLOPS * ck.get("node_tests", 0) + PRIM_FLOPS * ck.get("prim_tests", 0)
     ach = flops / (dk["ms"] * 1e-3) / 1e12 if flops else None
     roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": (ach / fp32_peak) if ach else None, "traffic": None,
@@ -505,7 +509,8 @@ def run_mine(args):
         if c.get("node_tests"):
             v["node_tests_per_iter"] = c["node_tests"] / n_prof
             v["prim_tests_per_iter"] = c["prim_tests"] / n_prof
-            v["tflops"] = (49.0 * c["node_tests"] + 45.0 * c["prim_tests"]) / (v["ms_per_iter"] * n_prof * 1e-3) / 1e12
+            v["tflops"] = (NODE_FLOPS * c["node_tests"] + PRIM_FLOPS * c["prim_tests"]) / (
+                v["ms_per_iter"] * n_prof * 1e-3) / 1e12
     if dom in ("update", "scatter"):
         rr = [r for r in rooflines if r["kernel"] == dom][0]
         roof = dict(rr, traffic=None, share=kernels[dom]["share"])

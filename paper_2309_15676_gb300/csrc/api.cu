@@ -755,14 +755,21 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     if (d->n_tris > 0) {
         std::vector<HostNode> hn;
         std::vector<int> order;
-        build_bvh(d->positions, d->tris, d->n_tris, hn, order);
-        std::vector<Node> nodes(hn.size());
-        for (size_t i = 0; i < hn.size(); ++i) {
-            const HostNode& h = hn[i];
-            nodes[i].a = make_float4(h.lo[0][0], h.hi[0][0], h.lo[0][1], h.hi[0][1]);
-            nodes[i].b = make_float4(h.lo[1][0], h.hi[1][0], h.lo[1][1], h.hi[1][1]);
-            nodes[i].c = make_float4(h.lo[0][2], h.hi[0][2], h.lo[1][2], h.hi[1][2]);
-            nodes[i].d = make_int4(h.child[0], h.child[1], 0, 0);
+        const int root2 = build_bvh(d->positions, d->tris, d->n_tris, hn, order);
+        std::vector<HostNode4> h4;
+        collapse_bvh4(hn, root2, h4);
+        std::vector<Node> nodes(h4.size());
+        for (size_t i = 0; i < h4.size(); ++i) {
+            const HostNode4& h = h4[i];
+            Node& n = nodes[i];
+            n.lx = make_float4(h.lo[0][0], h.lo[1][0], h.lo[2][0], h.lo[3][0]);
+            n.hx = make_float4(h.hi[0][0], h.hi[1][0], h.hi[2][0], h.hi[3][0]);
+            n.ly = make_float4(h.lo[0][1], h.lo[1][1], h.lo[2][1], h.lo[3][1]);
+            n.hy = make_float4(h.hi[0][1], h.hi[1][1], h.hi[2][1], h.hi[3][1]);
+            n.lz = make_float4(h.lo[0][2], h.lo[1][2], h.lo[2][2], h.lo[3][2]);
+            n.hz = make_float4(h.hi[0][2], h.hi[1][2], h.hi[2][2], h.hi[3][2]);
+            n.child = make_int4(h.child[0], h.child[1], h.child[2], h.child[3]);
+            n.pad = make_int4(0, 0, 0, 0);
         }
         std::vector<TriGeo> tg(d->n_tris);
         std::vector<TriAttr> ta(d->n_tris);
@@ -1435,7 +1442,7 @@ mer_status mer_autotune(mer_ctx* c, int32_t trial_iters, char* desc, size_t desc
     // candidates: block size x blocks per SM x shared-memory node staging
     const int blocks[] = {64, 128, 256};   // <= the kernels' launch bounds
     const int per_sm[] = {2, 4, 8, 16};
-    const int smem[] = {0, 256, 1024};
+    const int smem[] = {0, 128, 512};   // 128-byte nodes: 16 KB, 64 KB
     // every trial runs full iterations on a checkpoint of the state, restored afterwards
     size_t len = 0;
     mer_status s = mer_checkpoint_save(c, nullptr, &len);

@@ -1,6 +1,6 @@
 // Host-side BVH construction: binned SAH over triangle bounds (16 bins per axis,
-// leaves of at most 4 triangles), emitted in the two-boxes-per-node layout the
-// traversal kernels read (see Node in mer_internal.cuh).
+// leaves of at most 4 triangles), then collapsed into the four-wide nodes the traversal
+// kernels read (see Node in mer_internal.cuh).
 #include "bvh.h"
 
 #include <algorithm>
@@ -159,6 +159,69 @@ int build_bvh(const float* pos, const int32_t* tris, int n_tris, std::vector<Hos
     nodes.swap(B.nodes);
     order.swap(B.idx);
     return root;
+}
+
+namespace {
+
+struct Slot {
+    float lo[3], hi[3];
+    int ref;
+    float area() const {
+        const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return 2.0f * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+Slot slot_of(const HostNode& n, int k) {
+    Slot s;
+    for (int a = 0; a < 3; ++a) {
+        s.lo[a] = n.lo[k][a];
+        s.hi[a] = n.hi[k][a];
+    }
+    s.ref = n.child[k];
+    return s;
+}
+
+int emit4(const std::vector<HostNode>& bin, int n2, std::vector<HostNode4>& out) {
+    const int me = (int)out.size();
+    out.emplace_back();
+    Slot slots[4];
+    int ns = 2;
+    slots[0] = slot_of(bin[n2], 0);
+    slots[1] = slot_of(bin[n2], 1);
+    while (ns < 4) {
+        int best = -1;
+        float best_area = -1.0f;
+        for (int k = 0; k < ns; ++k)
+            if (slots[k].ref >= 0 && slots[k].area() > best_area) {
+                best = k;
+                best_area = slots[k].area();
+            }
+        if (best < 0) break;
+        const HostNode& c = bin[slots[best].ref];
+        slots[best] = slot_of(c, 0);
+        slots[ns++] = slot_of(c, 1);
+    }
+    int refs[4];
+    for (int k = 0; k < ns; ++k) refs[k] = slots[k].ref >= 0 ? emit4(bin, slots[k].ref, out) : slots[k].ref;
+    HostNode4& w = out[me];
+    for (int k = 0; k < 4; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            w.lo[k][a] = k < ns ? slots[k].lo[a] : 0.0f;
+            w.hi[k][a] = k < ns ? slots[k].hi[a] : 0.0f;
+        }
+        w.child[k] = k < ns ? refs[k] : kEmptyChild;
+    }
+    return me;
+}
+
+}  // namespace
+
+void collapse_bvh4(const std::vector<HostNode>& bin, int root, std::vector<HostNode4>& out) {
+    out.clear();
+    if (root < 0) return;
+    out.reserve(bin.size() / 2 + 1);
+    emit4(bin, root, out);
 }
 
 }  // namespace mer

@@ -15,6 +15,19 @@ struct HostNode {
     int child[2];
 };
 
+// Four-wide inner node: up to four child boxes and references (same encoding as HostNode;
+// unused slots hold kEmptyChild and an empty box).
+constexpr int kEmptyChild = 0x7fffffff;
+struct HostNode4 {
+    float lo[4][3], hi[4][3];
+    int child[4];
+};
+
+// Collapses a binary BVH (root `root`) into a four-wide one, root at index 0: each wide node
+// starts from a binary node's two children and repeatedly replaces the inner child of largest
+// surface area by its own two children until it holds four (or only leaves are left).
+void collapse_bvh4(const std::vector<HostNode>& bin, int root, std::vector<HostNode4>& out);
+
 // Builds a binned-SAH BVH over n_tris triangles (vertex positions pos[nv][3], indices
 // tris[n][3]). Returns the root's local index (-1 if no triangles); order[k] is the
 // original triangle id of leaf-ordered triangle k.

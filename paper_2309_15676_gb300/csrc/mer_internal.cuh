@@ -68,14 +68,15 @@ __device__ __forceinline__ v3 normalize(v3 a) { return a * (1.0f / sqrtf(dot(a, 
 // ---------------------------------------------------------------------------------
 // scene layout in HBM (per problem; ProblemDev holds the pointers)
 // ---------------------------------------------------------------------------------
-// BVH2 node, 64 B: both children's boxes stored in the parent so one node fetch tests both.
-//   a = (L.lo.x, L.hi.x, L.lo.y, L.hi.y)   b = (R.lo.x, R.hi.x, R.lo.y, R.hi.y)
-//   c = (L.lo.z, L.hi.z, R.lo.z, R.hi.z)   d = (left, right, left_count, right_count)
+// Four-wide BVH node, 128 B: the four children's boxes stored in the parent, one slab per
+// float4 (component k = child k), so one node fetch (seven 16-byte loads) tests all four.
 // child >= 0: inner node index; child < 0: leaf ~((first << 3) | (count - 1)) over the
-// leaf-ordered triangles [first, first + count).
-struct Node {
-    float4 a, b, c;
-    int4 d;
+// leaf-ordered triangles [first, first + count); NODE_EMPTY: unused slot.
+constexpr int NODE_EMPTY = 0x7fffffff;
+struct __align__(16) Node {
+    float4 lx, hx, ly, hy, lz, hz;
+    int4 child;
+    int4 pad;
 };
 
 // leaf-ordered triangle, 48 B: v0 (w = original primitive id as int bits), e1, e2

@@ -34,11 +34,13 @@ __device__ __forceinline__ Node load_node(const Node* __restrict__ nodes, const 
     if (i < smem_n) return s_nodes[i];
     const float4* p = reinterpret_cast<const float4*>(nodes + i);
     Node n;
-    n.a = __ldg(p);
-    n.b = __ldg(p + 1);
-    n.c = __ldg(p + 2);
-    const int4 d = __ldg(reinterpret_cast<const int4*>(p + 3));
-    n.d = d;
+    n.lx = __ldg(p);
+    n.hx = __ldg(p + 1);
+    n.ly = __ldg(p + 2);
+    n.hy = __ldg(p + 3);
+    n.lz = __ldg(p + 4);
+    n.hz = __ldg(p + 5);
+    n.child = __ldg(reinterpret_cast<const int4*>(p + 6));
     return n;
 }
 
@@ -95,7 +97,7 @@ struct Hit {
 // smaller primitive id, independent of traversal order.
 // algorithmic work of a traversal (counted only in the counting instantiation)
 struct TravCount {
-    unsigned nodes = 0;   // two-box node tests
+    unsigned nodes = 0;   // four-box node tests
     unsigned prims = 0;   // triangle and sphere tests
 };
 
@@ -121,32 +123,45 @@ __device__ __forceinline__ bool traverse(const ProblemDev& P, const Node* s_node
                 const Node n = load_node(P.nodes, s_nodes, smem_n, node);
                 if (STATS) tc.nodes++;
                 const float tfar = h.t * grow;
-                const float l0x = fmaf(n.a.x, ix, -ox), l1x = fmaf(n.a.y, ix, -ox);
-                const float l0y = fmaf(n.a.z, iy, -oy), l1y = fmaf(n.a.w, iy, -oy);
-                const float l0z = fmaf(n.c.x, iz, -oz), l1z = fmaf(n.c.y, iz, -oz);
-                const float r0x = fmaf(n.b.x, ix, -ox), r1x = fmaf(n.b.y, ix, -ox);
-                const float r0y = fmaf(n.b.z, iy, -oy), r1y = fmaf(n.b.w, iy, -oy);
-                const float r0z = fmaf(n.c.z, iz, -oz), r1z = fmaf(n.c.w, iz, -oz);
-                const float lmin = fmaxf(fmaxf(fminf(l0x, l1x), fminf(l0y, l1y)), fmaxf(fminf(l0z, l1z), 0.0f));
-                const float lmax = fminf(fminf(fmaxf(l0x, l1x), fmaxf(l0y, l1y)), fminf(fmaxf(l0z, l1z), tfar));
-                const float rmin = fmaxf(fmaxf(fminf(r0x, r1x), fminf(r0y, r1y)), fmaxf(fminf(r0z, r1z), 0.0f));
-                const float rmax = fminf(fminf(fmaxf(r0x, r1x), fmaxf(r0y, r1y)), fminf(fmaxf(r0z, r1z), tfar));
-                const bool hl = lmin <= lmax, hr = rmin <= rmax;
-                if (hl && hr) {
-                    int nearc = n.d.x, farc = n.d.y;
-                    if (rmin < lmin) { nearc = n.d.y; farc = n.d.x; }
-                    if (sp < 64) stack[sp++] = farc;
-                    node = nearc;
-                } else if (hl) {
-                    node = n.d.x;
-                } else if (hr) {
-                    node = n.d.y;
-                } else {
-                    if (sp == 0) { node = 0x7fffffff; break; }
-                    node = stack[--sp];
+                // slab test of the four children; a miss (or an unused slot) sorts last
+                float tn[4];
+                int rf[4];
+                const float lxs[4] = {n.lx.x, n.lx.y, n.lx.z, n.lx.w}, hxs[4] = {n.hx.x, n.hx.y, n.hx.z, n.hx.w};
+                const float lys[4] = {n.ly.x, n.ly.y, n.ly.z, n.ly.w}, hys[4] = {n.hy.x, n.hy.y, n.hy.z, n.hy.w};
+                const float lzs[4] = {n.lz.x, n.lz.y, n.lz.z, n.lz.w}, hzs[4] = {n.hz.x, n.hz.y, n.hz.z, n.hz.w};
+                const int cs[4] = {n.child.x, n.child.y, n.child.z, n.child.w};
+                int nh = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float x0 = fmaf(lxs[k], ix, -ox), x1 = fmaf(hxs[k], ix, -ox);
+                    const float y0 = fmaf(lys[k], iy, -oy), y1 = fmaf(hys[k], iy, -oy);
+                    const float z0 = fmaf(lzs[k], iz, -oz), z1 = fmaf(hzs[k], iz, -oz);
+                    const float t0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
+                    const float t1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tfar));
+                    const bool hit = t0 <= t1 && cs[k] != NODE_EMPTY;
+                    tn[k] = hit ? t0 : INFINITY;
+                    rf[k] = cs[k];
+                    nh += hit ? 1 : 0;
                 }
+                if (nh == 0) {
+                    if (sp == 0) { node = NODE_EMPTY; break; }
+                    node = stack[--sp];
+                    continue;
+                }
+                // nearest first: five compare-exchanges sort the four (t, child) pairs
+#define MER_CX(i, j)                                   \
+    if (tn[j] < tn[i]) {                               \
+        const float tt = tn[i]; tn[i] = tn[j]; tn[j] = tt; \
+        const int rr = rf[i]; rf[i] = rf[j]; rf[j] = rr;   \
+    }
+                MER_CX(0, 1) MER_CX(2, 3) MER_CX(0, 2) MER_CX(1, 3) MER_CX(1, 2)
+#undef MER_CX
+                if (nh > 3 && sp < 64) stack[sp++] = rf[3];
+                if (nh > 2 && sp < 64) stack[sp++] = rf[2];
+                if (nh > 1 && sp < 64) stack[sp++] = rf[1];
+                node = rf[0];
             }
-            if (node == 0x7fffffff) break;
+            if (node == NODE_EMPTY) break;
             // leaf
             const int x = ~node;
             const int first = x >> 3, count = (x & 7) + 1;
@@ -361,7 +376,7 @@ __device__ __forceinline__ int stage_nodes(const PassArgs& A, const Node*& s_nod
         cnt = P.nodes ? min(A.smem_nodes, P.n_nodes) : 0;
         const float4* src = reinterpret_cast<const float4*>(P.nodes);
         float4* dst = reinterpret_cast<float4*>(s);
-        for (int i = threadIdx.x; i < cnt * 4; i += blockDim.x) dst[i] = __ldg(src + i);
+        for (int i = threadIdx.x; i < cnt * 8; i += blockDim.x) dst[i] = __ldg(src + i);
         __syncthreads();
     }
     return cnt;
@@ -381,14 +396,17 @@ __device__ __forceinline__ void flush_counts(const PassArgs& A, int cls, const T
 
 // closest hit of path-queue entry j of depth `depth` (once per coincident pair)
 template <int NB, bool STATS>
+// Continuation item j: branch bsel only (an FD pair's two branches in two lanes), or every
+// branch in turn (bsel = -1).
 __device__ __forceinline__ void extend_item(const PassArgs& A, const Node* s_nodes, int n_staged, int depth, int64_t j,
-                                            TravCount& tc) {
+                                            int bsel, TravCount& tc) {
     const bool first = depth == 1;
     const int qi = depth & 1;
     uint32_t flags;
     int q;
     v3 o[NB], d[NB];
     if (first) {
+        if (NB == 2 && bsel == 1) return;   // both branches start on the same camera ray
         const PathId id = decode_path(A, j);
         q = id.q;
         const ProblemDev& P = A.probs[q];
@@ -400,8 +418,10 @@ __device__ __forceinline__ void extend_item(const PassArgs& A, const Node* s_nod
     } else {
         flags = A.qu[qi][QU_FLAGS * A.qcap + j];
         q = (flags >> 8) & 0xff;
+        if (bsel >= 0 && (!(flags & (1u << bsel)) || (bsel == 1 && (flags & FLAG_COINC)))) return;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
+            if (bsel >= 0 && b != bsel) continue;
             const float* f = A.qf[qi] + (size_t)(b * QF_PER_BRANCH) * A.qcap + j;
             o[b] = mk(f[(QF_O + 0) * A.qcap], f[(QF_O + 1) * A.qcap], f[(QF_O + 2) * A.qcap]);
             d[b] = mk(f[(QF_D + 0) * A.qcap], f[(QF_D + 1) * A.qcap], f[(QF_D + 2) * A.qcap]);
@@ -410,6 +430,7 @@ __device__ __forceinline__ void extend_item(const PassArgs& A, const Node* s_nod
     const ProblemDev& P = A.probs[q];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
+        if (bsel >= 0 && b != bsel) continue;
         if (!(flags & (1u << b))) continue;
         if (b == 1 && (flags & FLAG_COINC)) continue;
         Hit h;
@@ -808,12 +829,21 @@ __global__ void __launch_bounds__(256) k_trace(PassArgs A, int depth_ext, int de
     const int n_staged = stage_nodes(A, s_nodes);
     const int64_t n_ext = depth_ext == 1 ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth_ext], A.qcap);
     const int64_t n_sh = depth_sh > 0 ? min((int64_t)A.cnt[CNT_S + depth_sh], A.shcap) : 0;
-    const int64_t n = n_ext + n_sh;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // a launch whose lanes all fit in one pass of the resident grid is bound by the latency of
+    // its slowest item: an FD pair's two continuation rays then take two lanes; with more work
+    // than lanes, one lane traces both (fewer idle lanes, one read of the pair's state)
+    const bool split = NB == 2 && 2 * n_ext + n_sh <= stride;
+    const int64_t n_ext_lanes = split ? 2 * n_ext : n_ext;
+    const int64_t n = n_ext_lanes + n_sh;
     TravCount tc_e, tc_s;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        if (j < n_ext) extend_item<NB, STATS>(A, s_nodes, n_staged, depth_ext, j, tc_e);
-        else shadow_item<NB, MODE, STATS>(A, s_nodes, n_staged, j - n_ext, tc_s);
+        if (j < n_ext_lanes) {
+            if (split) extend_item<NB, STATS>(A, s_nodes, n_staged, depth_ext, j >> 1, (int)(j & 1), tc_e);
+            else extend_item<NB, STATS>(A, s_nodes, n_staged, depth_ext, j, NB == 2 ? -1 : 0, tc_e);
+        } else {
+            shadow_item<NB, MODE, STATS>(A, s_nodes, n_staged, j - n_ext_lanes, tc_s);
+        }
     }
     if (STATS) {
         const int cls = (NB == 1 ? KC_TRACE1_PRIMAL : KC_TRACE2_PRIMAL) + (MODE == MODE_REPLAY ? 1 : 0);
