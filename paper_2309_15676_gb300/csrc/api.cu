@@ -533,6 +533,7 @@ mer_status reset_state(mer_ctx* c, Problem* p) {
     for (float* a : {p->mu_f, p->mu_d, p->am, p->av, p->Fv, p->dFv})
         if (a) CK(c, cudaMemsetAsync(a, 0, nb, c->st));
     ProbState ps{};
+    ps.coef = update_coef(p->hyper, 0, 0, 0, 0.0);
     CK(c, cudaMemcpyAsync(c->d_pstate + p->id, &ps, sizeof ps, cudaMemcpyHostToDevice, c->st));
     CK(c, cudaStreamSynchronize(c->st));
     return MER_OK;

@@ -155,6 +155,13 @@ struct ProblemDev {
 
 // per-problem scalars that live on the device (read and advanced by kernels, so that a
 // captured iteration needs no host round trip)
+// per-problem scalars of the fused update for the coming iteration (start-up corrections, the
+// step-norm terms, Adam's bias corrections), computed once per problem and iteration
+struct UpdCoef {
+    float cF, cD, norm2, inv_norm, c1, c2;
+    int32_t stepD, pad;
+};
+
 struct ProbState {
     int32_t iteration;         // optimisation iteration i
     int32_t count_f, count_d;  // Moment2 step counts
@@ -162,6 +169,8 @@ struct ProbState {
     double dpi_norm2;          // ||pi_i - pi_{i-1}||^2 of the applied step
     double loss;               // L2 loss of the proportional primal image of the last gradient step
     double loss_acc;           // accumulator used by the loss kernel
+    UpdCoef coef;              // this iteration's update coefficients (set at reset and by the
+                               // previous update's finalize)
 };
 
 // ---------------------------------------------------------------------------------

@@ -28,51 +28,7 @@ constexpr int64_t UPD_CHUNK = (int64_t)UPD_THREADS * UPD_VEC_PER_THREAD * 4;   /
 
 int64_t update_blocks_for(int64_t n) { return (n + UPD_CHUNK - 1) / UPD_CHUNK; }
 
-struct Coef {
-    float cF, cD, norm2, inv_norm, c1, c2;
-    int stepD;
-};
-
-// prod_{j<=k} max(beta, j/(j+1)) in closed form: beta^min(k+1, K) * (k >= K ? K/(k+1) : 1),
-// K the first j with j/(j+1) > beta
-__device__ __forceinline__ double growing_prod(double beta, int k) {
-    long long K = (long long)floor(beta / (1.0 - beta));
-    if (K < 0) K = 0;
-    while (K > 0 && (double)(K - 1) / (double)K > beta) --K;
-    while ((double)K / (double)(K + 1) <= beta) ++K;
-    const long long reps = (long long)k + 1 < K ? (long long)k + 1 : K;
-    double p = pow(beta, (double)reps);
-    if ((long long)k >= K) p *= (double)K / (double)(k + 1);
-    return p;
-}
-
-__device__ __forceinline__ Coef make_coef(const UpdSeg& S, int iteration, int count_f, int count_d, double n2) {
-    Coef k;
-    const mer_hyper& h = S.hyper;
-    if (h.mode == MER_MODE_META) {
-        const double bf = (double)h.beta_f, bd = (double)h.beta_d;
-        if (h.flags & MER_META_GROWING_BETA) {
-            const double b = fmax(bf, (double)count_f / (double)(count_f + 1));
-            k.cF = (float)((1.0 - b) / (1.0 - growing_prod(bf, count_f)));
-        } else {
-            k.cF = (float)((1.0 - bf) / (1.0 - pow(bf, (double)(count_f + 1))));
-        }
-        k.stepD = (iteration >= 1 && n2 > 0.0) ? 1 : 0;
-        k.cD = k.stepD ? (float)((1.0 - bd) / (1.0 - pow(bd, (double)(count_d + 1)))) : 0.0f;
-        k.norm2 = (float)n2;
-        k.inv_norm = k.stepD ? (float)(1.0 / sqrt(n2)) : 0.0f;
-        const double t = (double)(iteration + 1);   // NAIVE_ADAM bias corrections
-        k.c1 = (float)(1.0 / (1.0 - pow((double)h.beta1, t)));
-        k.c2 = (float)(1.0 / (1.0 - pow((double)h.beta2, t)));
-    } else {
-        const double t = (double)(iteration + 1);
-        k.c1 = (float)(1.0 / (1.0 - pow((double)h.beta1, t)));
-        k.c2 = (float)(1.0 / (1.0 - pow((double)h.beta2, t)));
-        k.cF = k.cD = k.norm2 = k.inv_norm = 0.0f;
-        k.stepD = 0;
-    }
-    return k;
-}
+using Coef = UpdCoef;
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
@@ -328,9 +284,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_ctx(const UpdSeg* segs, 
         }
         s_seg = lo;
         const UpdSeg& S = segs[lo];
-        const ProbState st = ps[S.prob];
-        sk = make_coef(S, st.iteration, st.count_f, st.count_d, st.dpi_norm2);
-        s_cur = st.cur;
+        sk = ps[S.prob].coef;
+        s_cur = ps[S.prob].cur;
     }
     __syncthreads();
     const UpdSeg& S = segs[s_seg];
@@ -359,16 +314,13 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_finalize_ctx(const UpdSe
         st.iteration += 1;
         st.cur ^= 1;
         st.dpi_norm2 = tot;
+        st.coef = update_coef(S.hyper, st.iteration, st.count_f, st.count_d, tot);
     }
 }
 
 // standalone form: one segment passed by value, scalars from the caller
-__global__ void __launch_bounds__(UPD_THREADS) k_update_raw(UpdSeg S, int iteration, int count_f, int count_d,
-                                                            double n2, double* partials) {
-    __shared__ Coef sk;
-    if (threadIdx.x == 0) sk = make_coef(S, iteration, count_f, count_d, n2);
-    __syncthreads();
-    const float acc = update_block(S, sk, 0, blockIdx.x);
+__global__ void __launch_bounds__(UPD_THREADS) k_update_raw(UpdSeg S, Coef k, double* partials) {
+    const float acc = update_block(S, k, 0, blockIdx.x);
     const double tot = block_sum((double)acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
@@ -395,7 +347,8 @@ cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int c
     if (g_timer) g_timer->add_units(KC_UPDATE, S.n);
     if (nblocks > 0)
         MER_TIMED(KC_UPDATE, st,
-                  k_update_raw<<<(unsigned)nblocks, UPD_THREADS, 0, st>>>(S, iteration, count_f, count_d, n2, partials));
+                  k_update_raw<<<(unsigned)nblocks, UPD_THREADS, 0, st>>>(
+                      S, update_coef(S.hyper, iteration, count_f, count_d, n2), partials));
     MER_TIMED(KC_UPDATE_FIN, st, k_update_finalize_raw<<<1, UPD_THREADS, 0, st>>>(partials, nblocks, out));
     return cudaGetLastError();
 }

@@ -31,12 +31,53 @@ struct UpdSeg {
     mer_hyper hyper;
 };
 
+// prod_{j<=k} max(beta, j/(j+1)) in closed form: beta^min(k+1, K) * (k >= K ? K/(k+1) : 1),
+// K the first j with j/(j+1) > beta (MER_META_GROWING_BETA)
+__host__ __device__ inline double growing_prod(double beta, int k) {
+    long long K = (long long)floor(beta / (1.0 - beta));
+    if (K < 0) K = 0;
+    while (K > 0 && (double)(K - 1) / (double)K > beta) --K;
+    while ((double)K / (double)(K + 1) <= beta) ++K;
+    const long long reps = (long long)k + 1 < K ? (long long)k + 1 : K;
+    double p = pow(beta, (double)reps);
+    if ((long long)k >= K) p *= (double)K / (double)(k + 1);
+    return p;
+}
+
+// The update's scalars for iteration `iteration` with Moment2 counts count_f, count_d before the
+// step and ||dpi_i||^2 = n2 (double precision, once per problem; the per-element kernel reads them)
+__host__ __device__ inline UpdCoef update_coef(const mer_hyper& h, int iteration, int count_f, int count_d,
+                                               double n2) {
+    UpdCoef k;
+    k.pad = 0;
+    const double t = (double)(iteration + 1);
+    k.c1 = (float)(1.0 / (1.0 - pow((double)h.beta1, t)));    // Adam (and NAIVE_ADAM) bias corrections
+    k.c2 = (float)(1.0 / (1.0 - pow((double)h.beta2, t)));
+    if (h.mode == MER_MODE_META) {
+        const double bf = (double)h.beta_f, bd = (double)h.beta_d;
+        if (h.flags & MER_META_GROWING_BETA) {
+            const double b = fmax(bf, (double)count_f / (double)(count_f + 1));
+            k.cF = (float)((1.0 - b) / (1.0 - growing_prod(bf, count_f)));
+        } else {
+            k.cF = (float)((1.0 - bf) / (1.0 - pow(bf, (double)(count_f + 1))));
+        }
+        k.stepD = (iteration >= 1 && n2 > 0.0) ? 1 : 0;
+        k.cD = k.stepD ? (float)((1.0 - bd) / (1.0 - pow(bd, (double)(count_d + 1)))) : 0.0f;
+        k.norm2 = (float)n2;
+        k.inv_norm = k.stepD ? (float)(1.0 / sqrt(n2)) : 0.0f;
+    } else {
+        k.cF = k.cD = k.norm2 = k.inv_norm = 0.0f;
+        k.stepD = 0;
+    }
+    return k;
+}
+
 int64_t update_blocks_for(int64_t n);
 // records a context-free error message (thread-local) and returns code
 int mer_internal_fail(int code, const char* msg);
 cudaError_t launch_update_ctx(const UpdSeg* segs_dev, const int64_t* blk_off_dev, int n_segs, int64_t total_blocks,
                               ProbState* ps, double* partials, cudaStream_t st);
 cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int count_d, double n2, double* partials,
-                              int64_t nblocks, double* out, cudaStream_t st);
+                              int64_t nblocks, double* out, cudaStream_t st);   // coefficients computed on the host
 
 }  // namespace mer
