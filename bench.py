@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched comparison")
     ap.add_argument("--no-scale", action="store_true", help="skip the 1024^2 / 205k-triangle roofline leg")
     ap.add_argument("--only-scale", action="store_true", help="run only the scale leg (for profiling)")
+    ap.add_argument("--validate", action="store_true",
+                    help="add the statistical validation along prescribed trajectories (1000 runs, two schedules)")
     ap.add_argument("--scale-image", type=int, default=1024, help="image side of the scale leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
@@ -188,50 +190,78 @@ def eval_loss(torch, ctx, pid, target, spp=64):
     return float(((img - target) ** 2).mean())
 
 
+def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac):
+    """One optimisation run: iterations and GPU time (iterations only, evaluation excluded) until
+    the 64-spp eval loss drops below `frac` of its initial value; evaluated every 2 iterations for
+    the first 50, then every 10."""
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    sc = dict(w.scene)
+    sc["spp_prop"], sc["spp_fd"] = spp_prop, spp_fd
+    ctx = Context(0)
+    pid = ctx.add_scene(sc, HyperParams(mode=mode, lr=lr))
+    ctx.set_target(pid, target_img)
+    ctx.set_params(pid, w.init_tex)
+    l0 = eval_loss(torch, ctx, pid, target_img)
+    thr = frac * l0
+    gpu_ms, it, reached, reached_ms, last, lmin = 0.0, 0, None, None, l0, l0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    while it < max_iters:
+        k = 2 if it < 50 else 10
+        e0.record()
+        ctx.iterate(k, use_graph=True)
+        e1.record()
+        e1.synchronize()
+        gpu_ms += e0.elapsed_time(e1)
+        it += k
+        last = eval_loss(torch, ctx, pid, target_img)
+        lmin = min(lmin, last)
+        if reached is None and last <= thr:
+            reached, reached_ms = it, gpu_ms
+    ctx.close()
+    return {"lr": lr, "iters": reached, "gpu_s": reached_ms / 1e3 if reached else None, "loss0": l0,
+            "final_loss_ratio": last / l0, "min_loss_ratio": lmin / l0, "iters_run": it,
+            "gpu_s_total": gpu_ms / 1e3}
+
+
 def time_to_threshold(torch, w, target_img, max_iters, lrs=(0.001, 0.003, 0.01, 0.03), frac=0.05):
-    """Iterations and GPU time (iterations only, evaluation excluded) until the 64-spp eval loss
-    drops below `frac` of its initial value: meta-estimator (the workload's 1 FD + n proportional
-    spp) vs Adam on n+1 fresh proportional spp (equal spp per iteration), each at its best learning
-    rate of the grid. Evaluated every 2 iterations for the first 50, then every 10."""
-    from paper_2309_15676_gb300.api import Context, HyperParams, MODE_ADAM, MODE_META
+    """Meta-estimator (the workload's 1 FD + n proportional spp) vs Adam on n+1 fresh proportional
+    spp (equal spp per iteration), each at its best learning rate of the grid: iterations and GPU
+    time until the 64-spp eval loss drops below `frac` of its initial value."""
+    from paper_2309_15676_gb300.api import MODE_ADAM, MODE_META
     out = {}
     pp, pf = w.scene["spp_prop"], w.scene["spp_fd"]
     for name, mode, spp_prop, spp_fd in (("meta", MODE_META, pp, pf), ("adam", MODE_ADAM, pp + pf, 0)):
         best, runs = None, []
         for lr in lrs:
-            sc = dict(w.scene)
-            sc["spp_prop"], sc["spp_fd"] = spp_prop, spp_fd
-            ctx = Context(0)
-            pid = ctx.add_scene(sc, HyperParams(mode=mode, lr=lr))
-            ctx.set_target(pid, target_img)
-            ctx.set_params(pid, w.init_tex)
-            l0 = eval_loss(torch, ctx, pid, target_img)
-            thr = frac * l0
-            gpu_ms, it, reached, reached_ms, last, lmin = 0.0, 0, None, None, l0, l0
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            while it < max_iters:
-                k = 2 if it < 50 else 10
-                e0.record()
-                ctx.iterate(k, use_graph=True)
-                e1.record()
-                e1.synchronize()
-                gpu_ms += e0.elapsed_time(e1)
-                it += k
-                last = eval_loss(torch, ctx, pid, target_img)
-                lmin = min(lmin, last)
-                if reached is None and last <= thr:
-                    reached, reached_ms = it, gpu_ms
-            r = {"lr": lr, "iters": reached, "gpu_s": reached_ms / 1e3 if reached else None,
-                 "loss0": l0, "final_loss_ratio": last / l0, "min_loss_ratio": lmin / l0, "iters_run": it}
+            r = optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac)
             runs.append(r)
-            ctx.close()
-            key = (0 if reached else 1, r["gpu_s"] if reached else r["min_loss_ratio"])
+            key = (0 if r["iters"] else 1, r["gpu_s"] if r["iters"] else r["min_loss_ratio"])
             if best is None or key < best[0]:
                 best = (key, r)
         out[name] = dict(best[1], all_lrs=runs)
     out["threshold"] = f"{frac:.0%} of the iteration-0 64-spp eval loss"
     out["lr_grid"] = list(lrs)
     return out
+
+
+def spp_sweep(torch, iters=150, spps=(1, 2, 4, 8, 16, 32, 64), lr_meta=0.01, lr_adam=0.03, frac=0.05):
+    """The 512x512 / 32,768-triangle / 1024^2 x 5 spiral at depth 8: plain fresh-sample gradients
+    with Adam at s = 1..64 spp against the meta-estimator at its 1 FD + 2 proportional spp, each at
+    the learning rate tuned on the 256^2 spiral; iterations and GPU time to the threshold and the
+    loss after `iters` iterations."""
+    from paper_2309_15676_gb300 import synth
+    from paper_2309_15676_gb300.api import Context, HyperParams, MODE_ADAM, MODE_META
+    w = synth.workload_spiral(512, 512, 512, 32, 1024, max_depth=8)
+    ctx = Context(0)
+    pid = ctx.add_scene(w.scene, HyperParams())
+    target = ctx.render(pid, torch.from_numpy(w.target_tex).cuda(), spp=256, stream=4, iteration=0).clone()
+    ctx.close()
+    meta = optimise_run(torch, w, target, MODE_META, 2, 1, lr_meta, iters, frac)
+    adam = [dict(optimise_run(torch, w, target, MODE_ADAM, s_, 0, lr_adam, iters, frac), spp=s_) for s_ in spps]
+    return {"workload": "spiral512: 512^2, 32,768 triangles, 1024^2x5 textures, depth 8",
+            "meta": dict(meta, spp="1 FD + 2 proportional"), "adam_sweep": adam,
+            "lr": {"meta": lr_meta, "adam": lr_adam}, "threshold": f"{frac:.0%} of the iteration-0 64-spp eval loss",
+            "iterations": iters}
 
 
 def batched_compare(torch, n_problems=64, iters=3, seed=4):
@@ -547,6 +577,11 @@ def run_mine(args):
         tb = cb.render(pb, torch.from_numpy(wb.target_tex).cuda(), spp=256, stream=4, iteration=0).clone()
         cb.close()
         ttt["box64 (config 1: lr 0.01, 50 iterations)"] = time_to_threshold(torch, wb, tb, 50, lrs=(0.01,))
+        ttt["spiral512 spp sweep (config 3)"] = spp_sweep(torch)
+    validation = None
+    if rank == 0 and args.validate:
+        from paper_2309_15676_gb300.experiments import trajectory_study
+        validation = {kind: trajectory_study(runs=1000, iters=100, schedule=kind) for kind in ("linear", "exponential")}
     batched = batched_compare(torch) if (rank == 0 and not args.no_batch) else None
     scale = scale_profile(torch, hbm_peak, args.scale_image) if (rank == 0 and not args.no_scale) else None
     if rank == 0 and not args.no_cpu:
@@ -564,7 +599,7 @@ def run_mine(args):
                 "kernels": kernels, "peak_source": peak_kind,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                 "gpu_launches": int(launches_per_iter * args.steps), "launch_shapes": tuned,
-                "time_to_threshold": ttt, "batched": batched, "scale": scale}
+                "time_to_threshold": ttt, "batched": batched, "scale": scale, "validation": validation}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

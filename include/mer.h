@@ -180,6 +180,13 @@ mer_status mer_scene_add(mer_ctx* ctx, const mer_scene_desc* desc, int32_t* prob
 mer_status mer_params_set(mer_ctx* ctx, int32_t pid, const float* hwc, int32_t on_device);
 /* Copy the current parameters pi_i out (host pointer: synchronous; device: asynchronous). */
 mer_status mer_params_get(mer_ctx* ctx, int32_t pid, float* hwc_out, int32_t on_device);
+/* Replaces pi_{i+1}, the parameters the last update step produced, by the caller's values (HWC,
+ * host or device) and sets ||pi_{i+1} - pi_i||^2 and the next update's coefficients from them,
+ * so that the estimators run along a prescribed parameter trajectory instead of the optimiser's
+ * (the experiments of Sec. 6 "variance reduction without lag" and "approximation accuracy" move
+ * the parameters along a fixed schedule without an optimiser). The meta-estimator state, the
+ * Moment2 counts and the iteration are left as they are. Synchronous. */
+mer_status mer_params_force(mer_ctx* ctx, int32_t pid, const float* hwc, int32_t on_device);
 /* Set the target image ([height][width][3]). */
 mer_status mer_target_set(mer_ctx* ctx, int32_t pid, const float* img, int32_t on_device);
 /* Render the target image from the given parameters (device HWC texture) with spp samples

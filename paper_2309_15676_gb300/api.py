@@ -168,6 +168,12 @@ class Context:
         self._ck(self.L.mer_params_set(self.h, pid, _ptr(t), 1))
         torch.cuda.current_stream(self.device).synchronize()
 
+    def force_params(self, pid: int, tex):
+        """Replace the parameters the last update produced by `tex` (prescribed trajectory)."""
+        t = _dev_f32(tex, self.device)
+        torch.cuda.current_stream(self.device).synchronize()
+        self._ck(self.L.mer_params_force(self.h, pid, _ptr(t), 1))
+
     def get_params(self, pid: int) -> torch.Tensor:
         out = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
         self._ck(self.L.mer_params_get(self.h, pid, _ptr(out), 1))

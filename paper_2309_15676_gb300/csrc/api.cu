@@ -1021,6 +1021,18 @@ mer_status mer_params_get(mer_ctx* c, int32_t pid, float* out, int32_t on_device
     return MER_OK;
 }
 
+mer_status mer_params_force(mer_ctx* c, int32_t pid, const float* hwc, int32_t on_device) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !hwc) return fail(c, MER_ERR_INVALID_ARG, "bad problem id or input");
+    Guard g(c);
+    const int cur = read_cur(c, p);
+    mer_status s = copy_in(c, p->pslot[cur], hwc, p->n_par, on_device);
+    if (s) return s;
+    CK(c, launch_force_step(p->pslot[cur], p->pslot[cur ^ 1], p->n_par, c->d_pstate + p->id, p->hyper, c->st));
+    CK(c, cudaStreamSynchronize(c->st));
+    return MER_OK;
+}
+
 mer_status mer_target_set(mer_ctx* c, int32_t pid, const float* img, int32_t on_device) {
     Problem* p = get_prob(c, pid);
     if (!p) return fail(c, MER_ERR_INVALID_ARG, "bad problem id");

@@ -353,6 +353,27 @@ cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int c
     return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(UPD_THREADS) k_force_step(const float* __restrict__ pnew,
+                                                            const float* __restrict__ pold, int64_t n, ProbState* ps,
+                                                            mer_hyper h) {
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += UPD_THREADS) {
+        const double d = (double)pnew[i] - (double)pold[i];
+        v += d * d;
+    }
+    const double tot = block_sum(v);
+    if (threadIdx.x == 0) {
+        ps->dpi_norm2 = tot;
+        ps->coef = update_coef(h, ps->iteration, ps->count_f, ps->count_d, tot);
+    }
+}
+
+cudaError_t launch_force_step(const float* pnew, const float* pold, int64_t n, ProbState* ps, const mer_hyper& h,
+                              cudaStream_t st) {
+    k_force_step<<<1, UPD_THREADS, 0, st>>>(pnew, pold, n, ps, h);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------
 // Allocation-free form of the standalone update. Its only scratch is the per-block partial
 // sums of ||pi' - pi||^2; here they live in a fixed file-scope device array instead of a

@@ -77,6 +77,10 @@ int64_t update_blocks_for(int64_t n);
 int mer_internal_fail(int code, const char* msg);
 cudaError_t launch_update_ctx(const UpdSeg* segs_dev, const int64_t* blk_off_dev, int n_segs, int64_t total_blocks,
                               ProbState* ps, double* partials, cudaStream_t st);
+// ||pnew - pold||^2 over n parameters (one block, fixed order) into ps->dpi_norm2, and the next
+// update's coefficients for it
+cudaError_t launch_force_step(const float* pnew, const float* pold, int64_t n, ProbState* ps, const mer_hyper& h,
+                              cudaStream_t st);
 cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int count_d, double n2, double* partials,
                               int64_t nblocks, double* out, cudaStream_t st);   // coefficients computed on the host
 
