@@ -495,7 +495,11 @@ static void splat(const orc_scene* s, const mat_t* m, const double g[5], double*
 }
 
 /* ------------------------------------------------------------------------- */
-/* one path. mode 0: radiance only. mode 1: PRB replay — needs the path's       */
+/* one path. Directions, lobe choices, pdfs and MIS weights come from the        */
+/* parameters tex_s, the integrand (f and its derivative) from tex_e; tex_s =     */
+/* tex_e is the ordinary estimator, tex_s = pi_i with tex_e = pi_{i-1} the FD     */
+/* branch that shares the pi_i path and divides by its density (Eq. est_triv).    */
+/* mode 0: radiance only. mode 1: PRB replay — needs the path's                   */
 /* radiance Ltot from a mode-0 call with the same counters, the adjoint weight  */
 /* adj[c] = dLoss/dL_c of this sample, and accumulates into grad.               */
 /*                                                                               */
@@ -503,8 +507,8 @@ static void splat(const orc_scene* s, const mat_t* m, const double g[5], double*
 /* At vertex k: emission seen (MIS-weighted unless k = 1); if k < D, one NEE     */
 /* sample and one BSDF sample. D = 1 shows emitters only, D = 2 direct light.    */
 /* ------------------------------------------------------------------------- */
-static void trace(const orc_scene* s, const double* tex, uint32_t pixel, uint32_t sample, uint32_t iter,
-                  uint32_t stream, int mode, const double Ltot[3], const double adj[3], double* grad,
+static void trace(const orc_scene* s, const double* tex_s, const double* tex_e, uint32_t pixel, uint32_t sample,
+                  uint32_t iter, uint32_t stream, int mode, const double Ltot[3], const double adj[3], double* grad,
                   double Lout[3])
 {
     rng_ctx R = { { s->seed, s->key_id }, pixel, sample, iter, stream };
@@ -534,8 +538,9 @@ static void trace(const orc_scene* s, const double* tex, uint32_t pixel, uint32_
         v3 wo = vmul(d, -1.0);
         v3 nf = vdot(si.n, d) < 0.0 ? si.n : vmul(si.n, -1.0);
         v3 po = offset_point(si.p, nf);
-        mat_t m;
-        load_material(s, tex, &si, &m);
+        mat_t m, ms;   /* m: integrand (tex_e); ms: sampling and densities (tex_s) */
+        load_material(s, tex_e, &si, &m);
+        load_material(s, tex_s, &si, &ms);
         int want_grad = (mode == 1) && m.textured;
         double g[5] = { 0, 0, 0, 0, 0 };
 
@@ -546,7 +551,7 @@ static void trace(const orc_scene* s, const double* tex, uint32_t pixel, uint32_
         if (nee.ok) {
             double f[3], df[5][3];
             bsdf_eval(&m, nf, wo, nee.wi, f, want_grad ? df : NULL);
-            double pb = bsdf_pdf(&m, nf, wo, nee.wi);
+            double pb = bsdf_pdf(&ms, nf, wo, nee.wi);
             double cs = vdot(nee.wi, nf);
             double wl = mis2(nee.pdf, pb);
             double q = cs * wl / nee.pdf;
@@ -562,11 +567,11 @@ static void trace(const orc_scene* s, const double* tex, uint32_t pixel, uint32_
         /* BSDF sample for the continuation */
         draw4(&R, (uint32_t)k, 1, u, raw);
         v3 wi;
-        int ok = bsdf_sample(&m, nf, wo, u[0], u[1], u[2], &wi);
+        int ok = bsdf_sample(&ms, nf, wo, u[0], u[1], u[2], &wi);
         double f[3] = { 0, 0, 0 }, df[5][3], pb = 0.0;
         if (ok) {
             bsdf_eval(&m, nf, wo, wi, f, want_grad ? df : NULL);
-            pb = bsdf_pdf(&m, nf, wo, wi);
+            pb = bsdf_pdf(&ms, nf, wo, wi);
             if (pb <= 0.0) ok = 0;
         }
         if (want_grad) {
@@ -712,7 +717,7 @@ void orc_render_samples(const orc_scene* s, const double* tex, int64_t n, const 
                         const uint32_t* samples, uint32_t iter, uint32_t stream, double* out)
 {
     for (int64_t i = 0; i < n; ++i)
-        trace(s, tex, pixels[i], samples[i], iter, stream, 0, NULL, NULL, NULL, out + 3 * i);
+        trace(s, tex, tex, pixels[i], samples[i], iter, stream, 0, NULL, NULL, NULL, out + 3 * i);
 }
 
 /* mean over spp samples per pixel; image [H*W*3], sample index s = 0..spp-1 */
@@ -723,7 +728,7 @@ void orc_render_image(const orc_scene* s, const double* tex, int spp, uint32_t i
         double acc[3] = { 0, 0, 0 };
         for (int k = 0; k < spp; ++k) {
             double L[3];
-            trace(s, tex, (uint32_t)p, (uint32_t)k, iter, stream, 0, NULL, NULL, NULL, L);
+            trace(s, tex, tex, (uint32_t)p, (uint32_t)k, iter, stream, 0, NULL, NULL, NULL, L);
             for (int c = 0; c < 3; ++c) acc[c] += L[c];
         }
         for (int c = 0; c < 3; ++c) img[3 * p + c] = acc[c] / spp;
@@ -741,8 +746,39 @@ void orc_adjoint_image(const orc_scene* s, const double* tex, int spp, uint32_t 
         for (int k = 0; k < spp; ++k) {
             double adj[3] = { dimg[3 * p] / spp, dimg[3 * p + 1] / spp, dimg[3 * p + 2] / spp };
             double Lt[3], Lr[3];
-            trace(s, tex, (uint32_t)p, (uint32_t)k, iter, stream, 0, NULL, NULL, NULL, Lt);
-            trace(s, tex, (uint32_t)p, (uint32_t)k, iter, stream, 1, Lt, adj, grad, Lr);
+            trace(s, tex, tex, (uint32_t)p, (uint32_t)k, iter, stream, 0, NULL, NULL, NULL, Lt);
+            trace(s, tex, tex, (uint32_t)p, (uint32_t)k, iter, stream, 1, Lt, adj, grad, Lr);
+        }
+    }
+}
+
+/* The FD branch that shares the pi_i path (Eq. est_triv): image and PRB gradient of the
+ * integrand at tex_e along paths sampled, with their densities and MIS weights, at tex_s. */
+void orc_render_image_shared(const orc_scene* s, const double* tex_s, const double* tex_e, int spp, uint32_t iter,
+                             uint32_t stream, double* img)
+{
+    int64_t N = (int64_t)s->width * s->height;
+    for (int64_t p = 0; p < N; ++p) {
+        double acc[3] = { 0, 0, 0 };
+        for (int k = 0; k < spp; ++k) {
+            double L[3];
+            trace(s, tex_s, tex_e, (uint32_t)p, (uint32_t)k, iter, stream, 0, NULL, NULL, NULL, L);
+            for (int c = 0; c < 3; ++c) acc[c] += L[c];
+        }
+        for (int c = 0; c < 3; ++c) img[3 * p + c] = acc[c] / spp;
+    }
+}
+
+void orc_adjoint_image_shared(const orc_scene* s, const double* tex_s, const double* tex_e, int spp, uint32_t iter,
+                              uint32_t stream, const double* dimg, double* grad)
+{
+    int64_t N = (int64_t)s->width * s->height;
+    for (int64_t p = 0; p < N; ++p) {
+        for (int k = 0; k < spp; ++k) {
+            double adj[3] = { dimg[3 * p] / spp, dimg[3 * p + 1] / spp, dimg[3 * p + 2] / spp };
+            double Lt[3], Lr[3];
+            trace(s, tex_s, tex_e, (uint32_t)p, (uint32_t)k, iter, stream, 0, NULL, NULL, NULL, Lt);
+            trace(s, tex_s, tex_e, (uint32_t)p, (uint32_t)k, iter, stream, 1, Lt, adj, grad, Lr);
         }
     }
 }
@@ -772,8 +808,8 @@ void orc_adjoint_samples(const orc_scene* s, const double* tex, int64_t n, const
         if (stored) {
             trace_stored(s, tex, pixels[i], samples[i], iter, stream, adj + 3 * i, grad, Lr);
         } else {
-            trace(s, tex, pixels[i], samples[i], iter, stream, 0, NULL, NULL, NULL, Lt);
-            trace(s, tex, pixels[i], samples[i], iter, stream, 1, Lt, adj + 3 * i, grad, Lr);
+            trace(s, tex, tex, pixels[i], samples[i], iter, stream, 0, NULL, NULL, NULL, Lt);
+            trace(s, tex, tex, pixels[i], samples[i], iter, stream, 1, Lt, adj + 3 * i, grad, Lr);
         }
     }
 }

@@ -52,6 +52,10 @@ def lib():
         L.orc_render_samples.argtypes = [ct.POINTER(OrcScene), _f64p, ct.c_int64, _u32p, _u32p,
                                          ct.c_uint32, ct.c_uint32, _f64p]
         L.orc_render_image.argtypes = [ct.POINTER(OrcScene), _f64p, ct.c_int, ct.c_uint32, ct.c_uint32, _f64p]
+        L.orc_render_image_shared.argtypes = [ct.POINTER(OrcScene), _f64p, _f64p, ct.c_int, ct.c_uint32,
+                                              ct.c_uint32, _f64p]
+        L.orc_adjoint_image_shared.argtypes = [ct.POINTER(OrcScene), _f64p, _f64p, ct.c_int, ct.c_uint32,
+                                               ct.c_uint32, _f64p, _f64p]
         for name in ("orc_adjoint_image", "orc_adjoint_image_stored"):
             getattr(L, name).argtypes = [ct.POINTER(OrcScene), _f64p, ct.c_int, ct.c_uint32, ct.c_uint32,
                                          _f64p, _f64p]
@@ -176,6 +180,24 @@ def adjoint_image(sc: Scene, tex, spp, iteration, stream, dimg, stored=False):
     return grad
 
 
+def render_image_shared(sc: Scene, tex_s, tex_e, spp, iteration, stream):
+    """Image of the integrand at tex_e along paths sampled (directions, densities, MIS) at tex_s."""
+    out = np.zeros((sc.st.height, sc.st.width, 3), np.float64)
+    ts, te = _tex(tex_s), _tex(tex_e)
+    lib().orc_render_image_shared(sc.ref(), _p(ts, _f64p), _p(te, _f64p), spp, iteration, stream, _p(out, _f64p))
+    return out
+
+
+def adjoint_image_shared(sc: Scene, tex_s, tex_e, spp, iteration, stream, dimg):
+    """PRB gradient (w.r.t. tex_e) of sum(dimg * I) for the paths sampled at tex_s."""
+    grad = np.zeros(sc.tex_shape, np.float64)
+    ts, te = _tex(tex_s), _tex(tex_e)
+    d = np.ascontiguousarray(dimg, np.float64)
+    lib().orc_adjoint_image_shared(sc.ref(), _p(ts, _f64p), _p(te, _f64p), spp, iteration, stream, _p(d, _f64p),
+                                   _p(grad, _f64p))
+    return grad
+
+
 def adjoint_samples(sc: Scene, tex, pixels, samples, iteration, stream, adj, stored=False):
     pixels = np.ascontiguousarray(pixels, np.uint32)
     samples = np.ascontiguousarray(samples, np.uint32)
@@ -245,14 +267,23 @@ def prop_gradient(sc: Scene, tex, target, spp, iteration, stream_offset=0, loss_
     return g, loss, img
 
 
-def fd_gradient(sc: Scene, tex_cur, tex_prev, target, spp, iteration, stream_offset=0, loss_kind=0):
+def fd_gradient(sc: Scene, tex_cur, tex_prev, target, spp, iteration, stream_offset=0, loss_kind=0,
+                shared=False):
     """<dF_i> = <F_i>(u) - <F_{i-1}>(u): both terms use the same counters (streams FD_PRIMAL
     for the adjoint weights and FD_ADJ for the adjoint) at pi_i and pi_{i-1}; stream_offset
-    shifts both streams as in prop_gradient."""
+    shifts both streams as in prop_gradient. shared: the pi_{i-1} term follows the pi_i paths
+    and divides by their density (Eq. est_triv read literally) instead of replaying the same
+    random numbers with its own sampling."""
     img_c = render_image(sc, tex_cur, spp, iteration, ST_FD_PRIMAL + stream_offset)
-    img_p = render_image(sc, tex_prev, spp, iteration, ST_FD_PRIMAL + stream_offset)
+    if shared:
+        img_p = render_image_shared(sc, tex_cur, tex_prev, spp, iteration, ST_FD_PRIMAL + stream_offset)
+    else:
+        img_p = render_image(sc, tex_prev, spp, iteration, ST_FD_PRIMAL + stream_offset)
     _, d_c = image_loss(img_c, target, loss_kind)
     _, d_p = image_loss(img_p, target, loss_kind)
     g_c = adjoint_image(sc, tex_cur, spp, iteration, ST_FD_ADJ + stream_offset, d_c)
-    g_p = adjoint_image(sc, tex_prev, spp, iteration, ST_FD_ADJ + stream_offset, d_p)
+    if shared:
+        g_p = adjoint_image_shared(sc, tex_cur, tex_prev, spp, iteration, ST_FD_ADJ + stream_offset, d_p)
+    else:
+        g_p = adjoint_image(sc, tex_prev, spp, iteration, ST_FD_ADJ + stream_offset, d_p)
     return g_c - g_p

@@ -118,3 +118,45 @@ def test_fd_estimator_unbiased(oracle_lib):
     se = np.sqrt(d.var(0) / n + g1.var(0) / n + g0.var(0) / n) + 1e-12
     z = np.abs(diff) / se
     assert np.mean(z < 5) > 0.99 and np.var(d, 0).mean() < (np.var(g1, 0) + np.var(g0, 0)).mean()
+
+
+def test_shared_path_branch_reduces_to_the_ordinary_estimator(oracle_lib):
+    """Sampling and evaluating with the same parameters is the ordinary estimator (bit for bit)."""
+    w = synth.workload_spiral(6, 5, 32, 8, 8, max_depth=4)
+    sc = orc.Scene(w.scene)
+    tex = w.init_tex.astype(np.float64)
+    dimg = np.random.default_rng(7).normal(size=(5, 6, 3))
+    assert np.array_equal(orc.render_image_shared(sc, tex, tex, 2, 3, orc.ST_FD_PRIMAL),
+                          orc.render_image(sc, tex, 2, 3, orc.ST_FD_PRIMAL))
+    assert np.array_equal(orc.adjoint_image_shared(sc, tex, tex, 2, 3, orc.ST_FD_ADJ, dimg),
+                          orc.adjoint_image(sc, tex, 2, 3, orc.ST_FD_ADJ, dimg))
+
+
+def test_shared_path_equals_replay_on_lambertian_box(oracle_lib):
+    """On the Lambertian box the sampling and every density are independent of the albedo, so the
+    pi_{i-1} branch that shares the pi_i path is exactly the branch that replays the numbers."""
+    w = synth.workload_box(8, 8, 8, max_depth=3)
+    sc = orc.Scene(w.scene)
+    a = w.init_tex.astype(np.float64)
+    b = np.clip(a + np.random.default_rng(8).normal(0, 0.05, a.shape), 0.05, 0.95)
+    dimg = np.random.default_rng(9).normal(size=(8, 8, 3))
+    assert np.allclose(orc.render_image_shared(sc, a, b, 2, 1, orc.ST_FD_PRIMAL),
+                       orc.render_image(sc, b, 2, 1, orc.ST_FD_PRIMAL), rtol=1e-13, atol=1e-15)
+    assert np.allclose(orc.adjoint_image_shared(sc, a, b, 2, 1, orc.ST_FD_ADJ, dimg),
+                       orc.adjoint_image(sc, b, 2, 1, orc.ST_FD_ADJ, dimg), rtol=1e-12, atol=1e-15)
+
+
+def test_shared_path_branch_unbiased_on_glossy_scene(oracle_lib):
+    """On the principled spiral the shared-path image of pi_{i-1} (paths and densities of pi_i)
+    has the same expectation as the ordinary image of pi_{i-1}: means over seeds within 5 sigma."""
+    w = synth.workload_spiral(4, 4, 32, 8, 4, max_depth=3)
+    sc = orc.Scene(w.scene)
+    a = w.init_tex.astype(np.float64)
+    b = w.target_tex.astype(np.float64)
+    n = 200
+    x = np.array([orc.render_image_shared(sc, a, b, 1, s, orc.ST_EVAL) for s in range(n)])
+    y = np.array([orc.render_image(sc, b, 1, s + 10_000, orc.ST_EVAL) for s in range(n)])
+    se = np.sqrt(x.var(0) / n + y.var(0) / n) + 1e-12
+    z = (x.mean(0) - y.mean(0)) / se
+    assert np.all(np.abs(z) < 5), np.abs(z).max()
+    assert np.mean(z * z) < 3
