@@ -190,7 +190,7 @@ def eval_loss(torch, ctx, pid, target, spp=64):
     return float(((img - target) ** 2).mean())
 
 
-def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac):
+def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags=0):
     """One optimisation run: iterations and GPU time (iterations only, evaluation excluded) until
     the 64-spp eval loss drops below `frac` of its initial value; evaluated every 2 iterations for
     the first 50, then every 10."""
@@ -198,7 +198,7 @@ def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, fr
     sc = dict(w.scene)
     sc["spp_prop"], sc["spp_fd"] = spp_prop, spp_fd
     ctx = Context(0)
-    pid = ctx.add_scene(sc, HyperParams(mode=mode, lr=lr))
+    pid = ctx.add_scene(sc, HyperParams(mode=mode, lr=lr, flags=flags))
     ctx.set_target(pid, target_img)
     ctx.set_params(pid, w.init_tex)
     l0 = eval_loss(torch, ctx, pid, target_img)
@@ -224,16 +224,19 @@ def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, fr
 
 
 def time_to_threshold(torch, w, target_img, max_iters, lrs=(0.001, 0.003, 0.01, 0.03), frac=0.05):
-    """Meta-estimator (the workload's 1 FD + n proportional spp) vs Adam on n+1 fresh proportional
-    spp (equal spp per iteration), each at its best learning rate of the grid: iterations and GPU
+    """Meta-estimator (the workload's 1 FD + n proportional spp; FD pairs by random-number replay,
+    and with the pi_{i-1} branch sharing the pi_i path) vs Adam on n+1 fresh proportional spp
+    (equal spp per iteration), each at its best learning rate of the grid: iterations and GPU
     time until the 64-spp eval loss drops below `frac` of its initial value."""
-    from paper_2309_15676_gb300.api import MODE_ADAM, MODE_META
+    from paper_2309_15676_gb300.api import META_FD_SHARED_PATH, MODE_ADAM, MODE_META
     out = {}
     pp, pf = w.scene["spp_prop"], w.scene["spp_fd"]
-    for name, mode, spp_prop, spp_fd in (("meta", MODE_META, pp, pf), ("adam", MODE_ADAM, pp + pf, 0)):
+    for name, mode, spp_prop, spp_fd, flags in (("meta", MODE_META, pp, pf, 0),
+                                                ("meta_shared_path", MODE_META, pp, pf, META_FD_SHARED_PATH),
+                                                ("adam", MODE_ADAM, pp + pf, 0, 0)):
         best, runs = None, []
         for lr in lrs:
-            r = optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac)
+            r = optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags)
             runs.append(r)
             key = (0 if r["iters"] else 1, r["gpu_s"] if r["iters"] else r["min_loss_ratio"])
             if best is None or key < best[0]:
@@ -250,16 +253,18 @@ def spp_sweep(torch, iters=150, spps=(1, 2, 4, 8, 16, 32, 64), lr_meta=0.01, lr_
     the learning rate tuned on the 256^2 spiral; iterations and GPU time to the threshold and the
     loss after `iters` iterations."""
     from paper_2309_15676_gb300 import synth
-    from paper_2309_15676_gb300.api import Context, HyperParams, MODE_ADAM, MODE_META
+    from paper_2309_15676_gb300.api import Context, HyperParams, META_FD_SHARED_PATH, MODE_ADAM, MODE_META
     w = synth.workload_spiral(512, 512, 512, 32, 1024, max_depth=8)
     ctx = Context(0)
     pid = ctx.add_scene(w.scene, HyperParams())
     target = ctx.render(pid, torch.from_numpy(w.target_tex).cuda(), spp=256, stream=4, iteration=0).clone()
     ctx.close()
     meta = optimise_run(torch, w, target, MODE_META, 2, 1, lr_meta, iters, frac)
+    meta_shared = optimise_run(torch, w, target, MODE_META, 2, 1, lr_meta, iters, frac, META_FD_SHARED_PATH)
     adam = [dict(optimise_run(torch, w, target, MODE_ADAM, s_, 0, lr_adam, iters, frac), spp=s_) for s_ in spps]
     return {"workload": "spiral512: 512^2, 32,768 triangles, 1024^2x5 textures, depth 8",
-            "meta": dict(meta, spp="1 FD + 2 proportional"), "adam_sweep": adam,
+            "meta": dict(meta, spp="1 FD + 2 proportional"),
+            "meta_shared_path": dict(meta_shared, spp="1 FD (shared path) + 2 proportional"), "adam_sweep": adam,
             "lr": {"meta": lr_meta, "adam": lr_adam}, "threshold": f"{frac:.0%} of the iteration-0 64-spp eval loss",
             "iterations": iters}
 

@@ -87,13 +87,19 @@ typedef int mer_status;
  *  NAIVE_ADAM    <F_i>_M fed to Adam's moments (beta1, beta2, bias-corrected) instead of the
  *                update rule of Sec. 5 (the naive coupling Sec. 5 argues against)
  *  UNCORRELATED  Var[<F>] and Var[<dF>]_D stepped with independent samples F_var, dF_var of
- *                the same estimators (ablation "sample reuse", Sec. 6); <F_i>_M still uses F, dF */
+ *                the same estimators (ablation "sample reuse", Sec. 6); <F_i>_M still uses F, dF
+ *  FD_SHARED_PATH  the FD sample of Eq. est_triv read literally: the pi_{i-1} branch follows the
+ *                path sampled at pi_i (directions, lobe choices, light samples) and divides its
+ *                integrand by that path's density and MIS weights, instead of replaying the same
+ *                random numbers with its own sampling; identical to the replay wherever sampling
+ *                does not depend on the parameters (e.g. Lambertian albedo) */
 #define MER_META_PER_ELEMENT 1
 #define MER_META_NO_CLIP 2
 #define MER_META_CENTRED 4
 #define MER_META_GROWING_BETA 8
 #define MER_META_NAIVE_ADAM 16
 #define MER_META_UNCORRELATED 32
+#define MER_META_FD_SHARED_PATH 64
 
 typedef struct mer_hyper {
     int32_t mode;      /* MER_MODE_META or MER_MODE_ADAM */

@@ -51,6 +51,7 @@ META_CENTRED = 4
 META_GROWING_BETA = 8
 META_NAIVE_ADAM = 16
 META_UNCORRELATED = 32
+META_FD_SHARED_PATH = 64
 
 
 def _ptr(t):

@@ -709,7 +709,7 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
         mer_hyper_default(&p->hyper);
         p->hyper.flags = fl;
     }
-    if (p->hyper.flags & ~63) {
+    if (p->hyper.flags & ~127) {
         delete p;
         return fail(c, MER_ERR_INVALID_ARG, "unknown MER_META_* flag bits");
     }
@@ -911,6 +911,7 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     D.seed = d->seed;
     D.key_id = d->key_id;
     D.loss_kind = d->loss;
+    D.fd_shared = (p->meta && (p->hyper.flags & MER_META_FD_SHARED_PATH)) ? 1 : 0;
     // ---- optimiser state and images ----
     const size_t np = (size_t)p->n_par, npx = (size_t)p->n_pix * 3;
     AK(alloc(&p->pslot[0], np));

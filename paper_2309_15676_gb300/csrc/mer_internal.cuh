@@ -141,6 +141,7 @@ struct ProblemDev {
     float* F;
     float* dF;
     int32_t loss_kind;         // MER_LOSS_*
+    int32_t fd_shared;         // FD pairs: the pi_{i-1} branch follows the pi_i path (MER_META_FD_SHARED_PATH)
     float* Fv;                 // MER_META_UNCORRELATED: independent samples of F and dF (else NULL)
     float* dFv;
     // per-pixel arrays [n_pix][3]

@@ -445,8 +445,15 @@ __device__ __forceinline__ void extend_item(const PassArgs& A, const Node* s_nod
 // ---------------------------------------------------------------------------------
 // shade
 // ---------------------------------------------------------------------------------
+// blocks per SM the register budget keeps: the FD-pair replay is the heaviest, the proportional
+// radiance pass the lightest
 template <int NB, int MODE>
-__global__ void __launch_bounds__(256) k_shade(PassArgs A, int depth) {
+constexpr int shade_min_blocks() {
+    return (NB == 2 && MODE == MODE_REPLAY) ? 1 : (NB == 1 && MODE != MODE_REPLAY) ? 3 : 2;
+}
+
+template <int NB, int MODE>
+__global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(PassArgs A, int depth) {
     constexpr bool GRAD = MODE == MODE_REPLAY;
     const bool first = depth == 1;
     const int64_t n = first ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth], A.qcap);
@@ -563,6 +570,12 @@ __global__ void __launch_bounds__(256) k_shade(PassArgs A, int depth) {
             sh_want[b] = cont[b] = rec_want[b] = textured[b] = false;
             ls[b].ok = false;
         }
+        // FD pair with a shared path: branch 1 (pi_{i-1}) takes branch 0's light sample, BSDF sample
+        // and densities, and evaluates only its own integrand along them
+        const bool shared = NB == 2 && P.fd_shared != 0;
+        float pbN0 = 0.0f, pbC0 = 0.0f;
+        v3 wiC0 = mk(0, 0, 0);
+        bool okC0 = false;
         if (any_alive) {
             const uint4 r0 = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, (uint32_t)depth, 0);
             const uint4 r1 = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, (uint32_t)depth, 1);
@@ -599,7 +612,8 @@ __global__ void __launch_bounds__(256) k_shade(PassArgs A, int depth) {
                 if (ls[b].ok) {
                     float df[MAXC][3];
                     const v3 f = wg ? bsdf_f_grad(m, nf, wo, ls[b].wi, df) : bsdf_f(m, nf, wo, ls[b].wi);
-                    const float pb = bsdf_pdf(m, nf, wo, ls[b].wi);
+                    const float pb = (shared && b == 1) ? pbN0 : bsdf_pdf(m, nf, wo, ls[b].wi);
+                    if (b == 0) pbN0 = pb;
                     const float qn = dot(ls[b].wi, nf) * mis2(ls[b].pdf, pb) / ls[b].pdf;
                     contrib[b] = mk(beta[b].x * f.x * ls[b].le.x, beta[b].y * f.y * ls[b].le.y,
                                     beta[b].z * f.z * ls[b].le.z) * qn;
@@ -613,14 +627,27 @@ __global__ void __launch_bounds__(256) k_shade(PassArgs A, int depth) {
                 }
                 // BSDF sample for the continuation
                 v3 wi;
-                bool ok = bsdf_sample(m, nf, wo, u01(r1.x), u01(r1.y), u01(r1.z), wi);
+                bool ok;
                 float df[MAXC][3];
                 v3 f = mk(0, 0, 0);
                 float pb = 0.0f;
-                if (ok) {
-                    f = wg ? bsdf_f_grad(m, nf, wo, wi, df) : bsdf_f(m, nf, wo, wi);
-                    pb = bsdf_pdf(m, nf, wo, wi);
-                    ok = pb > 0.0f;
+                if (shared && b == 1) {
+                    wi = wiC0;
+                    ok = okC0;
+                    pb = pbC0;
+                    if (ok) f = wg ? bsdf_f_grad(m, nf, wo, wi, df) : bsdf_f(m, nf, wo, wi);
+                } else {
+                    ok = bsdf_sample(m, nf, wo, u01(r1.x), u01(r1.y), u01(r1.z), wi);
+                    if (ok) {
+                        f = wg ? bsdf_f_grad(m, nf, wo, wi, df) : bsdf_f(m, nf, wo, wi);
+                        pb = bsdf_pdf(m, nf, wo, wi);
+                        ok = pb > 0.0f;
+                    }
+                    if (b == 0) {
+                        okC0 = ok;
+                        wiC0 = wi;
+                        pbC0 = pb;
+                    }
                 }
                 if (wg) {
                     rec_want[b] = true;
