@@ -30,18 +30,43 @@ constexpr unsigned FULL = 0xffffffffu;
 // ---------------------------------------------------------------------------------
 // traversal
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ Node load_node(const Node* __restrict__ nodes, const Node* s_nodes, int smem_n, int i) {
-    if (i < smem_n) return s_nodes[i];
-    const float4* p = reinterpret_cast<const float4*>(nodes + i);
-    Node n;
-    n.lx = __ldg(p);
-    n.hx = __ldg(p + 1);
-    n.ly = __ldg(p + 2);
-    n.hy = __ldg(p + 3);
-    n.lz = __ldg(p + 4);
-    n.hz = __ldg(p + 5);
-    n.child = __ldg(reinterpret_cast<const int4*>(p + 6));
+// near and far slab planes of a node's four children along the ray: with the ray's direction
+// signs fixed, the near plane of an axis is the low one for a positive component and the high one
+// for a negative one, so the planes are fetched in ray order and need no per-box min/max
+struct NodeRay {
+    float4 nx, fx, ny, fy, nz, fz;
+    int4 child;
+};
+
+__device__ __forceinline__ NodeRay load_node(const Node* __restrict__ nodes, const Node* s_nodes, int smem_n, int i,
+                                             int sx, int sy, int sz) {
+    const float4* p = (i < smem_n) ? reinterpret_cast<const float4*>(s_nodes + i)
+                                   : reinterpret_cast<const float4*>(nodes + i);
+    NodeRay n;
+    if (i < smem_n) {
+        n.nx = p[0 + sx]; n.fx = p[1 - sx];
+        n.ny = p[2 + sy]; n.fy = p[3 - sy];
+        n.nz = p[4 + sz]; n.fz = p[5 - sz];
+        n.child = reinterpret_cast<const int4*>(p)[6];
+    } else {
+        n.nx = __ldg(p + 0 + sx); n.fx = __ldg(p + 1 - sx);
+        n.ny = __ldg(p + 2 + sy); n.fy = __ldg(p + 3 - sy);
+        n.nz = __ldg(p + 4 + sz); n.fz = __ldg(p + 5 - sz);
+        n.child = __ldg(reinterpret_cast<const int4*>(p) + 6);
+    }
     return n;
+}
+
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 __device__ __forceinline__ bool tri_test(const TriGeo& T, v3 o, v3 d, float& t, float& u, float& v) {
@@ -114,30 +139,28 @@ __device__ __forceinline__ bool traverse(const ProblemDev& P, const Node* s_node
         const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
         const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
         const float ox = o.x * ix, oy = o.y * iy, oz = o.z * iz;
+        const int sx = ix < 0.0f ? 1 : 0, sy = iy < 0.0f ? 1 : 0, sz = iz < 0.0f ? 1 : 0;
         int stack[64];
         int sp = 0;
         int node = 0;
         const float grow = 1.0f + 4.8e-7f;   // conservative box exit (a few ulp)
         while (true) {
             while (node >= 0) {
-                const Node n = load_node(P.nodes, s_nodes, smem_n, node);
+                const NodeRay n = load_node(P.nodes, s_nodes, smem_n, node, sx, sy, sz);
                 if (STATS) tc.nodes++;
                 const float tfar = h.t * grow;
                 // slab test of the four children; a miss (or an unused slot) sorts last
                 float tn[4];
                 int rf[4];
-                const float lxs[4] = {n.lx.x, n.lx.y, n.lx.z, n.lx.w}, hxs[4] = {n.hx.x, n.hx.y, n.hx.z, n.hx.w};
-                const float lys[4] = {n.ly.x, n.ly.y, n.ly.z, n.ly.w}, hys[4] = {n.hy.x, n.hy.y, n.hy.z, n.hy.w};
-                const float lzs[4] = {n.lz.x, n.lz.y, n.lz.z, n.lz.w}, hzs[4] = {n.hz.x, n.hz.y, n.hz.z, n.hz.w};
+                const float nxs[4] = {n.nx.x, n.nx.y, n.nx.z, n.nx.w}, fxs[4] = {n.fx.x, n.fx.y, n.fx.z, n.fx.w};
+                const float nys[4] = {n.ny.x, n.ny.y, n.ny.z, n.ny.w}, fys[4] = {n.fy.x, n.fy.y, n.fy.z, n.fy.w};
+                const float nzs[4] = {n.nz.x, n.nz.y, n.nz.z, n.nz.w}, fzs[4] = {n.fz.x, n.fz.y, n.fz.z, n.fz.w};
                 const int cs[4] = {n.child.x, n.child.y, n.child.z, n.child.w};
                 int nh = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float x0 = fmaf(lxs[k], ix, -ox), x1 = fmaf(hxs[k], ix, -ox);
-                    const float y0 = fmaf(lys[k], iy, -oy), y1 = fmaf(hys[k], iy, -oy);
-                    const float z0 = fmaf(lzs[k], iz, -oz), z1 = fmaf(hzs[k], iz, -oz);
-                    const float t0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
-                    const float t1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tfar));
+                    const float t0 = fmax3(fmaf(nxs[k], ix, -ox), fmaf(nys[k], iy, -oy), fmaxf(fmaf(nzs[k], iz, -oz), 0.0f));
+                    const float t1 = fmin3(fmaf(fxs[k], ix, -ox), fmaf(fys[k], iy, -oy), fminf(fmaf(fzs[k], iz, -oz), tfar));
                     const bool hit = t0 <= t1 && cs[k] != NODE_EMPTY;
                     tn[k] = hit ? t0 : INFINITY;
                     rf[k] = cs[k];
