@@ -30,7 +30,28 @@ METRIC = "paths/s, iters/s; time to loss threshold, meta-estimator vs plain MC, 
 PATHS_PER_PIXEL = 12            # 2 proportional x (primal, adjoint fwd, replay) + 1 FD pair x 6
 
 
-def parse():
+def replica_scene(scene: dict, rank: int) -> dict:
+    """Each rank optimises its own replica: the same problem under its own Philox key."""
+    sc = dict(scene)
+    sc["key_id"] = rank
+    return sc
+
+
+def slowest_rank_ms(ms: float, dist=None, device="cpu") -> float:
+    """The timed region's duration of the slowest rank (all-reduce MAX; the value itself at N = 1)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_step: float, steps: int, ms_max: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling: each rank its replica)."""
+    return world * units_per_step * steps / (ms_max * 1e-3)
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
@@ -46,7 +67,7 @@ def parse():
                     help="add the statistical validation along prescribed trajectories (1000 runs, two schedules)")
     ap.add_argument("--scale-image", type=int, default=1024, help="image side of the scale leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload():
@@ -447,8 +468,7 @@ def run_mine(args):
         return 0
 
     w = workload()
-    sc = dict(w.scene)
-    sc["key_id"] = rank                       # independent replica per rank
+    sc = replica_scene(w.scene, rank)          # independent replica per rank
     ctx = Context(local, max_paths=1 << 20)     # queue capacity: 16 spp chunks for the target render
     pid = ctx.add_scene(sc, HyperParams(lr=0.01))
     ctx.render_target(pid, torch.from_numpy(w.target_tex).cuda(), 256)
@@ -480,12 +500,9 @@ def run_mine(args):
             dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     launches_per_iter = ctx.launch_count()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * paths_per_iter * args.steps / (ms_max * 1e-3)
-    iters_per_s = world * args.steps / (ms_max * 1e-3)
+    ms_max = slowest_rank_ms(ms, dist, "cuda")
+    value = whole_job_rate(world, paths_per_iter, args.steps, ms_max)
+    iters_per_s = whole_job_rate(world, 1, args.steps, ms_max)
 
     # ---- per-kernel breakdown: event-timed launches of the same iteration (no graph) ----
     blob = ctx.checkpoint_save()
