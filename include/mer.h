@@ -186,6 +186,13 @@ mer_status mer_scene_add(mer_ctx* ctx, const mer_scene_desc* desc, int32_t* prob
 mer_status mer_params_set(mer_ctx* ctx, int32_t pid, const float* hwc, int32_t on_device);
 /* Copy the current parameters pi_i out (host pointer: synchronous; device: asynchronous). */
 mer_status mer_params_get(mer_ctx* ctx, int32_t pid, float* hwc_out, int32_t on_device);
+/* Failure detection of the bounded waits (the scatter's record staging waits on shared-memory
+ * barriers with a wall-time limit and reports MER_ERR_TIMEOUT instead of hanging): runs one
+ * such wait on a barrier that nothing completes, with limit_s in (0, 1] seconds, on the current
+ * device. Returns MER_ERR_TIMEOUT when the wait gave up as designed (MER_OK would mean the
+ * barrier completed); *waited_s receives how long it waited. The paper has no counterpart. */
+mer_status mer_wait_selftest(double limit_s, double* waited_s);
+
 /* Replaces pi_{i+1}, the parameters the last update step produced, by the caller's values (HWC,
  * host or device) and sets ||pi_{i+1} - pi_i||^2 and the next update's coefficients from them,
  * so that the estimators run along a prescribed parameter trajectory instead of the optimiser's

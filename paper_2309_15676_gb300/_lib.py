@@ -84,6 +84,7 @@ SIGNATURES = {
     "mer_params_set": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_params_get": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_params_force": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
+    "mer_wait_selftest": (ct.c_int, [ct.c_double, ct.POINTER(ct.c_double)]),
     "mer_target_set": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_target_render": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_render": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp]),

@@ -1022,6 +1022,27 @@ mer_status mer_params_get(mer_ctx* c, int32_t pid, float* out, int32_t on_device
     return MER_OK;
 }
 
+mer_status mer_wait_selftest(double limit_s, double* waited_s) {
+    if (!(limit_s > 0.0) || limit_s > 1.0) return fail(nullptr, MER_ERR_INVALID_ARG, "limit must be in (0, 1] s");
+    int32_t* d_status = nullptr;
+    uint64_t* d_ns = nullptr;
+    cudaError_t e = cudaMalloc(&d_status, sizeof(int32_t));
+    if (!e) e = cudaMalloc(&d_ns, sizeof(uint64_t));
+    if (!e) {
+        run_wait_selftest((uint64_t)(limit_s * 1e9), d_status, d_ns, nullptr);
+        e = cudaGetLastError();
+    }
+    int32_t st = MER_ERR_CUDA;
+    uint64_t ns = 0;
+    if (!e) e = cudaMemcpy(&st, d_status, sizeof st, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(&ns, d_ns, sizeof ns, cudaMemcpyDeviceToHost);
+    cudaFree(d_status);
+    cudaFree(d_ns);
+    if (e) return fail(nullptr, MER_ERR_CUDA, "wait self-test: %s", cudaGetErrorString(e));
+    if (waited_s) *waited_s = (double)ns * 1e-9;
+    return st;
+}
+
 mer_status mer_params_force(mer_ctx* c, int32_t pid, const float* hwc, int32_t on_device) {
     Problem* p = get_prob(c, pid);
     if (!p || !hwc) return fail(c, MER_ERR_INVALID_ARG, "bad problem id or input");

@@ -118,18 +118,36 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
     return done != 0;
 }
 
-// polls the barrier phase with the given parity; false once SC_WAIT_NS have passed (or after
+// polls the barrier phase with the given parity; false once limit_ns have passed (or after
 // SC_WAIT_POLLS polls) without the phase completing. The clock is read only after a first
 // unsuccessful poll.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = SC_WAIT_NS) {
     const uint32_t a = smem_addr(bar);
     if (mbar_try(a, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t k = 0; k < SC_WAIT_POLLS; ++k) {
         if (mbar_try(a, parity)) return true;
-        if ((k & 15u) == 15u && global_ns() - t0 > SC_WAIT_NS) return false;
+        if ((k & 15u) == 15u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
+}
+
+// Self-test of the bounded wait: one thread arms a fresh barrier for one arrival that nothing
+// makes, waits with the given limit and records the outcome (MER_OK or MER_ERR_TIMEOUT) and
+// the time the wait took.
+__global__ void k_wait_selftest(uint64_t limit_ns, int32_t* status, uint64_t* waited_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const uint64_t t0 = global_ns();
+    const bool ok = mbar_wait(&bar, 0u, limit_ns);
+    *waited_ns = global_ns() - t0;
+    *status = ok ? MER_OK : MER_ERR_TIMEOUT;
+}
+
+int run_wait_selftest(uint64_t limit_ns, int32_t* status, uint64_t* waited_ns, cudaStream_t st) {
+    k_wait_selftest<<<1, 1, 0, st>>>(limit_ns, status, waited_ns);
+    return 1;
 }
 
 // Phase 1, one record per lane: the bilinear footprint (clamp-to-edge) of the record's texel

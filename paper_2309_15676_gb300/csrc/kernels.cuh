@@ -43,6 +43,9 @@ int run_samples_out(const PassArgs& A, float* out, int grid, cudaStream_t st);
 cudaError_t set_trace_smem_limits(int max_nodes);
 
 // grad_over != nullptr: single-problem output; else each record's problem's F (which = 0) or dF (which = 1)
+// Bounded-wait self-test: a barrier nothing completes, waited on with limit_ns; device status
+// (MER_OK / MER_ERR_TIMEOUT) and the wait's duration
+int run_wait_selftest(uint64_t limit_ns, int32_t* status, uint64_t* waited_ns, cudaStream_t st);
 // Clears gradient texture `which` (0 F, 1 dF, 2 F_var, 3 dF_var) of every problem that has one.
 int run_zero_grads(const ProblemDev* probs, int n_probs, int which, int grid, cudaStream_t st);
 int run_scatter(uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
