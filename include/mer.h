@@ -111,6 +111,10 @@ typedef struct mer_hyper {
     float beta1;       /* Adam first moment */
     float beta2;       /* Adam second moment */
     int32_t flags;     /* MER_META_* variant bits (META mode only; 0 = as stated) */
+    float precond_lambda; /* > 0: texture gradients (F, dF and any variance samples) are replaced by
+                           * (I + lambda L)^{-1} g per channel before the update, L the Neumann graph
+                           * Laplacian of the texel grid (the gradient preconditioning of the
+                           * experiments of Sec. 6, after Nicolet et al. 2021); 0 = off */
 } mer_hyper;
 
 /* Scene of one problem. All arrays are HOST arrays, copied by mer_scene_add (the caller

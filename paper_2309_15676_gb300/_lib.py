@@ -26,7 +26,7 @@ _vp = ct.c_void_p
 
 class Hyper(ct.Structure):
     _fields_ = [("mode", ct.c_int32), ("lr", _f), ("beta_f", _f), ("beta_d", _f), ("eps", _f),
-                ("eps_alpha", _f), ("beta1", _f), ("beta2", _f), ("flags", ct.c_int32)]
+                ("eps_alpha", _f), ("beta1", _f), ("beta2", _f), ("flags", ct.c_int32), ("precond_lambda", _f)]
 
 
 class SceneDesc(ct.Structure):

@@ -34,10 +34,11 @@ class HyperParams:
     beta1: float = 0.9
     beta2: float = 0.999
     flags: int = 0            # MER_META_* variant bits (META_* constants below)
+    precond_lambda: float = 0.0   # > 0: (I + lambda L)^{-1} gradient preconditioning per texture channel
 
     def to_c(self) -> _lib.Hyper:
         return _lib.Hyper(self.mode, self.lr, self.beta_f, self.beta_d, self.eps, self.eps_alpha, self.beta1,
-                          self.beta2, self.flags)
+                          self.beta2, self.flags, self.precond_lambda)
 
 
 # image losses (scene key "loss"; the header's MER_LOSS_* values)

@@ -1,7 +1,8 @@
 """Build the CUDA library in-tree: paper_2309_15676_gb300/_build/libmer.so (sm_103a).
 
 Each translation unit is compiled by nvcc in parallel, then linked into one shared
-library with the CUDA runtime linked statically. IEEE division / square root and
+library with the CUDA runtime linked statically and cuBLAS (the texture preconditioner's plain
+matrix products) dynamically, found through an rpath to the toolkit. IEEE division / square root and
 denormals are kept (no fast-math): the update and the material model depend on them.
 """
 from __future__ import annotations
@@ -17,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmer.so")
-SOURCES = ["trace.cu", "update.cu", "kernels.cu", "api.cu", "bvh.cpp"]
+SOURCES = ["trace.cu", "update.cu", "kernels.cu", "api.cu", "precond.cu", "bvh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -58,7 +59,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(comp, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + [
+        "-L", cuda_lib, "-lcublas", "-Xlinker", "-rpath=" + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

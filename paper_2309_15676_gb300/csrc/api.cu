@@ -10,6 +10,7 @@
 
 #include "bvh.h"
 #include "kernels.cuh"
+#include "precond.cuh"
 #include "update.cuh"
 #include "wavefront.cuh"
 
@@ -31,6 +32,8 @@ struct Problem {
     float *mean = nullptr, *var = nullptr, *ap = nullptr;
     // variant state (MER_META_* flags), NULL unless needed
     float *mu_f = nullptr, *mu_d = nullptr, *am = nullptr, *av = nullptr, *Fv = nullptr, *dFv = nullptr;
+    Precond pc;                    // gradient preconditioner (precond_lambda > 0)
+    bool precond = false;
     float *target = nullptr, *img = nullptr, *dimg = nullptr, *imgA = nullptr, *imgB = nullptr;
     float *dimgA = nullptr, *dimgB = nullptr;
 };
@@ -62,6 +65,8 @@ struct mer_ctx {
     ProblemDev* d_probs = nullptr;
     ProbState* d_pstate = nullptr;
     double* d_loss = nullptr;
+    cublasHandle_t blas = nullptr;   // matrix products of the gradient preconditioner
+    void* blas_ws = nullptr;         // its fixed workspace (no allocation during graph capture)
     bool any_uncorrelated = false;   // some problem uses MER_META_UNCORRELATED
     // pass tables
     int32_t *d_prop_prob = nullptr, *d_fd_prob = nullptr;
@@ -98,7 +103,7 @@ thread_local std::string t_err = "no error";
 const char* const kClassNames[KC_COUNT] = {
     "trace_1_primal", "trace_1_replay", "shade_1_primal", "shade_1_replay",
     "trace_2_primal", "trace_2_replay", "shade_2_primal", "shade_2_replay",
-    "resolve", "l2_loss", "zero_grads", "scatter", "update", "update_finalize"};
+    "resolve", "l2_loss", "zero_grads", "scatter", "precond", "update", "update_finalize"};
 
 // CUDA-event timer installed in mer::g_timer while profiling is enabled
 struct EventTimer : KernelTimer {
@@ -435,6 +440,17 @@ int enqueue_gradient(mer_ctx* c) {
     evaluate(0u, 0, 1, c->d_loss);
     // MER_META_UNCORRELATED: a second, independent evaluation (own streams) for the variances
     if (c->any_uncorrelated) evaluate(MER_STREAM_VAR_OFFSET, 2, 3, c->d_loss + MER_MAX_PROBLEMS);
+    // gradient preconditioning of the problems that ask for it, before the update
+    for (Problem* p : c->probs) {
+        if (!p->precond) continue;
+        if (g_timer) g_timer->before(KC_PRECOND, s[0]);
+        for (float* gbuf : {p->F, p->meta ? p->dF : nullptr, p->Fv, p->dFv})
+            if (gbuf) n += precond_apply(c->blas, p->pc, gbuf, s[0]);
+        if (g_timer) {
+            g_timer->after(KC_PRECOND, s[0]);
+            g_timer->add_units(KC_PRECOND, p->n_par);
+        }
+    }
     return n;
 }
 
@@ -664,6 +680,8 @@ void mer_destroy(mer_ctx* c) {
         if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
         if (c->sx[i]) cudaStreamDestroy(c->sx[i]);
     }
+    if (c->blas) cublasDestroy(c->blas);
+    dfree(c->blas_ws);
     if (c->st) cudaStreamDestroy(c->st);
     delete c;
 }
@@ -708,6 +726,10 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
         const int32_t fl = p->hyper.flags;
         mer_hyper_default(&p->hyper);
         p->hyper.flags = fl;
+    }
+    if (!(p->hyper.precond_lambda >= 0.0f) || !std::isfinite(p->hyper.precond_lambda)) {
+        delete p;
+        return fail(c, MER_ERR_INVALID_ARG, "precond_lambda must be finite and >= 0");
     }
     if (p->hyper.flags & ~127) {
         delete p;
@@ -935,6 +957,23 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     if (vfl & MER_META_UNCORRELATED) {
         AK(alloc(&p->Fv, np));
         AK(alloc(&p->dFv, np));
+    }
+    if (p->hyper.precond_lambda > 0.0f) {
+        const cudaError_t pe = precond_init(p->pc, p->C, p->H, p->W, p->hyper.precond_lambda);
+        for (float* a : {p->pc.DW, p->pc.DH, p->pc.S, p->pc.T1, p->pc.T2})
+            if (a) p->allocs.push_back(a);   // freed with the problem, also on the error path
+        AK(pe);
+        p->precond = true;
+        if (!c->blas) {
+            const size_t ws = (size_t)32 << 20;
+            if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) {
+                c->blas = nullptr;
+                return bail(fail(c, MER_ERR_CUDA, "cublasCreate failed"));
+            }
+            AK(cudaMalloc(&c->blas_ws, ws));
+            cublasSetWorkspace(c->blas, c->blas_ws, ws);
+            cublasSetMathMode(c->blas, CUBLAS_PEDANTIC_MATH);   // plain FP32, no reduced-precision modes
+        }
     }
     AK(alloc(&p->target, npx));
     AK(alloc(&p->img, npx));

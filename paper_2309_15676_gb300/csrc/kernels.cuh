@@ -9,7 +9,7 @@ namespace mer {
 enum KernelClass {
     KC_TRACE1_PRIMAL, KC_TRACE1_REPLAY, KC_SHADE1_PRIMAL, KC_SHADE1_REPLAY,
     KC_TRACE2_PRIMAL, KC_TRACE2_REPLAY, KC_SHADE2_PRIMAL, KC_SHADE2_REPLAY,
-    KC_RESOLVE, KC_L2, KC_ZERO, KC_SCATTER, KC_UPDATE, KC_UPDATE_FIN, KC_COUNT
+    KC_RESOLVE, KC_L2, KC_ZERO, KC_SCATTER, KC_PRECOND, KC_UPDATE, KC_UPDATE_FIN, KC_COUNT
 };
 
 // records CUDA events around launches when installed (diagnostic mode, one thread)
