@@ -211,7 +211,7 @@ def eval_loss(torch, ctx, pid, target, spp=64):
     return float(((img - target) ** 2).mean())
 
 
-def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags=0):
+def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags=0, precond_lambda=0.0):
     """One optimisation run: iterations and GPU time (iterations only, evaluation excluded) until
     the 64-spp eval loss drops below `frac` of its initial value; evaluated every 2 iterations for
     the first 50, then every 10."""
@@ -219,9 +219,15 @@ def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, fr
     sc = dict(w.scene)
     sc["spp_prop"], sc["spp_fd"] = spp_prop, spp_fd
     ctx = Context(0)
-    pid = ctx.add_scene(sc, HyperParams(mode=mode, lr=lr, flags=flags))
+    pid = ctx.add_scene(sc, HyperParams(mode=mode, lr=lr, flags=flags, precond_lambda=precond_lambda))
     ctx.set_target(pid, target_img)
     ctx.set_params(pid, w.init_tex)
+    # capture the iteration graph (and initialise any library it calls) outside the timed region:
+    # one iteration, then rewind the state
+    blob = ctx.checkpoint_save()
+    ctx.iterate(1, use_graph=True)
+    ctx.checkpoint_load(blob)
+    torch.cuda.synchronize()
     l0 = eval_loss(torch, ctx, pid, target_img)
     thr = frac * l0
     gpu_ms, it, reached, reached_ms, last, lmin = 0.0, 0, None, None, l0, l0
@@ -244,25 +250,29 @@ def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, fr
             "gpu_s_total": gpu_ms / 1e3}
 
 
-def time_to_threshold(torch, w, target_img, max_iters, lrs=(0.001, 0.003, 0.01, 0.03), frac=0.05):
+def time_to_threshold(torch, w, target_img, max_iters, lrs=(0.001, 0.003, 0.01, 0.03), frac=0.05, precond=None):
     """Meta-estimator (the workload's 1 FD + n proportional spp; FD pairs by random-number replay,
     and with the pi_{i-1} branch sharing the pi_i path) vs Adam on n+1 fresh proportional spp
     (equal spp per iteration), each at its best learning rate of the grid: iterations and GPU
-    time until the 64-spp eval loss drops below `frac` of its initial value."""
+    time until the 64-spp eval loss drops below `frac` of its initial value. With `precond`
+    (a lambda), both methods are also run on preconditioned texture gradients."""
     from paper_2309_15676_gb300.api import META_FD_SHARED_PATH, MODE_ADAM, MODE_META
     out = {}
     pp, pf = w.scene["spp_prop"], w.scene["spp_fd"]
-    for name, mode, spp_prop, spp_fd, flags in (("meta", MODE_META, pp, pf, 0),
-                                                ("meta_shared_path", MODE_META, pp, pf, META_FD_SHARED_PATH),
-                                                ("adam", MODE_ADAM, pp + pf, 0, 0)):
+    methods = [("meta", MODE_META, pp, pf, 0, 0.0),
+               ("meta_shared_path", MODE_META, pp, pf, META_FD_SHARED_PATH, 0.0),
+               ("adam", MODE_ADAM, pp + pf, 0, 0, 0.0)]
+    if precond:
+        methods += [("meta_precond", MODE_META, pp, pf, 0, precond), ("adam_precond", MODE_ADAM, pp + pf, 0, 0, precond)]
+    for name, mode, spp_prop, spp_fd, flags, lam in methods:
         best, runs = None, []
         for lr in lrs:
-            r = optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags)
+            r = optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags, lam)
             runs.append(r)
             key = (0 if r["iters"] else 1, r["gpu_s"] if r["iters"] else r["min_loss_ratio"])
             if best is None or key < best[0]:
                 best = (key, r)
-        out[name] = dict(best[1], all_lrs=runs)
+        out[name] = dict(best[1], all_lrs=runs, precond_lambda=lam)
     out["threshold"] = f"{frac:.0%} of the iteration-0 64-spp eval loss"
     out["lr_grid"] = list(lrs)
     return out
@@ -283,9 +293,14 @@ def spp_sweep(torch, iters=150, spps=(1, 2, 4, 8, 16, 32, 64), lr_meta=0.01, lr_
     meta = optimise_run(torch, w, target, MODE_META, 2, 1, lr_meta, iters, frac)
     meta_shared = optimise_run(torch, w, target, MODE_META, 2, 1, lr_meta, iters, frac, META_FD_SHARED_PATH)
     adam = [dict(optimise_run(torch, w, target, MODE_ADAM, s_, 0, lr_adam, iters, frac), spp=s_) for s_ in spps]
+    # with preconditioned texture gradients (lambda 4), both methods at lr 0.03
+    meta_pc = optimise_run(torch, w, target, MODE_META, 2, 1, 0.03, iters, frac, 0, 4.0)
+    adam_pc = [dict(optimise_run(torch, w, target, MODE_ADAM, s_, 0, 0.03, iters, frac, 0, 4.0), spp=s_) for s_ in spps]
     return {"workload": "spiral512: 512^2, 32,768 triangles, 1024^2x5 textures, depth 8",
             "meta": dict(meta, spp="1 FD + 2 proportional"),
             "meta_shared_path": dict(meta_shared, spp="1 FD (shared path) + 2 proportional"), "adam_sweep": adam,
+            "meta_precond": dict(meta_pc, spp="1 FD + 2 proportional", precond_lambda=4.0),
+            "adam_sweep_precond": adam_pc,
             "lr": {"meta": lr_meta, "adam": lr_adam}, "threshold": f"{frac:.0%} of the iteration-0 64-spp eval loss",
             "iterations": iters}
 
@@ -589,7 +604,7 @@ def run_mine(args):
     ttt = None
     if rank == 0 and not args.no_ttt:
         ttt = {"spiral256 (learning rate tuned per method)":
-               time_to_threshold(torch, w, target_img, args.ttt_iters)}
+               time_to_threshold(torch, w, target_img, args.ttt_iters, lrs=(0.003, 0.01, 0.03, 0.1), precond=4.0)}
         # config 1 as stated: 64x64 box, 32x32 RGB albedo, depth 3, 1 FD + 1 proportional spp, lr 0.01,
         # 50 iterations (Adam on 2 fresh spp)
         from paper_2309_15676_gb300 import synth as _s
