@@ -876,3 +876,176 @@ void orc_philox_batch(int64_t n, const uint32_t* ctr, const uint32_t key[2], uin
 {
     for (int64_t i = 0; i < n; ++i) orc_philox(ctr + 4 * i, key, out + 4 * i);
 }
+
+/* ========================================================================= */
+/* Emissive-absorptive volume (the high-dimensional experiment of Sec. 6):    */
+/* a voxel grid of emission (RGB) and density over an axis-aligned box, seen  */
+/* from several pinhole views and rendered by a jittered ray march:           */
+/*   L = sum_k T_k (1 - exp(-sigma_k delta)) e_k + T_end * background,        */
+/*   T_{k+1} = T_k exp(-sigma_k delta),                                       */
+/* sample k at t0 + (k + u) delta for one uniform u per ray (Philox vertex 1), */
+/* samples past the exit skipped. Parameters: ((z ny + y) nx + x) * 4 + c,     */
+/* c = 0..2 emission, 3 density; trilinear, clamp-to-edge, voxel centres at    */
+/* (i + 1/2) / n across the box. Gradients by replay: d L / d e_k = T_k a_k,   */
+/* d L / d sigma_k = delta ((1 - a_k) T_k e_k - L_after_k).                    */
+/* ========================================================================= */
+typedef struct {
+    int32_t nx, ny, nz;
+    float lo[3], hi[3];
+    int32_t n_views, width, height;
+    const float* cameras;   /* [n_views][10]: eye, target, up, fov_deg */
+    float step;             /* march step (world units) */
+    float bg[3];
+    uint32_t seed, key_id;
+} orc_volume;
+
+static void vol_camera_ray(const orc_volume* v, int view, int px, int py, double j0, double j1, v3* o, v3* d)
+{
+    const float* c = v->cameras + 10 * view;
+    v3 eye = vload(c), tg = vload(c + 3), up = vload(c + 6);
+    v3 f = vnorm(vsub(tg, eye));
+    v3 r = vnorm(vcross(f, up));
+    v3 u = vcross(r, f);
+    double th = tan(0.5 * c[9] * PI / 180.0);
+    double asp = (double)v->width / (double)v->height;
+    double sx = (2.0 * (px + j0) / v->width - 1.0) * th * asp;
+    double sy = (1.0 - 2.0 * (py + j1) / v->height) * th;
+    *o = eye;
+    *d = vnorm(vadd(f, vadd(vmul(r, sx), vmul(u, sy))));
+}
+
+/* entry and exit of the box along the ray (t0 clamped to 0); 0 if the ray misses */
+static int vol_box(const orc_volume* v, v3 o, v3 d, double* t0, double* t1)
+{
+    double a = 0.0, b = INFINITY;
+    double oo[3] = { o.x, o.y, o.z }, dd[3] = { d.x, d.y, d.z };
+    for (int k = 0; k < 3; ++k) {
+        double lo = v->lo[k], hi = v->hi[k];
+        if (dd[k] == 0.0) {
+            if (oo[k] < lo || oo[k] > hi) return 0;
+            continue;
+        }
+        double ta = (lo - oo[k]) / dd[k], tb = (hi - oo[k]) / dd[k];
+        if (ta > tb) { double t = ta; ta = tb; tb = t; }
+        if (ta > a) a = ta;
+        if (tb < b) b = tb;
+    }
+    *t0 = a;
+    *t1 = b;
+    return b > a;
+}
+
+/* trilinear taps of point p: voxel indices and weights (clamp-to-edge) */
+static void vol_taps(const orc_volume* v, v3 p, int idx[8], double w[8])
+{
+    int n[3] = { v->nx, v->ny, v->nz };
+    double pp[3] = { p.x, p.y, p.z };
+    int i0[3], i1[3];
+    double f[3];
+    for (int k = 0; k < 3; ++k) {
+        double g = (pp[k] - v->lo[k]) / (v->hi[k] - v->lo[k]) * n[k] - 0.5;
+        double fl = floor(g);
+        f[k] = g - fl;
+        int a = (int)fl, b = a + 1;
+        if (a < 0) a = 0;
+        if (a > n[k] - 1) a = n[k] - 1;
+        if (b < 0) b = 0;
+        if (b > n[k] - 1) b = n[k] - 1;
+        i0[k] = a;
+        i1[k] = b;
+    }
+    for (int c = 0; c < 8; ++c) {
+        int x = (c & 1) ? i1[0] : i0[0], y = (c & 2) ? i1[1] : i0[1], z = (c & 4) ? i1[2] : i0[2];
+        double wx = (c & 1) ? f[0] : 1.0 - f[0], wy = (c & 2) ? f[1] : 1.0 - f[1], wz = (c & 4) ? f[2] : 1.0 - f[2];
+        idx[c] = (z * v->ny + y) * v->nx + x;
+        w[c] = wx * wy * wz;
+    }
+}
+
+/* one sample of pixel `pixel` (= view * W * H + py * W + px). mode 0: radiance into Lout. mode 1:
+ * replay with the sample's total radiance Ltot and adjoint weight adj, gradients into grad. */
+static void vol_march(const orc_volume* v, const double* par, uint32_t pixel, uint32_t sample, uint32_t iter,
+                      uint32_t stream, int mode, const double Ltot[3], const double adj[3], double* grad,
+                      double Lout[3])
+{
+    rng_ctx R = { { v->seed, v->key_id }, pixel, sample, iter, stream };
+    uint32_t per_view = (uint32_t)v->width * (uint32_t)v->height;
+    int view = (int)(pixel / per_view);
+    uint32_t local = pixel % per_view;
+    double u[4];
+    draw4(&R, 0, 0, u, NULL);
+    v3 o, d;
+    vol_camera_ray(v, view, (int)(local % (uint32_t)v->width), (int)(local / (uint32_t)v->width), u[0], u[1], &o, &d);
+    double L[3] = { 0, 0, 0 }, T = 1.0;
+    double t0, t1;
+    if (vol_box(v, o, d, &t0, &t1)) {
+        draw4(&R, 1, 0, u, NULL);
+        const double dl = v->step;
+        for (int k = 0;; ++k) {
+            double t = t0 + (k + u[0]) * dl;
+            if (!(t < t1)) break;
+            v3 p = vadd(o, vmul(d, t));
+            int idx[8];
+            double w[8], e[3] = { 0, 0, 0 }, sg = 0.0;
+            vol_taps(v, p, idx, w);
+            for (int c = 0; c < 8; ++c) {
+                for (int j = 0; j < 3; ++j) e[j] += w[c] * par[4 * (size_t)idx[c] + j];
+                sg += w[c] * par[4 * (size_t)idx[c] + 3];
+            }
+            double tr = exp(-sg * dl), a = 1.0 - tr;
+            for (int j = 0; j < 3; ++j) L[j] += T * a * e[j];
+            if (mode == 1) {
+                double ge[3], gs = 0.0;
+                for (int j = 0; j < 3; ++j) {
+                    double after = Ltot[j] - L[j];
+                    ge[j] = adj[j] * T * a;
+                    gs += adj[j] * (tr * T * e[j] - after);
+                }
+                gs *= dl;
+                for (int c = 0; c < 8; ++c) {
+                    for (int j = 0; j < 3; ++j) grad[4 * (size_t)idx[c] + j] += w[c] * ge[j];
+                    grad[4 * (size_t)idx[c] + 3] += w[c] * gs;
+                }
+            }
+            T *= tr;
+        }
+    }
+    for (int j = 0; j < 3; ++j) L[j] += T * v->bg[j];
+    for (int j = 0; j < 3; ++j) Lout[j] = L[j];
+}
+
+void orc_vol_render_samples(const orc_volume* v, const double* par, int64_t n, const uint32_t* pixels,
+                            const uint32_t* samples, uint32_t iter, uint32_t stream, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) vol_march(v, par, pixels[i], samples[i], iter, stream, 0, NULL, NULL, NULL, out + 3 * i);
+}
+
+/* mean over spp samples per pixel; image [n_views * H * W * 3] */
+void orc_vol_render_image(const orc_volume* v, const double* par, int spp, uint32_t iter, uint32_t stream, double* img)
+{
+    int64_t N = (int64_t)v->n_views * v->width * v->height;
+    for (int64_t p = 0; p < N; ++p) {
+        double acc[3] = { 0, 0, 0 };
+        for (int k = 0; k < spp; ++k) {
+            double L[3];
+            vol_march(v, par, (uint32_t)p, (uint32_t)k, iter, stream, 0, NULL, NULL, NULL, L);
+            for (int c = 0; c < 3; ++c) acc[c] += L[c];
+        }
+        for (int c = 0; c < 3; ++c) img[3 * p + c] = acc[c] / spp;
+    }
+}
+
+/* gradient of sum_p dimg[p] . I_p (I_p the spp-sample mean), accumulated into grad [nvox * 4] */
+void orc_vol_adjoint_image(const orc_volume* v, const double* par, int spp, uint32_t iter, uint32_t stream,
+                           const double* dimg, double* grad)
+{
+    int64_t N = (int64_t)v->n_views * v->width * v->height;
+    for (int64_t p = 0; p < N; ++p) {
+        for (int k = 0; k < spp; ++k) {
+            double adj[3] = { dimg[3 * p] / spp, dimg[3 * p + 1] / spp, dimg[3 * p + 2] / spp };
+            double Lt[3], Lr[3];
+            vol_march(v, par, (uint32_t)p, (uint32_t)k, iter, stream, 0, NULL, NULL, NULL, Lt);
+            vol_march(v, par, (uint32_t)p, (uint32_t)k, iter, stream, 1, Lt, adj, grad, Lr);
+        }
+    }
+}

@@ -67,6 +67,11 @@ def lib():
         L.orc_l2_loss.argtypes = [ct.c_int64, _f64p, _f64p, _f64p]
         L.orc_l2_loss.restype = ct.c_double
         L.orc_mrse_loss.argtypes = [ct.c_int64, _f64p, _f64p, _f64p]
+        L.orc_vol_render_samples.argtypes = [ct.POINTER(OrcVolume), _f64p, ct.c_int64, _u32p, _u32p, ct.c_uint32,
+                                             ct.c_uint32, _f64p]
+        L.orc_vol_render_image.argtypes = [ct.POINTER(OrcVolume), _f64p, ct.c_int, ct.c_uint32, ct.c_uint32, _f64p]
+        L.orc_vol_adjoint_image.argtypes = [ct.POINTER(OrcVolume), _f64p, ct.c_int, ct.c_uint32, ct.c_uint32,
+                                            _f64p, _f64p]
         L.orc_mrse_loss.restype = ct.c_double
         _lib = L
     return _lib
@@ -287,3 +292,61 @@ def fd_gradient(sc: Scene, tex_cur, tex_prev, target, spp, iteration, stream_off
     else:
         g_p = adjoint_image(sc, tex_prev, spp, iteration, ST_FD_ADJ + stream_offset, d_p)
     return g_c - g_p
+
+
+# ---------------------------------------------------------------------------------------
+# emissive-absorptive volume (see orc_vol_* in oracle.c)
+# ---------------------------------------------------------------------------------------
+class OrcVolume(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32), ("lo", ct.c_float * 3),
+                ("hi", ct.c_float * 3), ("n_views", ct.c_int32), ("width", ct.c_int32), ("height", ct.c_int32),
+                ("cameras", ct.POINTER(ct.c_float)), ("step", ct.c_float), ("bg", ct.c_float * 3),
+                ("seed", ct.c_uint32), ("key_id", ct.c_uint32)]
+
+
+class Volume:
+    """A volume scene dict (synth.volume_scene) held for the oracle."""
+
+    def __init__(self, scene: dict):
+        self.cams = np.ascontiguousarray(scene["cameras"], np.float32)
+        v = OrcVolume()
+        v.nx, v.ny, v.nz = scene["nx"], scene["ny"], scene["nz"]
+        v.lo = (ct.c_float * 3)(*scene["lo"])
+        v.hi = (ct.c_float * 3)(*scene["hi"])
+        v.n_views, v.width, v.height = scene["n_views"], scene["width"], scene["height"]
+        v.cameras = self.cams.ctypes.data_as(ct.POINTER(ct.c_float))
+        v.step = scene["step"]
+        v.bg = (ct.c_float * 3)(*scene["bg"])
+        v.seed, v.key_id = scene["seed"], scene["key_id"]
+        self.v = v
+        self.shape = (scene["nz"], scene["ny"], scene["nx"], 4)
+        self.image_shape = (scene["n_views"], scene["height"], scene["width"], 3)
+
+    def ref(self):
+        return ct.byref(self.v)
+
+
+def vol_render_image(vol: Volume, params, spp, iteration, stream):
+    out = np.zeros(vol.image_shape, np.float64)
+    par = np.ascontiguousarray(params, np.float64)
+    lib().orc_vol_render_image(vol.ref(), _p(par, _f64p), spp, iteration, stream, _p(out, _f64p))
+    return out
+
+
+def vol_render_samples(vol: Volume, params, pixels, samples, iteration, stream):
+    pixels = np.ascontiguousarray(pixels, np.uint32)
+    samples = np.ascontiguousarray(samples, np.uint32)
+    out = np.zeros((len(pixels), 3), np.float64)
+    par = np.ascontiguousarray(params, np.float64)
+    lib().orc_vol_render_samples(vol.ref(), _p(par, _f64p), len(pixels), _p(pixels, _u32p), _p(samples, _u32p),
+                                 iteration, stream, _p(out, _f64p))
+    return out
+
+
+def vol_adjoint_image(vol: Volume, params, spp, iteration, stream, dimg):
+    grad = np.zeros(vol.shape, np.float64)
+    par = np.ascontiguousarray(params, np.float64)
+    d = np.ascontiguousarray(dimg, np.float64)
+    lib().orc_vol_adjoint_image(vol.ref(), _p(par, _f64p), spp, iteration, stream, _p(d, _f64p), _p(grad, _f64p))
+    return grad
+

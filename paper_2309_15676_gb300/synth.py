@@ -385,3 +385,47 @@ def workload_batch(n_problems=64, seed=4, scale=1.0):
                                 name=f"p{q}_dsphere")
         out.append(w)
     return out
+
+
+def _blobs(n, rng, k, emit_scale, dens_scale):
+    """Sum of k Gaussian blobs of emission (RGB) and density on an n^3 grid (voxel centres)."""
+    c = (np.arange(n, dtype=np.float32) + 0.5) / n * 2.0 - 1.0
+    out = np.zeros((n, n, n, 4), np.float32)
+    for _ in range(k):
+        mu = rng.uniform(-0.55, 0.55, 3).astype(np.float32)
+        s = np.float32(rng.uniform(0.12, 0.3))
+        col = rng.uniform(0.2, 1.0, 3).astype(np.float32) * emit_scale
+        rho = np.float32(rng.uniform(0.5, 1.0) * dens_scale)
+        gx = np.exp(-((c - mu[0]) ** 2) / (2 * s * s))
+        gy = np.exp(-((c - mu[1]) ** 2) / (2 * s * s))
+        gz = np.exp(-((c - mu[2]) ** 2) / (2 * s * s))
+        g = gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+        out[..., :3] += g[..., None] * col
+        out[..., 3] += g * rho
+    return out
+
+
+def volume_scene(n=256, views=4, width=256, height=256, step=None, seed=7, key_id=0, bg=(0.0, 0.0, 0.0)):
+    """An n^3 voxel volume in the box [-1, 1]^3 seen from `views` pinhole cameras on a circle of
+    radius 3.2 around it (30 degrees above the equator), fov 40; march step one voxel (2/n)."""
+    cams = []
+    for v in range(views):
+        a = 2.0 * math.pi * v / views
+        eye = [3.2 * math.cos(a) * math.cos(0.5236), 3.2 * math.sin(0.5236), 3.2 * math.sin(a) * math.cos(0.5236)]
+        cams.append(eye + [0.0, 0.0, 0.0] + [0.0, 1.0, 0.0] + [40.0])
+    return {"kind": "volume", "nx": n, "ny": n, "nz": n, "lo": [-1.0, -1.0, -1.0], "hi": [1.0, 1.0, 1.0],
+            "n_views": views, "width": width, "height": height, "cameras": np.asarray(cams, np.float32),
+            "step": float(2.0 / n if step is None else step), "bg": list(bg), "seed": seed, "key_id": key_id,
+            "clamp_lo": [0.0, 0.0, 0.0, 0.0], "clamp_hi": [4.0, 4.0, 4.0, 60.0]}
+
+
+def workload_volume(n=256, views=4, width=256, height=256, seed=7, key_id=0):
+    """Emissive-absorptive volume (the 256^3 x 4 = 67M-parameter experiment): target = eight
+    Gaussian blobs of emission and density (seed 21), init = a uniform faint grey volume."""
+    s = volume_scene(n, views, width, height, seed=seed, key_id=key_id)
+    target = _blobs(n, np.random.default_rng(21), 8, 1.0, 12.0)
+    init = np.empty((n, n, n, 4), np.float32)
+    init[..., :3] = 0.2
+    init[..., 3] = 1.0
+    return Workload(f"volume{n}_{views}x{width}", s, init, target)
+
