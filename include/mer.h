@@ -190,6 +190,44 @@ mer_status mer_scene_add(mer_ctx* ctx, const mer_scene_desc* desc, int32_t* prob
 mer_status mer_params_set(mer_ctx* ctx, int32_t pid, const float* hwc, int32_t on_device);
 /* Copy the current parameters pi_i out (host pointer: synchronous; device: asynchronous). */
 mer_status mer_params_get(mer_ctx* ctx, int32_t pid, float* hwc_out, int32_t on_device);
+/* ---- Emissive-absorptive volume (the high-dimensional experiment of Sec. 6) ----
+ * A voxel grid of emission (RGB) and density over the box [lo, hi], seen from n_views pinhole
+ * cameras (width x height each; images stacked view-major, RGB fp32) and rendered by a jittered
+ * ray march: L = sum_k T_k (1 - exp(-sigma_k * step)) e_k + T_end * background with
+ * T_{k+1} = T_k exp(-sigma_k * step); sample k at t0 + (k + u) * step, u one Philox uniform per ray
+ * (vertex 1; the pixel jitter is vertex 0), samples past the box exit skipped. Parameters: device
+ * float4 per voxel (emission RGB, density) at ((z * ny + y) * nx + x), 16-byte aligned; trilinear
+ * interpolation, clamp-to-edge, voxel centres at (i + 1/2) / n across the box. Pixel index =
+ * view * width * height + y * width + x; counters as for surfaces (pixel, sample, iteration,
+ * stream). */
+typedef struct mer_volume_desc {
+    int32_t nx, ny, nz;
+    float lo[3], hi[3];
+    int32_t n_views, width, height;
+    const float* cameras;     /* HOST [n_views][10]: eye xyz, target xyz, up xyz, fov_deg */
+    float step;               /* march step, world units (> 0) */
+    float background[3];
+    uint32_t seed, key_id;    /* Philox key */
+} mer_volume_desc;
+typedef struct mer_volume mer_volume;
+mer_status mer_volume_create(const mer_volume_desc* desc, int32_t device, mer_volume** out);
+void mer_volume_destroy(mer_volume* vol);
+/* img_dev [n_views * height * width * 3] = mean over spp samples (asynchronous on cuda_stream) */
+mer_status mer_volume_render(mer_volume* vol, const float* params_dev, int32_t spp, uint32_t stream,
+                             uint32_t iteration, float* img_dev, void* cuda_stream);
+/* grad_dev (voxel float4s, caller-zeroed) += d/dparams of sum_p dimg[p] . I_p by replay of the
+ * same counters (the ray's radiance pass, then the replay; no stored samples) */
+mer_status mer_volume_adjoint(mer_volume* vol, const float* params_dev, const float* dimg_dev, int32_t spp,
+                              uint32_t stream, uint32_t iteration, float* grad_dev, void* cuda_stream);
+/* FD pair (Eq. est_triv): the same counters at paramsA and paramsB; grad_dev += g_A - g_B */
+mer_status mer_volume_adjoint_pair(mer_volume* vol, const float* paramsA_dev, const float* paramsB_dev,
+                                   const float* dimgA_dev, const float* dimgB_dev, int32_t spp, uint32_t stream,
+                                   uint32_t iteration, float* grad_dev, void* cuda_stream);
+/* Image loss of n_pix RGB pixels (MER_LOSS_L2 or MER_LOSS_MRSE, as in step a7): *loss_dev (device
+ * double) = the loss, dimg_dev = dLoss/dimg. */
+mer_status mer_image_loss(int32_t kind, int64_t n_pix, const float* img_dev, const float* target_dev,
+                          float* dimg_dev, double* loss_dev, void* cuda_stream);
+
 /* Failure detection of the bounded waits (the scatter's record staging waits on shared-memory
  * barriers with a wall-time limit and reports MER_ERR_TIMEOUT instead of hanging): runs one
  * such wait on a barrier that nothing completes, with limit_s in (0, 1] seconds, on the current

@@ -64,6 +64,12 @@ class StateView(ct.Structure):
                [("n", ct.c_int64)]
 
 
+class VolumeDesc(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32), ("lo", _f * 3), ("hi", _f * 3),
+                ("n_views", ct.c_int32), ("width", ct.c_int32), ("height", ct.c_int32), ("cameras", _fp),
+                ("step", _f), ("background", _f * 3), ("seed", ct.c_uint32), ("key_id", ct.c_uint32)]
+
+
 class UpdateArrays(ct.Structure):
     _fields_ = [(n, _vp) for n in ("pi", "pi_next", "F", "dF", "m2f", "m2d", "mean", "var", "alpha_prev",
                                    "mu_f", "mu_d", "adam_m", "adam_v", "F_var", "dF_var")]
@@ -85,6 +91,12 @@ SIGNATURES = {
     "mer_params_get": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_params_force": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_wait_selftest": (ct.c_int, [ct.c_double, ct.POINTER(ct.c_double)]),
+    "mer_volume_create": (ct.c_int, [ct.POINTER(VolumeDesc), ct.c_int32, ct.POINTER(_vp)]),
+    "mer_volume_destroy": (None, [_vp]),
+    "mer_volume_render": (ct.c_int, [_vp, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp, _vp]),
+    "mer_volume_adjoint": (ct.c_int, [_vp, _vp, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp, _vp]),
+    "mer_volume_adjoint_pair": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp, _vp]),
+    "mer_image_loss": (ct.c_int, [ct.c_int32, ct.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "mer_target_set": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_target_render": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_render": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp]),

@@ -327,6 +327,74 @@ def meta_step_raw(hyper: HyperParams, pi, pi_next, F, dF, m2f, m2d, mean, var, a
     return out
 
 
+class Volume:
+    """Emissive-absorptive volume (mer_volume_*): render, replay adjoints and FD pairs of voxel
+    parameters (torch float32 (nz, ny, nx, 4) on the device: emission RGB, density)."""
+
+    def __init__(self, scene: dict, device: int = 0):
+        self.L = _lib.load()
+        self.device = torch.device("cuda", device)
+        self.cams = np.ascontiguousarray(scene["cameras"], np.float32)
+        d = _lib.VolumeDesc()
+        d.nx, d.ny, d.nz = scene["nx"], scene["ny"], scene["nz"]
+        d.lo = (ct.c_float * 3)(*scene["lo"])
+        d.hi = (ct.c_float * 3)(*scene["hi"])
+        d.n_views, d.width, d.height = scene["n_views"], scene["width"], scene["height"]
+        d.cameras = self.cams.ctypes.data_as(ct.POINTER(ct.c_float))
+        d.step = scene["step"]
+        d.background = (ct.c_float * 3)(*scene["bg"])
+        d.seed, d.key_id = scene["seed"], scene["key_id"]
+        h = ct.c_void_p()
+        check(self.L.mer_volume_create(ct.byref(d), device, ct.byref(h)))
+        self.h = h
+        self.shape = (scene["nz"], scene["ny"], scene["nx"], 4)
+        self.image_shape = (scene["n_views"], scene["height"], scene["width"], 3)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mer_volume_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, params, spp=1, stream=STREAM_EVAL, iteration=0) -> torch.Tensor:
+        p = _dev_f32(params, self.device)
+        img = torch.empty(self.image_shape, device=self.device, dtype=torch.float32)
+        check(self.L.mer_volume_render(self.h, _ptr(p), spp, stream, iteration, _ptr(img), _cur_stream(self.device)))
+        return img
+
+    def adjoint(self, params, dimg, spp=1, stream=STREAM_EVAL, iteration=0, grad=None) -> torch.Tensor:
+        p, d = _dev_f32(params, self.device), _dev_f32(dimg, self.device)
+        g = torch.zeros(self.shape, device=self.device, dtype=torch.float32) if grad is None else grad
+        check(self.L.mer_volume_adjoint(self.h, _ptr(p), _ptr(d), spp, stream, iteration, _ptr(g),
+                                        _cur_stream(self.device)))
+        return g
+
+    def adjoint_pair(self, pA, pB, dA, dB, spp=1, stream=STREAM_FD_ADJ, iteration=0, grad=None) -> torch.Tensor:
+        a, b = _dev_f32(pA, self.device), _dev_f32(pB, self.device)
+        da, db = _dev_f32(dA, self.device), _dev_f32(dB, self.device)
+        g = torch.zeros(self.shape, device=self.device, dtype=torch.float32) if grad is None else grad
+        check(self.L.mer_volume_adjoint_pair(self.h, _ptr(a), _ptr(b), _ptr(da), _ptr(db), spp, stream, iteration,
+                                             _ptr(g), _cur_stream(self.device)))
+        return g
+
+
+def image_loss(img: torch.Tensor, target: torch.Tensor, kind: int = 0):
+    """(loss device double tensor, dLoss/dimg) of an RGB image (mer_image_loss)."""
+    L = _lib.load()
+    img = img.contiguous()
+    target = target.contiguous()
+    dimg = torch.empty_like(img)
+    loss = torch.zeros(1, device=img.device, dtype=torch.float64)
+    check(L.mer_image_loss(kind, img.numel() // 3, _ptr(img), _ptr(target), _ptr(dimg), _ptr(loss),
+                           _cur_stream(img.device)))
+    return loss, dimg
+
+
 def meta_step_raw_ex(hyper: HyperParams, arrays: dict, C, lo, hi, iteration, count_f, count_d, dpi_norm2,
                      zero_grads=True, out=None):
     """mer_meta_step_raw_ex on torch device tensors (dict keys as in mer_update_arrays; absent keys

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmer.so")
-SOURCES = ["trace.cu", "update.cu", "kernels.cu", "api.cu", "precond.cu", "bvh.cpp"]
+SOURCES = ["trace.cu", "update.cu", "kernels.cu", "api.cu", "precond.cu", "volume.cu", "bvh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
