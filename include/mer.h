@@ -24,6 +24,13 @@
  *  - Random numbers: Philox4x32-10 with key (seed, key_id) and counter
  *    (pixel, sample, iteration, stream<<16 | vertex<<4 | block); uniforms are
  *    (x >> 8) * 2^-24. Streams: MER_STREAM_*.
+ *
+ * Steps of one iteration, as the comments below number them:
+ *  a1 Philox streams; a2 camera rays; a3 BVH traversal and intersection; a4 surface
+ *  interaction (texture fetch, BSDF parameters); a5 next-event estimation with MIS; a6 BSDF
+ *  sample and continuation; a7 image and loss adjoint; a8 path-replay adjoint; a9 the FD pair
+ *  at pi_i and pi_{i-1}; a10 scatter of texel gradients; a11 the fused update; a12 batching of
+ *  problems and graph capture of the iteration.
  */
 #ifndef MER_H
 #define MER_H
@@ -391,6 +398,39 @@ typedef struct mer_kernel_time {
 mer_status mer_profile_enable(mer_ctx* ctx, int32_t enable);
 /* Synchronises, writes up to max_entries launch classes that ran (in a fixed order) and clears them. */
 mer_status mer_profile_read(mer_ctx* ctx, mer_kernel_time* out, int32_t max_entries, int32_t* n_out);
+
+/* Optimiser of a volume's voxel parameters toward target images (the 256^3 emissive-absorptive
+ * experiment of Sec. 6) by the meta-estimator (MER_MODE_META) or Adam (MER_MODE_ADAM). It owns two
+ * parameter slots (pi_i and pi_{i-1}), F, dF, the optimiser state and its images. One iteration:
+ * the proportional sample <F_i> (render pi_i on MER_STREAM_PROP_PRIMAL, loss adjoint, replay on
+ * MER_STREAM_PROP_ADJ), in META mode concurrently the FD sample <dF_i> of Eq. est_triv (pi_i and
+ * pi_{i-1} rendered on the same MER_STREAM_FD_PRIMAL rays, both loss adjoints, paired replay on
+ * MER_STREAM_FD_ADJ), then the fused update a11 over the 4 nvox parameters (channel c = index % 4
+ * clamped to [lo[c], hi[c]]). Every per-iteration scalar (iteration, slot, step counts, ||dpi||^2,
+ * the update's coefficients) stays on the device, so mer_volume_opt_iterate with use_graph = 1
+ * replays one captured graph. hyper->flags: every MER_META_* variant (UNCORRELATED repeats both
+ * samples on the streams + MER_STREAM_VAR_OFFSET; FD_SHARED_PATH changes nothing, no sampling
+ * decision of the march depends on the parameters); precond_lambda must be 0.
+ * target: device image [n_views][height][width][3] (copied); init: device voxels (copied into
+ * both slots, 16-byte aligned). vol must outlive the optimiser. Synchronous. */
+typedef struct mer_volume_opt mer_volume_opt;
+mer_status mer_volume_opt_create(mer_volume* vol, const mer_hyper* hyper, int32_t loss_kind, int32_t spp_f,
+                                 int32_t spp_d, const float* lo4, const float* hi4, const float* target_dev,
+                                 const float* init_dev, mer_volume_opt** out);
+void mer_volume_opt_destroy(mer_volume_opt* opt);
+/* Both slots = params_dev (device, copied); the optimiser state and iteration count reset. Synchronous. */
+mer_status mer_volume_opt_set_params(mer_volume_opt* opt, const float* params_dev);
+/* n_iters iterations, ordered after earlier work on cuda_stream, which waits for them (asynchronous;
+ * the optimiser's own streams run the work). use_graph = 1: one graph captured on first use. */
+mer_status mer_volume_opt_iterate(mer_volume_opt* opt, int32_t n_iters, int32_t use_graph, void* cuda_stream);
+/* iteration, loss of the last proportional primal image, ||dpi||^2, step counts; paths_per_iter =
+ * ray marches per iteration (a rendered ray counts one, a replayed one two). Synchronous. */
+mer_status mer_volume_opt_stats(mer_volume_opt* opt, mer_iter_stats* out);
+/* Device pointers of the optimiser's arrays (valid until destroy; pi_cur / pi_prev as of the
+ * last completed iteration; NULL where the mode and flags keep no such array). Synchronous. */
+mer_status mer_volume_opt_state(mer_volume_opt* opt, mer_state_view* out);
+/* Kernel launches (and memsets) one iteration enqueues. */
+mer_status mer_volume_opt_launches(mer_volume_opt* opt, int32_t* out);
 
 #ifdef __cplusplus
 }

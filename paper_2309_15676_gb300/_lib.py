@@ -97,6 +97,14 @@ SIGNATURES = {
     "mer_volume_adjoint": (ct.c_int, [_vp, _vp, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp, _vp]),
     "mer_volume_adjoint_pair": (ct.c_int, [_vp, _vp, _vp, _vp, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp, _vp]),
     "mer_image_loss": (ct.c_int, [ct.c_int32, ct.c_int64, _vp, _vp, _vp, _vp, _vp]),
+    "mer_volume_opt_create": (ct.c_int, [_vp, ct.POINTER(Hyper), ct.c_int32, ct.c_int32, ct.c_int32, _fp, _fp, _vp,
+                                         _vp, ct.POINTER(_vp)]),
+    "mer_volume_opt_destroy": (None, [_vp]),
+    "mer_volume_opt_set_params": (ct.c_int, [_vp, _vp]),
+    "mer_volume_opt_iterate": (ct.c_int, [_vp, ct.c_int32, ct.c_int32, _vp]),
+    "mer_volume_opt_stats": (ct.c_int, [_vp, ct.POINTER(IterStats)]),
+    "mer_volume_opt_state": (ct.c_int, [_vp, ct.POINTER(StateView)]),
+    "mer_volume_opt_launches": (ct.c_int, [_vp, ct.POINTER(ct.c_int32)]),
     "mer_target_set": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_target_render": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_render": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp]),

@@ -383,6 +383,73 @@ class Volume:
         return g
 
 
+class VolumeOptimizer:
+    """mer_volume_opt_*: the meta-estimator (or Adam) fitting a Volume's voxels to target images,
+    every iteration on the device (one captured graph with use_graph=True)."""
+
+    def __init__(self, vol: Volume, target, init, hyper: HyperParams = None, loss: int = LOSS_L2, spp_f: int = 1,
+                 spp_d: int = 1, lo=(0.0, 0.0, 0.0, 0.0), hi=(4.0, 4.0, 4.0, 60.0)):
+        self.L = vol.L
+        self.vol = vol                          # kept alive: the optimiser borrows its description
+        self.device = vol.device
+        hyper = hyper or HyperParams()
+        t = _dev_f32(target, self.device)
+        p = _dev_f32(init, self.device)
+        lo_a = (ct.c_float * 4)(*[float(x) for x in lo])
+        hi_a = (ct.c_float * 4)(*[float(x) for x in hi])
+        h = hyper.to_c()
+        out = ct.c_void_p()
+        check(self.L.mer_volume_opt_create(vol.h, ct.byref(h), loss, spp_f, spp_d, lo_a, hi_a, _ptr(t), _ptr(p),
+                                           ct.byref(out)))
+        self.h = out
+        self.shape = vol.shape
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mer_volume_opt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        check(self.L.mer_volume_opt_set_params(self.h, _ptr(_dev_f32(params, self.device))))
+
+    def iterate(self, n: int = 1, use_graph: bool = True):
+        check(self.L.mer_volume_opt_iterate(self.h, n, int(use_graph), _cur_stream(self.device)))
+
+    def stats(self) -> dict:
+        s = _lib.IterStats()
+        check(self.L.mer_volume_opt_stats(self.h, ct.byref(s)))
+        return dict(iteration=s.iteration, loss=s.loss, dpi_norm2=s.dpi_norm2, count_f=s.count_f,
+                    count_d=s.count_d, marches_per_iter=s.paths_per_iter)
+
+    def launches(self) -> int:
+        n = ct.c_int32()
+        check(self.L.mer_volume_opt_launches(self.h, ct.byref(n)))
+        return n.value
+
+    def state(self) -> dict:
+        """Copies of the optimiser's arrays (voxel-shaped)."""
+        v = _lib.StateView()
+        check(self.L.mer_volume_opt_state(self.h, ct.byref(v)))
+        out = {}
+        for name in ("pi_cur", "pi_prev", "F", "dF", "m2f", "m2d", "mean", "var", "alpha_prev",
+                     "mu_f", "mu_d", "adam_m", "adam_v", "F_var", "dF_var"):
+            addr = ct.cast(getattr(v, name), ct.c_void_p).value
+            if not addr:
+                continue
+            t = torch.empty(self.shape, device=self.device, dtype=torch.float32)
+            _memcpy_d2d(t, addr, v.n * 4)
+            out[name] = t
+        return out
+
+    def params(self) -> torch.Tensor:
+        return self.state()["pi_cur"]
+
 def image_loss(img: torch.Tensor, target: torch.Tensor, kind: int = 0):
     """(loss device double tensor, dLoss/dimg) of an RGB image (mer_image_loss)."""
     L = _lib.load()

@@ -139,31 +139,68 @@ __device__ __forceinline__ v3 vol_march(const VolDev& V, const float4* __restric
     return L + mk(V.bg[0], V.bg[1], V.bg[2]) * T;
 }
 
-__global__ void __launch_bounds__(256) k_vol_render(VolDev V, const float4* __restrict__ par, int spp, uint32_t stream,
-                                                    uint32_t iter, float* img) {
+// The parameter vectors and iteration of a launch: given explicitly, or (ps != nullptr) the
+// optimiser's two slots, pi_i = slot[ps->cur] and pi_{i-1} = the other, at iteration ps->iteration,
+// read on the device so that one captured graph serves every iteration.
+struct VolSel {
+    const float4* a;
+    const float4* b;            // second vector of a pair, or nullptr
+    const float4* slot[2];
+    const ProbState* ps;
+    uint32_t iter;
+    int32_t pair;
+};
+
+__device__ __forceinline__ void vol_resolve(const VolSel& S, const float4*& a, const float4*& b, uint32_t& iter) {
+    if (S.ps) {
+        const int c = S.ps->cur & 1;
+        a = S.slot[c];
+        b = S.pair ? S.slot[c ^ 1] : nullptr;
+        iter = (uint32_t)S.ps->iteration;
+    } else {
+        a = S.a;
+        b = S.b;
+        iter = S.iter;
+    }
+}
+
+// one thread per pixel, spp samples; with a pair the same rays are marched through both vectors
+__global__ void __launch_bounds__(256) k_vol_render(VolDev V, VolSel S, int spp, uint32_t stream, float* imgA,
+                                                    float* imgB) {
+    const float4 *pa, *pb;
+    uint32_t iter;
+    vol_resolve(S, pa, pb, iter);
     const int64_t N = (int64_t)V.views * V.width * V.height;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float inv = 1.0f / (float)spp;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += stride) {
-        v3 acc = mk(0, 0, 0);
+        v3 acc = mk(0, 0, 0), accB = mk(0, 0, 0);
         for (int s = 0; s < spp; ++s) {
             v3 o, d;
             float u;
             vol_ray(V, (uint32_t)p, (uint32_t)s, iter, stream, o, d, u);
-            acc = acc + vol_march<0>(V, par, o, d, u, mk(0, 0, 0), mk(0, 0, 0), 0.0f, nullptr);
+            acc = acc + vol_march<0>(V, pa, o, d, u, mk(0, 0, 0), mk(0, 0, 0), 0.0f, nullptr);
+            if (pb) accB = accB + vol_march<0>(V, pb, o, d, u, mk(0, 0, 0), mk(0, 0, 0), 0.0f, nullptr);
         }
-        const float inv = 1.0f / (float)spp;
-        img[3 * p + 0] = acc.x * inv;
-        img[3 * p + 1] = acc.y * inv;
-        img[3 * p + 2] = acc.z * inv;
+        imgA[3 * p + 0] = acc.x * inv;
+        imgA[3 * p + 1] = acc.y * inv;
+        imgA[3 * p + 2] = acc.z * inv;
+        if (pb) {
+            imgB[3 * p + 0] = accB.x * inv;
+            imgB[3 * p + 1] = accB.y * inv;
+            imgB[3 * p + 2] = accB.z * inv;
+        }
     }
 }
 
-// one thread per (pixel, sample): radiance pass(es), then the replay(s); with parB the pair's
-// second branch is subtracted (same counters at the second parameter vector)
-__global__ void __launch_bounds__(256) k_vol_adjoint(VolDev V, const float4* __restrict__ parA,
-                                                     const float4* __restrict__ parB, const float* __restrict__ dA,
+// one thread per (pixel, sample): radiance pass(es), then the replay(s); with a pair the second
+// branch is subtracted (same counters at the second parameter vector)
+__global__ void __launch_bounds__(256) k_vol_adjoint(VolDev V, VolSel S, const float* __restrict__ dA,
                                                      const float* __restrict__ dB, int spp, uint32_t stream,
-                                                     uint32_t iter, float4* grad) {
+                                                     float4* grad) {
+    const float4 *parA, *parB;
+    uint32_t iter;
+    vol_resolve(S, parA, parB, iter);
     const int64_t N = (int64_t)V.views * V.width * V.height;
     const int64_t total = N * spp;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -198,6 +235,7 @@ __global__ void __launch_bounds__(256) k_image_loss(int kind, int64_t n_pix, con
         dimg[i] = sc * r * w;
         l += (double)r * (double)r * (double)w;
     }
+    if (!loss) return;
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, l / (3.0 * (double)n_pix));
 }
@@ -293,8 +331,10 @@ extern "C" mer_status mer_volume_render(mer_volume* v, const float* params, int3
         return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_render");
     cudaSetDevice(v->device);
     const int64_t N = (int64_t)v->dev.views * v->dev.width * v->dev.height;
-    k_vol_render<<<vol_grid(N), 256, 0, (cudaStream_t)cuda_stream>>>(v->dev, reinterpret_cast<const float4*>(params), spp,
-                                                                        stream, iteration, img);
+    VolSel S{};
+    S.a = reinterpret_cast<const float4*>(params);
+    S.iter = iteration;
+    k_vol_render<<<vol_grid(N), 256, 0, (cudaStream_t)cuda_stream>>>(v->dev, S, spp, stream, img, nullptr);
     const cudaError_t e = cudaGetLastError();
     return e ? mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e)) : MER_OK;
 }
@@ -305,9 +345,12 @@ static mer_status vol_adjoint(mer_volume* v, const float* pA, const float* pB, c
         return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_adjoint");
     cudaSetDevice(v->device);
     const int64_t N = (int64_t)v->dev.views * v->dev.width * v->dev.height;
-    k_vol_adjoint<<<vol_grid(N * spp), 256, 0, (cudaStream_t)cuda_stream>>>(
-        v->dev, reinterpret_cast<const float4*>(pA), reinterpret_cast<const float4*>(pB), dA, dB, spp, stream, iteration,
-        reinterpret_cast<float4*>(grad));
+    VolSel S{};
+    S.a = reinterpret_cast<const float4*>(pA);
+    S.b = reinterpret_cast<const float4*>(pB);
+    S.iter = iteration;
+    k_vol_adjoint<<<vol_grid(N * spp), 256, 0, (cudaStream_t)cuda_stream>>>(v->dev, S, dA, dB, spp, stream,
+                                                                             reinterpret_cast<float4*>(grad));
     const cudaError_t e = cudaGetLastError();
     return e ? mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e)) : MER_OK;
 }
@@ -333,4 +376,324 @@ extern "C" mer_status mer_image_loss(int32_t kind, int64_t n_pix, const float* i
     k_image_loss<<<vol_grid(3 * n_pix), 256, 0, st>>>(kind, n_pix, img, target, dimg, loss);
     const cudaError_t e = cudaGetLastError();
     return e ? mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e)) : MER_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Optimiser of a volume's voxels toward target images (mer_volume_opt_*). One iteration, all
+// on the device and capturable as one graph:
+//   branch 1 (proportional <F>): render pi_i (PROP_PRIMAL), loss adjoint, replay (PROP_ADJ) into F;
+//   branch 2 (META, FD <dF>):   render pi_i and pi_{i-1} on the same rays (FD_PRIMAL), both loss
+//                                adjoints, paired replay (FD_ADJ) into dF;
+//   UNCORRELATED: each branch repeats itself on streams + MER_STREAM_VAR_OFFSET into F_var, dF_var;
+//   then the fused update of the texture problems (one segment, C = 4) with its finalize, which
+//   advances the iteration, swaps the slots and computes the next coefficients on the device.
+// ---------------------------------------------------------------------------------------
+
+struct mer_volume_opt {
+    mer_volume* vol = nullptr;
+    int device = 0;
+    mer_hyper h{};
+    int32_t loss_kind = 0, spp_f = 1, spp_d = 1;
+    bool meta = true;
+    int64_t n = 0, n_pix = 0;
+    float* slot[2] = {nullptr, nullptr};
+    float *F = nullptr, *dF = nullptr, *m2f = nullptr, *m2d = nullptr, *mean = nullptr, *var = nullptr, *ap = nullptr;
+    float *mu_f = nullptr, *mu_d = nullptr, *am = nullptr, *av = nullptr, *Fv = nullptr, *dFv = nullptr;
+    float *target = nullptr, *imgP = nullptr, *dP = nullptr, *imgA = nullptr, *imgB = nullptr, *dA = nullptr,
+          *dB = nullptr;
+    ProbState* d_ps = nullptr;
+    UpdSeg* d_seg = nullptr;
+    int64_t* d_blk_off = nullptr;
+    double* d_partials = nullptr;
+    int64_t nblocks = 0;
+    cudaStream_t st = nullptr, st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int launches = 0;
+    std::vector<void*> allocs;
+};
+
+static cudaError_t vopt_alloc(mer_volume_opt* o, float** p, int64_t n) {
+    const cudaError_t e = cudaMalloc(p, sizeof(float) * (size_t)std::max<int64_t>(n, 1));
+    if (!e) o->allocs.push_back(*p);
+    return e;
+}
+
+static void vopt_free(mer_volume_opt* o) {
+    cudaSetDevice(o->device);
+    if (o->gexec) cudaGraphExecDestroy(o->gexec);
+    for (void* a : o->allocs) cudaFree(a);
+    cudaFree(o->d_ps);
+    cudaFree(o->d_seg);
+    cudaFree(o->d_blk_off);
+    cudaFree(o->d_partials);
+    for (cudaEvent_t e : {o->ev_fork, o->ev_join, o->ev_in, o->ev_out})
+        if (e) cudaEventDestroy(e);
+    if (o->st) cudaStreamDestroy(o->st);
+    if (o->st2) cudaStreamDestroy(o->st2);
+    delete o;
+}
+
+static VolSel vopt_sel(const mer_volume_opt* o, int pair) {
+    VolSel S{};
+    S.slot[0] = reinterpret_cast<const float4*>(o->slot[0]);
+    S.slot[1] = reinterpret_cast<const float4*>(o->slot[1]);
+    S.ps = o->d_ps;
+    S.pair = pair;
+    return S;
+}
+
+// one branch: (pair ? FD : proportional) sample of the current iteration into grad (cleared first)
+static int vopt_branch(mer_volume_opt* o, int pair, uint32_t soff, float* grad, double* loss, cudaStream_t s) {
+    const VolDev& V = o->vol->dev;
+    const int spp = pair ? o->spp_d : o->spp_f;
+    const uint32_t sp = (pair ? MER_STREAM_FD_PRIMAL : MER_STREAM_PROP_PRIMAL) + soff;
+    const uint32_t sa = (pair ? MER_STREAM_FD_ADJ : MER_STREAM_PROP_ADJ) + soff;
+    const VolSel S = vopt_sel(o, pair);
+    const int g3 = vol_grid(3 * o->n_pix);
+    cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)o->n, s);
+    if (pair) {
+        k_vol_render<<<vol_grid(o->n_pix), 256, 0, s>>>(V, S, spp, sp, o->imgA, o->imgB);
+        k_image_loss<<<g3, 256, 0, s>>>(o->loss_kind, o->n_pix, o->imgA, o->target, o->dA, nullptr);
+        k_image_loss<<<g3, 256, 0, s>>>(o->loss_kind, o->n_pix, o->imgB, o->target, o->dB, nullptr);
+        k_vol_adjoint<<<vol_grid(o->n_pix * spp), 256, 0, s>>>(V, S, o->dA, o->dB, spp, sa,
+                                                                reinterpret_cast<float4*>(grad));
+        return 4;
+    }
+    if (loss) cudaMemsetAsync(loss, 0, sizeof(double), s);
+    k_vol_render<<<vol_grid(o->n_pix), 256, 0, s>>>(V, S, spp, sp, o->imgP, nullptr);
+    k_image_loss<<<g3, 256, 0, s>>>(o->loss_kind, o->n_pix, o->imgP, o->target, o->dP, loss);
+    k_vol_adjoint<<<vol_grid(o->n_pix * spp), 256, 0, s>>>(V, S, o->dP, nullptr, spp, sa,
+                                                            reinterpret_cast<float4*>(grad));
+    return 3;
+}
+
+static int vopt_enqueue(mer_volume_opt* o) {
+    int n = 0;
+    const bool unc = o->meta && (o->h.flags & MER_META_UNCORRELATED);
+    if (o->meta) {
+        cudaEventRecord(o->ev_fork, o->st);
+        cudaStreamWaitEvent(o->st2, o->ev_fork, 0);
+        n += vopt_branch(o, 1, 0, o->dF, nullptr, o->st2);
+        if (unc) n += vopt_branch(o, 1, MER_STREAM_VAR_OFFSET, o->dFv, nullptr, o->st2);
+        cudaEventRecord(o->ev_join, o->st2);
+    }
+    n += vopt_branch(o, 0, 0, o->F, &o->d_ps->loss, o->st);
+    if (unc) n += vopt_branch(o, 0, MER_STREAM_VAR_OFFSET, o->Fv, nullptr, o->st);
+    if (o->meta) cudaStreamWaitEvent(o->st, o->ev_join, 0);
+    if (g_timer) g_timer->add_units(KC_UPDATE, o->n);
+    launch_update_ctx(o->d_seg, o->d_blk_off, 1, o->nblocks, o->d_ps, o->d_partials, o->st);
+    return n + 2;
+}
+
+static mer_status vopt_reset(mer_volume_opt* o, const float* params) {
+    const size_t nb = sizeof(float) * (size_t)o->n;
+    cudaError_t e = cudaMemcpyAsync(o->slot[0], params, nb, cudaMemcpyDeviceToDevice, o->st);
+    if (!e) e = cudaMemcpyAsync(o->slot[1], params, nb, cudaMemcpyDeviceToDevice, o->st);
+    for (float* a : {o->F, o->dF, o->m2f, o->m2d, o->mean, o->var, o->mu_f, o->mu_d, o->am, o->av, o->Fv, o->dFv})
+        if (!e && a) e = cudaMemsetAsync(a, 0, nb, o->st);
+    if (!e) run_fill(o->ap, o->n, -INFINITY, o->st);
+    ProbState ps{};
+    ps.coef = update_coef(o->h, 0, 0, 0, 0.0);
+    if (!e) e = cudaMemcpyAsync(o->d_ps, &ps, sizeof ps, cudaMemcpyHostToDevice, o->st);
+    if (!e) e = cudaStreamSynchronize(o->st);
+    return e ? mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e)) : MER_OK;
+}
+
+extern "C" mer_status mer_volume_opt_create(mer_volume* vol, const mer_hyper* hyper, int32_t loss_kind, int32_t spp_f,
+                                            int32_t spp_d, const float* lo, const float* hi, const float* target,
+                                            const float* init, mer_volume_opt** out) {
+    if (!vol || !hyper || !lo || !hi || !target || !init || !out || !aligned16(init))
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_opt_create");
+    if (hyper->mode != MER_MODE_META && hyper->mode != MER_MODE_ADAM)
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "unknown optimiser mode");
+    if (hyper->flags & ~127) return mer_internal_fail(MER_ERR_INVALID_ARG, "unknown MER_META_* flag bits");
+    if (hyper->precond_lambda != 0.0f)
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "gradient preconditioning applies to textures only");
+    if (loss_kind != MER_LOSS_L2 && loss_kind != MER_LOSS_MRSE)
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "unknown loss kind");
+    if (spp_f < 1 || (hyper->mode == MER_MODE_META && spp_d < 1))
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "samples per pixel must be >= 1");
+    for (int k = 0; k < 4; ++k)
+        if (!(lo[k] <= hi[k])) return mer_internal_fail(MER_ERR_INVALID_ARG, "clamp range lo > hi");
+    if (cudaSetDevice(vol->device) != cudaSuccess) return mer_internal_fail(MER_ERR_CUDA, "bad device");
+    mer_volume_opt* o = new mer_volume_opt();
+    o->vol = vol;
+    o->device = vol->device;
+    o->h = *hyper;
+    o->meta = hyper->mode == MER_MODE_META;
+    o->loss_kind = loss_kind;
+    o->spp_f = spp_f;
+    o->spp_d = o->meta ? spp_d : 0;
+    o->n = 4 * vol->n_vox;
+    o->n_pix = (int64_t)vol->dev.views * vol->dev.width * vol->dev.height;
+    const int fl = o->meta ? hyper->flags : 0;
+    cudaError_t e = cudaStreamCreateWithFlags(&o->st, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamCreateWithFlags(&o->st2, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&o->ev_fork, &o->ev_join, &o->ev_in, &o->ev_out})
+        if (!e) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (float** a : {&o->slot[0], &o->slot[1], &o->F, &o->m2f, &o->mean, &o->ap})
+        if (!e) e = vopt_alloc(o, a, o->n);
+    if (o->meta)
+        for (float** a : {&o->dF, &o->m2d, &o->var})
+            if (!e) e = vopt_alloc(o, a, o->n);
+    if (fl & MER_META_CENTRED)
+        for (float** a : {&o->mu_f, &o->mu_d})
+            if (!e) e = vopt_alloc(o, a, o->n);
+    if (fl & MER_META_NAIVE_ADAM)
+        for (float** a : {&o->am, &o->av})
+            if (!e) e = vopt_alloc(o, a, o->n);
+    if (fl & MER_META_UNCORRELATED)
+        for (float** a : {&o->Fv, &o->dFv})
+            if (!e) e = vopt_alloc(o, a, o->n);
+    for (float** a : {&o->target, &o->imgP, &o->dP, &o->imgA, &o->imgB, &o->dA, &o->dB})
+        if (!e) e = vopt_alloc(o, a, 3 * o->n_pix);
+    o->nblocks = update_blocks_for(o->n);
+    if (!e) e = cudaMalloc(&o->d_ps, sizeof(ProbState));
+    if (!e) e = cudaMalloc(&o->d_seg, sizeof(UpdSeg));
+    if (!e) e = cudaMalloc(&o->d_blk_off, 2 * sizeof(int64_t));
+    if (!e) e = cudaMalloc(&o->d_partials, sizeof(double) * (size_t)std::max<int64_t>(1, o->nblocks));
+    if (e) {
+        vopt_free(o);
+        return mer_internal_fail(e == cudaErrorMemoryAllocation ? MER_ERR_OOM : MER_ERR_CUDA, cudaGetErrorString(e));
+    }
+    UpdSeg S;
+    memset(&S, 0, sizeof S);
+    S.pA = o->slot[0];
+    S.pB = o->slot[1];
+    S.F = o->F;
+    S.dF = o->dF;
+    S.m2f = o->m2f;
+    S.m2d = o->m2d;
+    S.mean = o->mean;
+    S.var = o->var;
+    S.ap = o->ap;
+    S.mu_f = o->mu_f;
+    S.mu_d = o->mu_d;
+    S.am = o->am;
+    S.av = o->av;
+    S.Fv = o->Fv;
+    S.dFv = o->dFv;
+    S.n = o->n;
+    S.C = 4;
+    S.prob = 0;
+    S.zero_grads = 0;        // each branch clears its gradient before its replay
+    for (int k = 0; k < 8; ++k) {
+        S.lo[k] = k < 4 ? lo[k] : 0.0f;
+        S.hi[k] = k < 4 ? hi[k] : 0.0f;
+    }
+    S.hyper = o->h;
+    S.hyper.flags = fl;
+    o->h.flags = fl;
+    const int64_t boff[2] = {0, o->nblocks};
+    e = cudaMemcpy(o->d_seg, &S, sizeof S, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(o->d_blk_off, boff, sizeof boff, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(o->target, target, sizeof(float) * 3 * (size_t)o->n_pix, cudaMemcpyDeviceToDevice);
+    if (e) {
+        vopt_free(o);
+        return mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e));
+    }
+    const mer_status s = vopt_reset(o, init);
+    if (s) {
+        vopt_free(o);
+        return s;
+    }
+    *out = o;
+    return MER_OK;
+}
+
+extern "C" void mer_volume_opt_destroy(mer_volume_opt* o) {
+    if (!o) return;
+    cudaStreamSynchronize(o->st);
+    vopt_free(o);
+}
+
+extern "C" mer_status mer_volume_opt_set_params(mer_volume_opt* o, const float* params) {
+    if (!o || !params || !aligned16(params)) return mer_internal_fail(MER_ERR_INVALID_ARG, "bad parameters");
+    cudaSetDevice(o->device);
+    return vopt_reset(o, params);
+}
+
+extern "C" mer_status mer_volume_opt_iterate(mer_volume_opt* o, int32_t n_iters, int32_t use_graph,
+                                             void* cuda_stream) {
+    if (!o || n_iters < 0) return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_opt_iterate");
+    cudaSetDevice(o->device);
+    const cudaStream_t user = (cudaStream_t)cuda_stream;
+    cudaEventRecord(o->ev_in, user);
+    cudaStreamWaitEvent(o->st, o->ev_in, 0);
+    cudaError_t e = cudaSuccess;
+    if (!use_graph) {
+        for (int i = 0; i < n_iters; ++i) o->launches = vopt_enqueue(o);
+        e = cudaGetLastError();
+    } else {
+        if (!o->gexec) {
+            cudaGraph_t graph = nullptr;
+            KernelTimer* saved = g_timer;
+            g_timer = nullptr;   // no event timing inside a captured graph
+            e = cudaStreamBeginCapture(o->st, cudaStreamCaptureModeThreadLocal);
+            if (!e) {
+                const int n = vopt_enqueue(o);
+                e = cudaStreamEndCapture(o->st, &graph);
+                if (!e) e = cudaGraphInstantiate(&o->gexec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (!e) o->launches = n;
+            }
+            g_timer = saved;
+        }
+        for (int i = 0; i < n_iters && !e; ++i) e = cudaGraphLaunch(o->gexec, o->st);
+    }
+    cudaEventRecord(o->ev_out, o->st);
+    cudaStreamWaitEvent(user, o->ev_out, 0);
+    return e ? mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e)) : MER_OK;
+}
+
+extern "C" mer_status mer_volume_opt_stats(mer_volume_opt* o, mer_iter_stats* out) {
+    if (!o || !out) return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_opt_stats");
+    cudaSetDevice(o->device);
+    ProbState ps;
+    cudaError_t e = cudaMemcpyAsync(&ps, o->d_ps, sizeof ps, cudaMemcpyDeviceToHost, o->st);
+    if (!e) e = cudaStreamSynchronize(o->st);
+    if (e) return mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e));
+    out->iteration = ps.iteration;
+    out->loss = ps.loss;
+    out->dpi_norm2 = ps.dpi_norm2;
+    out->count_f = ps.count_f;
+    out->count_d = ps.count_d;
+    // ray marches: render + radiance/replay pair per proportional sample, twice that per FD sample
+    const int64_t per = o->n_pix * (3 * (int64_t)o->spp_f + 6 * (int64_t)o->spp_d);
+    out->paths_per_iter = (o->meta && (o->h.flags & MER_META_UNCORRELATED)) ? 2 * per : per;
+    return MER_OK;
+}
+
+extern "C" mer_status mer_volume_opt_state(mer_volume_opt* o, mer_state_view* out) {
+    if (!o || !out) return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_opt_state");
+    cudaSetDevice(o->device);
+    int32_t cur = 0;
+    cudaError_t e = cudaMemcpyAsync(&cur, &o->d_ps->cur, sizeof cur, cudaMemcpyDeviceToHost, o->st);
+    if (!e) e = cudaStreamSynchronize(o->st);
+    if (e) return mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e));
+    memset(out, 0, sizeof *out);
+    out->pi_cur = o->slot[cur & 1];
+    out->pi_prev = o->slot[(cur & 1) ^ 1];
+    out->F = o->F;
+    out->dF = o->dF;
+    out->m2f = o->m2f;
+    out->m2d = o->m2d;
+    out->mean = o->mean;
+    out->var = o->var;
+    out->alpha_prev = o->ap;
+    out->mu_f = o->mu_f;
+    out->mu_d = o->mu_d;
+    out->adam_m = o->am;
+    out->adam_v = o->av;
+    out->F_var = o->Fv;
+    out->dF_var = o->dFv;
+    out->n = o->n;
+    return MER_OK;
+}
+
+extern "C" mer_status mer_volume_opt_launches(mer_volume_opt* o, int32_t* out) {
+    if (!o || !out) return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_opt_launches");
+    *out = o->launches;
+    return MER_OK;
 }
