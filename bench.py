@@ -67,6 +67,8 @@ def parse(argv=None):
                     help="add the statistical validation along prescribed trajectories (1000 runs, two schedules)")
     ap.add_argument("--scale-image", type=int, default=1024, help="image side of the scale leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-volume", action="store_true", help="skip the 256^3 volume leg")
+    ap.add_argument("--only-volume", action="store_true", help="run only the volume leg (for profiling)")
     return ap.parse_args(argv)
 
 
@@ -462,6 +464,63 @@ def update_roofline(torch, hbm_peak, n=67_108_864, reps=10):
             "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
 
 
+def volume_leg(torch, iters=400, lr=0.1, warm=3, timed=20, frac=0.005):
+    """The 256^3 emissive-absorptive volume (67.1M parameters, four 256^2 views, 1 + 1 spp): kernel
+    times, graph-launched iteration times of the meta-estimator and of Adam, and their loss curves at
+    equal iterations (evaluation renders at 4 spp on an independent stream). The volume (268 MB per
+    parameter array) is larger than L2, so every launch streams it."""
+    from paper_2309_15676_gb300 import synth
+    from paper_2309_15676_gb300.api import (MODE_ADAM, MODE_META, STREAM_EVAL, STREAM_TARGET, HyperParams, Volume,
+                                             VolumeOptimizer, image_loss)
+    w = synth.workload_volume()
+    v = Volume(w.scene)
+    tp = torch.from_numpy(w.target_tex).cuda()
+    ip = torch.from_numpy(w.init_tex).cuda()
+    target = v.render(tp, spp=16, stream=STREAM_TARGET).clone()
+    img = v.render(ip)
+    _, d = image_loss(img, target)
+    g = torch.zeros_like(ip)
+
+    def ev_ms(fn, reps=5):
+        fn()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s0.record()
+        for _ in range(reps):
+            fn()
+        s1.record()
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / reps
+
+    kernels = {"render_1spp": ev_ms(lambda: v.render(ip)), "adjoint_1spp": ev_ms(lambda: v.adjoint(ip, d, grad=g)),
+               "adjoint_pair_1spp": ev_ms(lambda: v.adjoint_pair(ip, tp, d, d, grad=g)),
+               "image_loss": ev_ms(lambda: image_loss(img, target))}
+    l0 = float(image_loss(v.render(ip, spp=4, stream=STREAM_EVAL), target)[0].item())
+    out = {"workload": "volume256: 256^3 x 4 voxels (67.1M parameters), 4 views of 256^2, step one voxel, "
+                       "1 proportional + 1 FD spp", "kernels_ms": kernels, "init_loss": l0}
+    for name, mode in (("meta", MODE_META), ("adam", MODE_ADAM)):
+        o = VolumeOptimizer(v, target, ip, HyperParams(lr=lr, mode=mode))
+        o.iterate(warm, use_graph=True)
+        ms = ev_ms(lambda: o.iterate(1, use_graph=True), reps=timed)
+        st = o.stats()
+        o.set_params(ip)
+        curve, hit = [], None
+        for k in range(iters // 50):
+            o.iterate(50, use_graph=True)
+            lk = float(image_loss(v.render(o.params(), spp=4, stream=STREAM_EVAL), target)[0].item())
+            curve.append(lk)
+            if hit is None and lk <= frac * l0:
+                hit = 50 * (k + 1)
+        out[name] = {"lr": lr, "ms_per_iter": ms, "marches_per_iter": st["marches_per_iter"],
+                     "marches_per_s": st["marches_per_iter"] / (ms * 1e-3), "launches_per_iter": o.launches(),
+                     "loss_every_50": curve,
+                     "iters_to_threshold": hit, "seconds_to_threshold": None if hit is None else hit * ms * 1e-3}
+        o.close()
+    out["threshold"] = f"{frac} x initial loss"
+    v.close()
+    return out
+
+
 def run_mine(args):
     import numpy as np
     import torch
@@ -480,6 +539,9 @@ def run_mine(args):
     hbm_peak, peak_kind, sm_max = measured_peaks()
     if args.only_scale:
         print(json.dumps({"scale": scale_profile(torch, hbm_peak, args.scale_image)}), flush=True)
+        return 0
+    if args.only_volume:
+        print(json.dumps({"volume": volume_leg(torch)}), flush=True)
         return 0
 
     w = workload()
@@ -621,6 +683,7 @@ def run_mine(args):
         validation = {kind: trajectory_study(runs=1000, iters=100, schedule=kind) for kind in ("linear", "exponential")}
     batched = batched_compare(torch) if (rank == 0 and not args.no_batch) else None
     scale = scale_profile(torch, hbm_peak, args.scale_image) if (rank == 0 and not args.no_scale) else None
+    volume = volume_leg(torch) if (rank == 0 and not args.no_volume) else None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(w)
     if rank == 0:
@@ -636,7 +699,8 @@ def run_mine(args):
                 "kernels": kernels, "peak_source": peak_kind,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                 "gpu_launches": int(launches_per_iter * args.steps), "launch_shapes": tuned,
-                "time_to_threshold": ttt, "batched": batched, "scale": scale, "validation": validation}
+                "time_to_threshold": ttt, "batched": batched, "scale": scale, "volume": volume,
+                "validation": validation}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -99,44 +99,91 @@ __device__ __forceinline__ void vol_ray(const VolDev& V, uint32_t pixel, uint32_
     u = u01(draw(V.seed, V.key_id, pixel, sample, iter, stream, 1, 0).x);
 }
 
-// mode 0: radiance; mode 1: replay adding sg * dLoss/dparams into grad (sg = +1 or -1)
-template <int MODE>
-__device__ __forceinline__ v3 vol_march(const VolDev& V, const float4* __restrict__ par, v3 o, v3 d, float u, v3 Ltot,
-                                        v3 adj, float sg, float4* grad) {
+// Per-step record of the adjoint's radiance pass: sigma_k and adj . e_k, one float2 plane
+// [max_steps][slots] per branch
+// Radiance of one parameter vector along one ray. With REC, step k (k < max_steps) also stores
+// sigma_k and adj . e_k at rec[k * slots] (the caller offsets rec by its thread slot) and the march
+// stops after max_steps; returns the step count.
+template <bool REC>
+__device__ __forceinline__ int vol_march(const VolDev& V, const float4* __restrict__ par, v3 o, v3 d, float u, v3& Lout,
+                                         v3 adj = v3{}, float2* rec = nullptr, int64_t slots = 0, int max_steps = 0) {
     v3 L = mk(0, 0, 0);
     float T = 1.0f;
     float t0, t1;
+    int k = 0;
     if (vol_box(V, o, d, t0, t1)) {
         const float dl = V.step;
-        for (int k = 0;; ++k) {
+        for (;; ++k) {
+            if (REC && k >= max_steps) break;
             const float t = t0 + ((float)k + u) * dl;
             if (!(t < t1)) break;
             Taps tp;
             vol_taps(V, o + d * t, tp);
-            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, s = 0.0f;
+            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f, sd = 0.0f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const float4 q = __ldg(par + tp.idx[c]);
                 e0 = fmaf(tp.w[c], q.x, e0);
                 e1 = fmaf(tp.w[c], q.y, e1);
                 e2 = fmaf(tp.w[c], q.z, e2);
-                s = fmaf(tp.w[c], q.w, s);
+                sd = fmaf(tp.w[c], q.w, sd);
             }
-            const float tr = expf(-s * dl), a = 1.0f - tr;
+            const float tr = expf(-sd * dl), a = 1.0f - tr;
             L = L + mk(e0, e1, e2) * (T * a);
-            if (MODE == 1) {
-                const float ta = T * a;
-                const float ge0 = sg * adj.x * ta, ge1 = sg * adj.y * ta, ge2 = sg * adj.z * ta;
-                const float gs = sg * dl * (adj.x * (tr * T * e0 - (Ltot.x - L.x)) + adj.y * (tr * T * e1 - (Ltot.y - L.y)) +
-                                            adj.z * (tr * T * e2 - (Ltot.z - L.z)));
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    red4(grad + tp.idx[c], tp.w[c] * ge0, tp.w[c] * ge1, tp.w[c] * ge2, tp.w[c] * gs);
-            }
             T *= tr;
+            if (REC) rec[(int64_t)k * slots] = make_float2(sd, adj.x * e0 + adj.y * e1 + adj.z * e2);
         }
     }
-    return L + mk(V.bg[0], V.bg[1], V.bg[2]) * T;
+    Lout = L + mk(V.bg[0], V.bg[1], V.bg[2]) * T;
+    return k;
+}
+
+// Replay of the first n steps of the ray from the radiance pass's records (no parameter reads):
+// with T_k, a_k = 1 - exp(-sigma_k delta) and the running s_k = sum_{i<=k} T_i a_i adj . e_i,
+//   dLoss/de_k = T_k a_k adj,   dLoss/dsigma_k = delta (exp(-sigma_k delta) T_k adj . e_k - (adjL - s_k)),
+// adjL = adj . (total radiance) per branch; branch 1 of a pair enters with sign -1. The branches'
+// sum goes to the eight taps by one vector reduction each. (Summing shared corners of consecutive
+// steps in registers first issues fewer reductions but diverges per lane and measured slower.)
+template <int NB>
+__device__ __forceinline__ void vol_replay(const VolDev& V, v3 o, v3 d, float u, int n, const float2* rec,
+                                           int64_t slots, int64_t plane, const v3* adj, const float* adjL,
+                                           float4* grad) {
+    float t0, t1;
+    if (n <= 0 || !vol_box(V, o, d, t0, t1)) return;
+    const float dl = V.step;
+    float T[NB], acc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        T[j] = 1.0f;
+        acc[j] = 0.0f;
+    }
+    for (int k = 0; k < n; ++k) {
+        const float t = t0 + ((float)k + u) * dl;
+        Taps tp;
+        vol_taps(V, o + d * t, tp);
+        float sd[NB], se[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const float2 r = rec[j * plane + (int64_t)k * slots];
+            sd[j] = r.x;
+            se[j] = r.y;
+        }
+        float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, g3 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const float sg = j == 0 ? 1.0f : -1.0f;
+            const float tr = expf(-sd[j] * dl), a = 1.0f - tr;
+            const float ta = T[j] * a;
+            acc[j] = fmaf(ta, se[j], acc[j]);
+            g0 = fmaf(sg * ta, adj[j].x, g0);
+            g1 = fmaf(sg * ta, adj[j].y, g1);
+            g2 = fmaf(sg * ta, adj[j].z, g2);
+            g3 = fmaf(sg * dl, tr * T[j] * se[j] - (adjL[j] - acc[j]), g3);
+            T[j] *= tr;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) red4(grad + tp.idx[c], tp.w[c] * g0, tp.w[c] * g1, tp.w[c] * g2, tp.w[c] * g3);
+    }
 }
 
 // The parameter vectors and iteration of a launch: given explicitly, or (ps != nullptr) the
@@ -164,61 +211,86 @@ __device__ __forceinline__ void vol_resolve(const VolSel& S, const float4*& a, c
     }
 }
 
-// one thread per pixel, spp samples; with a pair the same rays are marched through both vectors
+// one thread per pixel, spp samples; with a pair the same rays are marched through both vectors,
+// one after the other
+template <int NB>
 __global__ void __launch_bounds__(256) k_vol_render(VolDev V, VolSel S, int spp, uint32_t stream, float* imgA,
                                                     float* imgB) {
-    const float4 *pa, *pb;
+    const float4* par[2];
     uint32_t iter;
-    vol_resolve(S, pa, pb, iter);
+    vol_resolve(S, par[0], par[1], iter);
     const int64_t N = (int64_t)V.views * V.width * V.height;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float inv = 1.0f / (float)spp;
+    float* img[2] = {imgA, imgB};
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += stride) {
-        v3 acc = mk(0, 0, 0), accB = mk(0, 0, 0);
+        v3 acc[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) acc[j] = mk(0, 0, 0);
         for (int s = 0; s < spp; ++s) {
             v3 o, d;
             float u;
             vol_ray(V, (uint32_t)p, (uint32_t)s, iter, stream, o, d, u);
-            acc = acc + vol_march<0>(V, pa, o, d, u, mk(0, 0, 0), mk(0, 0, 0), 0.0f, nullptr);
-            if (pb) accB = accB + vol_march<0>(V, pb, o, d, u, mk(0, 0, 0), mk(0, 0, 0), 0.0f, nullptr);
+            v3 L;
+            vol_march<false>(V, par[0], o, d, u, L);
+            acc[0] = acc[0] + L;
+            if (NB == 2) {
+                vol_march<false>(V, par[1], o, d, u, L);
+                acc[NB - 1] = acc[NB - 1] + L;
+            }
         }
-        imgA[3 * p + 0] = acc.x * inv;
-        imgA[3 * p + 1] = acc.y * inv;
-        imgA[3 * p + 2] = acc.z * inv;
-        if (pb) {
-            imgB[3 * p + 0] = accB.x * inv;
-            imgB[3 * p + 1] = accB.y * inv;
-            imgB[3 * p + 2] = accB.z * inv;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            img[j][3 * p + 0] = acc[j].x * inv;
+            img[j][3 * p + 1] = acc[j].y * inv;
+            img[j][3 * p + 2] = acc[j].z * inv;
         }
     }
 }
 
-// one thread per (pixel, sample): radiance pass(es), then the replay(s); with a pair the second
-// branch is subtracted (same counters at the second parameter vector)
+// one thread per (pixel, sample): the radiance pass, recording each step, then the replay from the
+// records; with a pair (NB = 2) the second branch's radiance pass follows the first's (same
+// counters at the second parameter vector) and one replay handles both, the second subtracted.
+// Thread slot q owns records rec[j * plane + k * slots + q], plane = max_steps * slots.
+template <int NB>
 __global__ void __launch_bounds__(256) k_vol_adjoint(VolDev V, VolSel S, const float* __restrict__ dA,
                                                      const float* __restrict__ dB, int spp, uint32_t stream,
-                                                     float4* grad) {
-    const float4 *parA, *parB;
+                                                     float4* grad, float2* rec, int64_t slots, int max_steps) {
+    const float4* par[2];
     uint32_t iter;
-    vol_resolve(S, parA, parB, iter);
+    vol_resolve(S, par[0], par[1], iter);
     const int64_t N = (int64_t)V.views * V.width * V.height;
     const int64_t total = N * spp;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t plane = (int64_t)max_steps * slots;
     const float inv = 1.0f / (float)spp;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const float* dimg[2] = {dA, dB};
+    for (int64_t i = q; i < total; i += stride) {
         const int64_t p = i / spp;
         const uint32_t s = (uint32_t)(i - p * spp);
         v3 o, d;
         float u;
         vol_ray(V, (uint32_t)p, s, iter, stream, o, d, u);
-        const v3 adjA = mk(dA[3 * p] * inv, dA[3 * p + 1] * inv, dA[3 * p + 2] * inv);
-        const v3 LA = vol_march<0>(V, parA, o, d, u, mk(0, 0, 0), mk(0, 0, 0), 0.0f, nullptr);
-        vol_march<1>(V, parA, o, d, u, LA, adjA, 1.0f, grad);
-        if (parB) {
-            const v3 adjB = mk(dB[3 * p] * inv, dB[3 * p + 1] * inv, dB[3 * p + 2] * inv);
-            const v3 LB = vol_march<0>(V, parB, o, d, u, mk(0, 0, 0), mk(0, 0, 0), 0.0f, nullptr);
-            vol_march<1>(V, parB, o, d, u, LB, adjB, -1.0f, grad);
+        v3 adj[NB];
+        float adjL[NB];
+        int n = 0;
+#pragma unroll 1
+        for (int j = 0; j < NB; ++j) {      // not unrolled: one copy of the march, like the single kernel
+            const float* dj = j ? dimg[NB - 1] : dimg[0];
+            const v3 aj = mk(dj[3 * p] * inv, dj[3 * p + 1] * inv, dj[3 * p + 2] * inv);
+            v3 L;
+            n = vol_march<true>(V, j ? par[1] : par[0], o, d, u, L, aj, rec + j * plane + q, slots, max_steps);
+            const float al = aj.x * L.x + aj.y * L.y + aj.z * L.z;
+            if (j == 0) {
+                adj[0] = aj;
+                adjL[0] = al;
+            } else {
+                adj[NB - 1] = aj;
+                adjL[NB - 1] = al;
+            }
         }
+        vol_replay<NB>(V, o, d, u, n, rec + q, slots, plane, adj, adjL, grad);
     }
 }
 
@@ -249,6 +321,12 @@ struct mer_volume {
     VolDev dev{};
     VolCam* d_cams = nullptr;
     int64_t n_vox = 0;
+    int max_steps = 0;           // bound on the march steps of any ray through the box
+    // radiance-pass records of the adjoint (index 0: single, 1: pair), allocated on first use:
+    // one [max_steps][slots] float2 plane per branch, slots = the persistent grid's threads
+    void* rec[2] = {nullptr, nullptr};
+    int64_t rec_slots[2] = {0, 0};
+    int rec_blocks[2] = {0, 0};
 };
 
 extern "C" mer_status mer_volume_create(const mer_volume_desc* d, int32_t device, mer_volume** out) {
@@ -304,6 +382,17 @@ extern "C" mer_status mer_volume_create(const mer_volume_desc* d, int32_t device
     }
     V.cams = v->d_cams;
     v->n_vox = (int64_t)d->nx * d->ny * d->nz;
+    // steps k with t0 + (k + u) delta < t1 number at most floor((t1 - t0) / delta) + 1, and t1 - t0 is
+    // at most the box diagonal; one more for rounding
+    double diag2 = 0.0;
+    for (int k = 0; k < 3; ++k) diag2 += ((double)d->hi[k] - d->lo[k]) * ((double)d->hi[k] - d->lo[k]);
+    const double ms = std::floor(std::sqrt(diag2) / (double)d->step) + 2.0;
+    if (ms > 1e6) {
+        cudaFree(v->d_cams);
+        delete v;
+        return mer_internal_fail(MER_ERR_INVALID_ARG, "march step too small for the volume box");
+    }
+    v->max_steps = (int)ms;
     *out = v;
     return MER_OK;
 }
@@ -312,7 +401,45 @@ extern "C" void mer_volume_destroy(mer_volume* v) {
     if (!v) return;
     cudaSetDevice(v->device);
     cudaFree(v->d_cams);
+    cudaFree(v->rec[0]);
+    cudaFree(v->rec[1]);
     delete v;
+}
+
+// the adjoint's persistent grid (SMs x resident blocks) and its record buffer, for NB branches
+template <int NB>
+static cudaError_t vol_ensure_rec(mer_volume* v) {
+    const int i = NB - 1;
+    if (v->rec[i]) return cudaSuccess;
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vol_adjoint<NB>, 256, 0);
+    if (e) return e;
+    const int blocks = std::max(1, sms * std::max(occ, 1));
+    const int64_t slots = (int64_t)blocks * 256;
+    e = cudaMalloc(&v->rec[i], (size_t)NB * (size_t)slots * (size_t)v->max_steps * sizeof(float2));
+    if (e) {
+        v->rec[i] = nullptr;
+        return e;
+    }
+    v->rec_slots[i] = slots;
+    v->rec_blocks[i] = blocks;
+    return cudaSuccess;
+}
+
+template <int NB>
+static cudaError_t vol_launch_adjoint(mer_volume* v, const VolSel& S, const float* dA, const float* dB, int spp,
+                                      uint32_t stream, float* grad, cudaStream_t st) {
+    const cudaError_t e = vol_ensure_rec<NB>(v);
+    if (e) return e;
+    const int i = NB - 1;
+    const int64_t total = (int64_t)v->dev.views * v->dev.width * v->dev.height * spp;
+    const int blocks = (int)std::min<int64_t>(v->rec_blocks[i], (total + 255) / 256);
+    k_vol_adjoint<NB><<<std::max(blocks, 1), 256, 0, st>>>(v->dev, S, dA, dB, spp, stream, reinterpret_cast<float4*>(grad),
+                                                           static_cast<float2*>(v->rec[i]),
+                                                           v->rec_slots[i], v->max_steps);
+    return cudaGetLastError();
 }
 
 static int vol_grid(int64_t n) {
@@ -334,7 +461,7 @@ extern "C" mer_status mer_volume_render(mer_volume* v, const float* params, int3
     VolSel S{};
     S.a = reinterpret_cast<const float4*>(params);
     S.iter = iteration;
-    k_vol_render<<<vol_grid(N), 256, 0, (cudaStream_t)cuda_stream>>>(v->dev, S, spp, stream, img, nullptr);
+    k_vol_render<1><<<vol_grid(N), 256, 0, (cudaStream_t)cuda_stream>>>(v->dev, S, spp, stream, img, nullptr);
     const cudaError_t e = cudaGetLastError();
     return e ? mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e)) : MER_OK;
 }
@@ -344,14 +471,12 @@ static mer_status vol_adjoint(mer_volume* v, const float* pA, const float* pB, c
     if (!v || !pA || !dA || !grad || spp < 1 || !aligned16(pA) || !aligned16(grad) || (pB && (!dB || !aligned16(pB))))
         return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_adjoint");
     cudaSetDevice(v->device);
-    const int64_t N = (int64_t)v->dev.views * v->dev.width * v->dev.height;
     VolSel S{};
     S.a = reinterpret_cast<const float4*>(pA);
     S.b = reinterpret_cast<const float4*>(pB);
     S.iter = iteration;
-    k_vol_adjoint<<<vol_grid(N * spp), 256, 0, (cudaStream_t)cuda_stream>>>(v->dev, S, dA, dB, spp, stream,
-                                                                             reinterpret_cast<float4*>(grad));
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = pB ? vol_launch_adjoint<2>(v, S, dA, dB, spp, stream, grad, (cudaStream_t)cuda_stream)
+                             : vol_launch_adjoint<1>(v, S, dA, dB, spp, stream, grad, (cudaStream_t)cuda_stream);
     return e ? mer_internal_fail(MER_ERR_CUDA, cudaGetErrorString(e)) : MER_OK;
 }
 
@@ -453,18 +578,16 @@ static int vopt_branch(mer_volume_opt* o, int pair, uint32_t soff, float* grad, 
     const int g3 = vol_grid(3 * o->n_pix);
     cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)o->n, s);
     if (pair) {
-        k_vol_render<<<vol_grid(o->n_pix), 256, 0, s>>>(V, S, spp, sp, o->imgA, o->imgB);
+        k_vol_render<2><<<vol_grid(o->n_pix), 256, 0, s>>>(V, S, spp, sp, o->imgA, o->imgB);
         k_image_loss<<<g3, 256, 0, s>>>(o->loss_kind, o->n_pix, o->imgA, o->target, o->dA, nullptr);
         k_image_loss<<<g3, 256, 0, s>>>(o->loss_kind, o->n_pix, o->imgB, o->target, o->dB, nullptr);
-        k_vol_adjoint<<<vol_grid(o->n_pix * spp), 256, 0, s>>>(V, S, o->dA, o->dB, spp, sa,
-                                                                reinterpret_cast<float4*>(grad));
+        vol_launch_adjoint<2>(o->vol, S, o->dA, o->dB, spp, sa, grad, s);
         return 4;
     }
     if (loss) cudaMemsetAsync(loss, 0, sizeof(double), s);
-    k_vol_render<<<vol_grid(o->n_pix), 256, 0, s>>>(V, S, spp, sp, o->imgP, nullptr);
+    k_vol_render<1><<<vol_grid(o->n_pix), 256, 0, s>>>(V, S, spp, sp, o->imgP, nullptr);
     k_image_loss<<<g3, 256, 0, s>>>(o->loss_kind, o->n_pix, o->imgP, o->target, o->dP, loss);
-    k_vol_adjoint<<<vol_grid(o->n_pix * spp), 256, 0, s>>>(V, S, o->dP, nullptr, spp, sa,
-                                                            reinterpret_cast<float4*>(grad));
+    vol_launch_adjoint<1>(o->vol, S, o->dP, nullptr, spp, sa, grad, s);
     return 3;
 }
 
@@ -549,6 +672,8 @@ extern "C" mer_status mer_volume_opt_create(mer_volume* vol, const mer_hyper* hy
     for (float** a : {&o->target, &o->imgP, &o->dP, &o->imgA, &o->imgB, &o->dA, &o->dB})
         if (!e) e = vopt_alloc(o, a, 3 * o->n_pix);
     o->nblocks = update_blocks_for(o->n);
+    if (!e) e = vol_ensure_rec<1>(vol);          // allocated here, not inside a graph capture
+    if (!e && o->meta) e = vol_ensure_rec<2>(vol);
     if (!e) e = cudaMalloc(&o->d_ps, sizeof(ProbState));
     if (!e) e = cudaMalloc(&o->d_seg, sizeof(UpdSeg));
     if (!e) e = cudaMalloc(&o->d_blk_off, 2 * sizeof(int64_t));
