@@ -308,8 +308,15 @@ __global__ void __launch_bounds__(256) k_image_loss(int kind, int64_t n_pix, con
         l += (double)r * (double)r * (double)w;
     }
     if (!loss) return;
+    __shared__ double part[8];
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l / (3.0 * (double)n_pix));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < 8; ++w) b += part[w];
+        atomicAdd(loss, b / (3.0 * (double)n_pix));     // one atomic per block
+    }
 }
 
 }  // namespace mer
