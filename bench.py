@@ -662,6 +662,29 @@ def run_mine(args):
            "iters_per_s": world * args.steps / e2e_s}
     ctx.close()
 
+    # ---- the same iterations with replays that re-trace every ray (no per-vertex hit store) ----
+    retrace = None
+    if rank == 0:
+        cr = Context(local, max_paths=1 << 20, replay_retrace=True)
+        pr = cr.add_scene(sc, HyperParams(lr=0.01))
+        cr.set_target(pr, target_img)
+        cr.set_params(pr, w.init_tex)
+        shape_r = cr.autotune(3) if not args.no_autotune else "defaults"
+        cr.iterate(3, use_graph=True)
+        kr = min(args.steps, 50)
+        evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kr)]
+        torch.cuda.synchronize()
+        for k in range(kr):
+            l2_flush(torch, flush)
+            evr[k][0].record()
+            cr.iterate(1, use_graph=True)
+            evr[k][1].record()
+        torch.cuda.synchronize()
+        msr = sum(a.elapsed_time(b) for a, b in evr) / kr
+        retrace = {"ms_per_step": msr, "paths_per_s": paths_per_iter / (msr * 1e-3), "steps": kr,
+                   "launches_per_iter": cr.launch_count(), "launch_shape": shape_r}
+        cr.close()
+
     cpu = None
     ttt = None
     if rank == 0 and not args.no_ttt:
@@ -695,6 +718,7 @@ def run_mine(args):
                            "paths_per_iter": paths_per_iter, "l2": "flushed (256 MiB write) between timed steps",
                            "parallelism": f"replicas x{world}"},
                 "iters_per_s": iters_per_s,
+                "replay_retrace": retrace,
                 "roofline": roof, "rooflines": rooflines + ([upd67] if upd67 else []),
                 "kernels": kernels, "peak_source": peak_kind,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),

@@ -164,6 +164,12 @@ typedef struct mer_config {
     int32_t blocks_per_sm;    /* persistent-grid occupancy target (0 = default) */
     int32_t smem_nodes;       /* BVH nodes staged in shared memory per block (0 = off) */
     int64_t max_paths;        /* capacity hint for path queues (0 = size from the scenes) */
+    /* 0 (default): the iteration's PRB radiance passes keep each path vertex's closest hit and
+     * NEE visibility (16 B + 1 B per vertex and branch) and the replays read them instead of
+     * tracing again (same hits, no traversal launches); 1: the replays re-trace every ray, so no
+     * per-vertex state is kept. The estimates are the same either way; mer_adjoint and
+     * mer_adjoint_pair always re-trace. */
+    int32_t replay_retrace;
 } mer_config;
 
 typedef struct mer_iter_stats {

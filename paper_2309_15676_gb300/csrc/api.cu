@@ -51,6 +51,10 @@ struct Wave {
     float* lacc = nullptr;
     float* ltot = nullptr;
     Record* rec = nullptr;
+    // hit store of the ADJ_FWD passes (sets 2 and 3), read by their replays (PassArgs::hs)
+    float4* hs = nullptr;
+    uint8_t* hvis = nullptr;
+    int hs_depth = 0;
 };
 
 struct mer_ctx {
@@ -237,6 +241,7 @@ void free_wave(Wave& w) {
     }
     dfree(w.hitf); dfree(w.hitp); dfree(w.shf); dfree(w.shu); dfree(w.lacc); dfree(w.ltot);
     dfree(w.rec); dfree(w.cnt);
+    dfree(w.hs); dfree(w.hvis);
     w = Wave();
 }
 
@@ -244,7 +249,7 @@ void free_wavefront(mer_ctx* c) {
     for (Wave& w : c->w) free_wave(w);
 }
 
-mer_status alloc_wave(mer_ctx* c, Wave& w, int64_t Q, int64_t R) {
+mer_status alloc_wave(mer_ctx* c, Wave& w, int64_t Q, int64_t R, int hs_depth) {
     const int64_t S = 2 * Q;
     for (int i = 0; i < 2; ++i) {
         CK(c, dalloc(&w.qf[i], (size_t)(2 * QF_PER_BRANCH) * Q));
@@ -259,6 +264,14 @@ mer_status alloc_wave(mer_ctx* c, Wave& w, int64_t Q, int64_t R) {
     CK(c, dalloc(&w.rec, (size_t)R));
     CK(c, dalloc(&w.cnt, (size_t)CNT_WORDS));
     CK(c, cudaMemset(w.cnt, 0, sizeof(uint32_t) * CNT_WORDS));
+    if (hs_depth > 0) {
+        const size_t ne = (size_t)2 * hs_depth * Q;          // two branches
+        CK(c, dalloc(&w.hs, ne));
+        CK(c, dalloc(&w.hvis, ne));
+        CK(c, cudaMemset(w.hs, 0xff, sizeof(float4) * ne));   // prim = -1 (miss) until written
+        CK(c, cudaMemset(w.hvis, 0, ne));
+        w.hs_depth = hs_depth;
+    }
     w.qcap = Q;
     w.shcap = S;
     w.rcap = R;
@@ -270,14 +283,17 @@ mer_status alloc_wave(mer_ctx* c, Wave& w, int64_t Q, int64_t R) {
 mer_status ensure_wavefront(mer_ctx* c, int64_t need_paths, int maxD) {
     const int64_t want_q = std::max<int64_t>(need_paths, c->cfg.max_paths > 0 ? c->cfg.max_paths : 0);
     const int64_t want_r = 2 * want_q * std::max(1, maxD - 1);
-    if (want_q <= c->w[0].qcap && want_r <= c->w[0].rcap) return MER_OK;
+    if (want_q <= c->w[0].qcap && want_r <= c->w[0].rcap && (c->cfg.replay_retrace || maxD <= c->w[2].hs_depth))
+        return MER_OK;
     cudaStreamSynchronize(c->st);
     for (cudaStream_t s : c->sx) cudaStreamSynchronize(s);
     free_wavefront(c);
     const int64_t Q = std::max<int64_t>(want_q, 1024);
     const int64_t R = std::max<int64_t>(want_r, 1024);
     for (int i = 0; i < 4; ++i) {
-        mer_status s = alloc_wave(c, c->w[i], Q, i < 2 ? R : 1);
+        // sets 0 and 1 replay (records); sets 2 and 3 run the ADJ_FWD passes (hit store)
+        const int hs_depth = (i < 2 || c->cfg.replay_retrace) ? 0 : std::max(1, maxD);
+        mer_status s = alloc_wave(c, c->w[i], Q, i < 2 ? R : 1, hs_depth);
         if (s) return s;
     }
     c->graph_dirty = true;
@@ -316,6 +332,14 @@ LaunchShape shape_of(mer_ctx* c) {
     return L;
 }
 
+// the hit store of wave set w (its ADJ_FWD pass writes it, the matching replay reads it)
+void hit_store(PassArgs& A, const Wave& w) {
+    A.hs = w.hs;
+    A.hvis = w.hvis;
+    A.hs_depth = w.hs_depth;
+    A.hs_cap = w.qcap;
+}
+
 // zero the pass counters (not the error word) and run one pass on stream st
 int pass(mer_ctx* c, cudaStream_t st, PassArgs A, int nb, int mode, int maxD) {
     cudaMemsetAsync(A.cnt, 0, CNT_ERR * sizeof(uint32_t), st);
@@ -330,7 +354,7 @@ int pass(mer_ctx* c, cudaStream_t st, PassArgs A, int nb, int mode, int maxD) {
         for (int k = 2; k <= maxD; ++k) rays += h[CNT_Q + k];
         for (int k = 1; k <= maxD; ++k) sh += h[CNT_S + k];
         const int rep = mode == MODE_REPLAY ? 1 : 0;
-        g_timer->add_units((nb == 1 ? KC_TRACE1_PRIMAL : KC_TRACE2_PRIMAL) + rep, rays + sh);
+        if (!(rep && A.hs)) g_timer->add_units((nb == 1 ? KC_TRACE1_PRIMAL : KC_TRACE2_PRIMAL) + rep, rays + sh);
         g_timer->add_units((nb == 1 ? KC_SHADE1_PRIMAL : KC_SHADE2_PRIMAL) + rep, rays);
         if (mode == MODE_REPLAY) g_timer->add_units(KC_SCATTER, h[CNT_R]);
     }
@@ -402,6 +426,7 @@ int enqueue_gradient(mer_ctx* c) {
         PassArgs PR = prop_args(2);
         PR.stream = MER_STREAM_PROP_ADJ + soff;
         PR.lacc = c->w[2].ltot;                  // per-path radiance L_total of the replayed paths
+        hit_store(PR, c->w[2]);
         n += pass(c, s[2], PR, 1, MODE_ADJ_FWD, c->maxD_prop);
         if (have_fd) {
             PassArgs D = fd_args(1);
@@ -411,6 +436,7 @@ int enqueue_gradient(mer_ctx* c) {
             PassArgs DR = fd_args(3);
             DR.stream = MER_STREAM_FD_ADJ + soff;
             DR.lacc = c->w[3].ltot;
+            hit_store(DR, c->w[3]);
             n += pass(c, s[3], DR, 2, MODE_ADJ_FWD, c->maxD_fd);
         }
         join(4);
@@ -423,6 +449,7 @@ int enqueue_gradient(mer_ctx* c) {
         P = prop_args(0);
         P.stream = MER_STREAM_PROP_ADJ + soff;
         P.ltot = c->w[2].ltot;
+        hit_store(P, c->w[2]);
         n += pass(c, s[0], P, 1, MODE_REPLAY, c->maxD_prop);
         zero(wF, s[0]);
         n += run_scatter(c->w[0].cnt, c->w[0].rec, c->w[0].rcap, c->d_probs, NP, nullptr, wF, G, s[0]);
@@ -431,6 +458,7 @@ int enqueue_gradient(mer_ctx* c) {
             PassArgs D = fd_args(1);
             D.stream = MER_STREAM_FD_ADJ + soff;
             D.ltot = c->w[3].ltot;
+            hit_store(D, c->w[3]);
             n += pass(c, s[1], D, 2, MODE_REPLAY, c->maxD_fd);
             zero(wD, s[1]);
             n += run_scatter(c->w[1].cnt, c->w[1].rec, c->w[1].rcap, c->d_probs, NP, nullptr, wD, G, s[1]);

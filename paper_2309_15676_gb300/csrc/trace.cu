@@ -478,6 +478,10 @@ constexpr int shade_min_blocks() {
 template <int NB, int MODE>
 __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(PassArgs A, int depth) {
     constexpr bool GRAD = MODE == MODE_REPLAY;
+    // hit store (PassArgs::hs): the ADJ_FWD pass records what its replay needs, the replay reads
+    // it back instead of tracing
+    const bool store = MODE != MODE_REPLAY && A.hs != nullptr;
+    const bool stored = MODE == MODE_REPLAY && A.hs != nullptr;
     const bool first = depth == 1;
     const int64_t n = first ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth], A.qcap);
     const int64_t nw = (n + 31) & ~(int64_t)31;
@@ -538,10 +542,25 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
             }
             const int hb = (b == 1 && coinc) ? 0 : b;
             Hit h;
-            h.t = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_T) * A.qcap + j];
-            h.b1 = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_B1) * A.qcap + j];
-            h.b2 = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_B2) * A.qcap + j];
-            h.prim = A.hitp[(size_t)hb * A.qcap + j];
+            if (stored) {
+                const float4 hv = A.hs[((int64_t)hb * A.hs_depth + depth - 1) * A.hs_cap + g];
+                h.t = hv.x;
+                h.b1 = hv.y;
+                h.b2 = hv.z;
+                h.prim = __float_as_int(hv.w);
+                if (h.prim < -1 || h.prim >= P.n_tris + P.n_sph) {   // not this pass's path: never used
+                    set_err(A, MER_ERR_STATE);
+                    h.prim = -1;
+                }
+            } else {
+                h.t = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_T) * A.qcap + j];
+                h.b1 = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_B1) * A.qcap + j];
+                h.b2 = A.hitf[(size_t)(hb * HF_PER_BRANCH + HF_B2) * A.qcap + j];
+                h.prim = A.hitp[(size_t)hb * A.qcap + j];
+                if (store && hb == b)   // ADJ_FWD: keep the hit for the replay, by path
+                    A.hs[((int64_t)b * A.hs_depth + depth - 1) * A.hs_cap + g] =
+                        make_float4(h.t, h.b1, h.b2, __int_as_float(h.prim));
+            }
             if (h.prim < 0) {
                 if (P.has_env) {
                     const float w = first ? 1.0f : mis2(pdfb[b], pdfenv[b]);
@@ -646,7 +665,9 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
 #pragma unroll
                         for (int k = 0; k < MAXC; ++k) dN[k] = k3.x * df[k][0] + k3.y * df[k][1] + k3.z * df[k][2];
                     }
-                    sh_want[b] = wg || contrib[b].x != 0.0f || contrib[b].y != 0.0f || contrib[b].z != 0.0f;
+                    // (the storing ADJ_FWD pass tests every shadow ray its replay will need)
+                    sh_want[b] = wg || (store && textured[b]) || contrib[b].x != 0.0f || contrib[b].y != 0.0f ||
+                                 contrib[b].z != 0.0f;
                 }
                 // BSDF sample for the continuation
                 v3 wi;
@@ -704,6 +725,23 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
             }
         }
 
+        // ---- stored replay: the NEE shadow rays' visibility from the ADJ_FWD pass ----
+        if (stored && valid) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (!sh_want[b]) continue;
+                if (!A.hvis[((int64_t)b * A.hs_depth + depth - 1) * A.hs_cap + g]) continue;
+                const v3 l = lacc[b] + contrib[b];
+                A.lacc[(size_t)(b * 3 + 0) * A.qcap + g] = l.x;
+                A.lacc[(size_t)(b * 3 + 1) * A.qcap + g] = l.y;
+                A.lacc[(size_t)(b * 3 + 2) * A.qcap + g] = l.z;
+                if (rec_want[b]) {
+#pragma unroll
+                    for (int k = 0; k < MAXC; ++k) gbase[b][k] += gnee[b][k];
+                }
+            }
+        }
+
         // ---- records (REPLAY) ----
         const bool merged = coinc && rec_want[0] && (NB == 2 && rec_want[NB - 1]);
         uint32_t rec_idx[NB];
@@ -742,8 +780,8 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
             if (merged) rec_idx[NB - 1] = rec_idx[0];
         }
 
-        // ---- shadow rays ----
-        {
+        // ---- shadow rays (none in a stored replay) ----
+        if (!stored) {
             const bool sh_shared = coinc && ls[0].ok;   // one shadow ray serves both branches
             uint32_t nsh = 0;
             if (sh_shared) nsh = (sh_want[0] || (NB == 2 && sh_want[NB - 1])) ? 1u : 0u;
@@ -839,7 +877,7 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
 // any-hit of shadow entry j; if the light is visible, add the NEE radiance to the path's
 // accumulator and (replay) the NEE part of the gradient to its record
 template <int NB, int MODE, bool STATS>
-__device__ __forceinline__ void shadow_item(const PassArgs& A, const Node* s_nodes, int n_staged, int64_t j,
+__device__ __forceinline__ void shadow_item(const PassArgs& A, const Node* s_nodes, int n_staged, int64_t j, int depth_sh,
                                             TravCount& tc) {
     const size_t C = (size_t)A.shcap;
     const float* F = A.shf;
@@ -851,7 +889,14 @@ __device__ __forceinline__ void shadow_item(const PassArgs& A, const Node* s_nod
     const int q = meta & 0xff;
     const uint32_t mask = (meta >> 8) & 3u;
     Hit h;
-    if (traverse<true, STATS>(A.probs[q], s_nodes, q == A.smem_prob ? n_staged : 0, o, d, tmax, h, tc)) return;
+    const bool occluded = traverse<true, STATS>(A.probs[q], s_nodes, q == A.smem_prob ? n_staged : 0, o, d, tmax, h, tc);
+    if (MODE != MODE_REPLAY && A.hs) {   // ADJ_FWD: keep the visibility for the replay, by path
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (mask & (1u << b))
+                A.hvis[((int64_t)b * A.hs_depth + depth_sh - 1) * A.hs_cap + g] = occluded ? 0 : 1;
+    }
+    if (occluded) return;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         if (!(mask & (1u << b))) continue;
@@ -892,7 +937,7 @@ __global__ void __launch_bounds__(256) k_trace(PassArgs A, int depth_ext, int de
             if (split) extend_item<NB, STATS>(A, s_nodes, n_staged, depth_ext, j >> 1, (int)(j & 1), tc_e);
             else extend_item<NB, STATS>(A, s_nodes, n_staged, depth_ext, j, NB == 2 ? -1 : 0, tc_e);
         } else {
-            shadow_item<NB, MODE, STATS>(A, s_nodes, n_staged, j - n_ext_lanes, tc_s);
+            shadow_item<NB, MODE, STATS>(A, s_nodes, n_staged, j - n_ext_lanes, depth_sh, tc_s);
         }
     }
     if (STATS) {
@@ -984,12 +1029,17 @@ struct PassLauncher {
         else MER_TIMED(cls, st, k_shade<NB, MODE><<<g_shade, L.block, 0, st>>>(B, depth));
     }
 
-    // trace(1) shade(1) trace(2, 1) shade(2) ... shade(D) trace(-, D): 2D + 1 launches
+    // trace(1) shade(1) trace(2, 1) shade(2) ... shade(D) trace(-, D): 2D + 1 launches; a replay
+    // with a hit store: shade(1) ... shade(D)
     int run(const PassArgs& A, int max_depth, const LaunchShape& L, cudaStream_t st) {
         const size_t smem = (size_t)L.smem_nodes * sizeof(Node);
         PassArgs B = A;
         B.smem_nodes = L.smem_nodes;
         grids(L, smem);
+        if (MODE == MODE_REPLAY && B.hs) {
+            for (int depth = 1; depth <= max_depth; ++depth) shade(B, depth, L, st);
+            return max_depth;
+        }
         for (int depth = 1; depth <= max_depth; ++depth) {
             trace(B, depth, depth - 1, L, smem, st);
             shade(B, depth, L, st);

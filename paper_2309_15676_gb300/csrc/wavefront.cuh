@@ -66,6 +66,15 @@ struct PassArgs {
     const float* ltot;        // [NB*3][qcap] radiance of the ADJ_FWD pass (REPLAY)
     Record* rec;
     int64_t rcap;
+    // hit store of a PRB pair of passes: the ADJ_FWD pass (PRIMAL kernels) writes, for branch b,
+    // depth k (1-based) and path g, the closest hit hs[(b * hs_depth + k - 1) * hs_cap + g] =
+    // {t, b1, b2, prim bits} (its shade kernel, as it reads the hit) and the visibility of the NEE
+    // shadow ray hvis[same index] (0 / 1, the shadow test); its REPLAY pass reads them and launches
+    // no traversal. nullptr: the replay re-traces.
+    float4* hs;
+    uint8_t* hvis;
+    int32_t hs_depth;
+    int64_t hs_cap;
     int32_t smem_nodes;       // top BVH nodes of problem smem_prob staged in shared memory
     int32_t smem_prob;
     unsigned long long* stats; // counting run: [2*class] node tests, [2*class+1] primitive tests

@@ -59,8 +59,9 @@ def test_struct_sizes_match_header():
     prog = r'''
 #include <stdio.h>
 #include "mer.h"
-int main(void){printf("%zu %zu %zu %zu %zu\n", sizeof(mer_hyper), sizeof(mer_scene_desc), sizeof(mer_config),
- sizeof(mer_iter_stats), sizeof(mer_state_view));return 0;}'''
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mer_hyper), sizeof(mer_scene_desc),
+ sizeof(mer_config), sizeof(mer_iter_stats), sizeof(mer_state_view), sizeof(mer_volume_desc),
+ sizeof(mer_update_arrays), sizeof(mer_kernel_time));return 0;}'''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         open(c, "w").write(prog)
@@ -68,4 +69,5 @@ int main(void){printf("%zu %zu %zu %zu %zu\n", sizeof(mer_hyper), sizeof(mer_sce
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert sizes == [ct.sizeof(_lib.Hyper), ct.sizeof(_lib.SceneDesc), ct.sizeof(_lib.Config),
-                     ct.sizeof(_lib.IterStats), ct.sizeof(_lib.StateView)]
+                     ct.sizeof(_lib.IterStats), ct.sizeof(_lib.StateView), ct.sizeof(_lib.VolumeDesc),
+                     ct.sizeof(_lib.UpdateArrays), ct.sizeof(_lib.KernelTime)]
