@@ -5,9 +5,11 @@
 // sample k at t0 + (k + u) delta with one Philox uniform u per ray (vertex 1), samples past the
 // exit skipped. Voxel parameters are one float4 each (emission RGB, density) at
 // ((z ny + y) nx + x); trilinear, clamp-to-edge, voxel centres at (i + 1/2) / n across the box.
-// The adjoint replays the march from the same counters with the ray's total radiance (O(1)
-// memory): dL/de_k = T_k a_k, dL/dsigma_k = delta ((1 - a_k) T_k e_k - L_after_k), distributed to
-// the eight voxels by the trilinear weights with fire-and-forget float4 reductions.
+// The adjoint marches each ray twice from the same counters: a radiance pass that records
+// (sigma_k, adj . e_k) per step (8 bytes per step of each ray in flight, in a buffer the volume
+// owns) and a replay that reads the records back instead of the voxels:
+// dL/de_k = T_k a_k, dL/dsigma_k = delta ((1 - a_k) T_k e_k - L_after_k), distributed to the
+// eight voxels by the trilinear weights with fire-and-forget float4 reductions.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -99,11 +101,10 @@ __device__ __forceinline__ void vol_ray(const VolDev& V, uint32_t pixel, uint32_
     u = u01(draw(V.seed, V.key_id, pixel, sample, iter, stream, 1, 0).x);
 }
 
-// Per-step record of the adjoint's radiance pass: sigma_k and adj . e_k, one float2 plane
-// [max_steps][slots] per branch
-// Radiance of one parameter vector along one ray. With REC, step k (k < max_steps) also stores
-// sigma_k and adj . e_k at rec[k * slots] (the caller offsets rec by its thread slot) and the march
-// stops after max_steps; returns the step count.
+// Radiance of one parameter vector along one ray. With REC (the adjoint's radiance pass), step k
+// (k < max_steps) also records sigma_k and adj . e_k at rec[k * slots] — one float2 plane
+// [max_steps][slots] per branch, the caller offsetting rec by its plane and thread slot — and the
+// march stops after max_steps; returns the step count.
 template <bool REC>
 __device__ __forceinline__ int vol_march(const VolDev& V, const float4* __restrict__ par, v3 o, v3 d, float u, v3& Lout,
                                          v3 adj = v3{}, float2* rec = nullptr, int64_t slots = 0, int max_steps = 0) {
