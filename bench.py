@@ -215,8 +215,8 @@ def eval_loss(torch, ctx, pid, target, spp=64):
 
 def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags=0, precond_lambda=0.0):
     """One optimisation run: iterations and GPU time (iterations only, evaluation excluded) until
-    the 64-spp eval loss drops below `frac` of its initial value; evaluated every 2 iterations for
-    the first 50, then every 10."""
+    the 64-spp eval loss drops below `frac` of its initial value (and below 10% of it); evaluated
+    every 2 iterations for the first 50, then every 10."""
     from paper_2309_15676_gb300.api import Context, HyperParams
     sc = dict(w.scene)
     sc["spp_prop"], sc["spp_fd"] = spp_prop, spp_fd
@@ -233,6 +233,7 @@ def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, fr
     l0 = eval_loss(torch, ctx, pid, target_img)
     thr = frac * l0
     gpu_ms, it, reached, reached_ms, last, lmin = 0.0, 0, None, None, l0, l0
+    r10, r10_ms = None, None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     while it < max_iters:
         k = 2 if it < 50 else 10
@@ -246,8 +247,11 @@ def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, fr
         lmin = min(lmin, last)
         if reached is None and last <= thr:
             reached, reached_ms = it, gpu_ms
+        if r10 is None and last <= 0.1 * l0:
+            r10, r10_ms = it, gpu_ms
     ctx.close()
     return {"lr": lr, "iters": reached, "gpu_s": reached_ms / 1e3 if reached else None, "loss0": l0,
+            "iters_10pct": r10, "gpu_s_10pct": r10_ms / 1e3 if r10 else None,
             "final_loss_ratio": last / l0, "min_loss_ratio": lmin / l0, "iters_run": it,
             "gpu_s_total": gpu_ms / 1e3}
 
