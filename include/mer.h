@@ -382,8 +382,9 @@ mer_status mer_checkpoint_load(mer_ctx* ctx, const void* buf, size_t len);
  * description written to desc (may be NULL). Changes no optimisation state. */
 mer_status mer_autotune(mer_ctx* ctx, int32_t trial_iters, char* desc, size_t desc_len);
 
-/* Number of kernel launches the last mer_iterate / mer_gradient_step + mer_update_step enqueued
- * per iteration (for launch accounting). */
+/* Number of the library's own kernel launches the last mer_iterate / mer_gradient_step +
+ * mer_update_step enqueued per iteration (for launch accounting; memsets and cuBLAS calls are not
+ * counted). */
 mer_status mer_launch_count(mer_ctx* ctx, int64_t* launches_per_iter);
 
 /* Per-kernel timing (diagnostic). While enabled, every launch of the wavefront, scatter, loss and

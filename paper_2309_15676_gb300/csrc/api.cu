@@ -344,7 +344,7 @@ void hit_store(PassArgs& A, const Wave& w) {
 int pass(mer_ctx* c, cudaStream_t st, PassArgs A, int nb, int mode, int maxD) {
     cudaMemsetAsync(A.cnt, 0, CNT_ERR * sizeof(uint32_t), st);
     const LaunchShape L = shape_of(c);
-    const int n = 1 + run_pass(A, nb, mode, maxD, L, st);
+    const int n = run_pass(A, nb, mode, maxD, L, st);   // kernel launches (the memset is not one)
     if (g_timer) {
         // work items of this pass: rays per depth and NEE rays, read back from the pass counters
         uint32_t h[CNT_WORDS];
@@ -416,7 +416,6 @@ int enqueue_gradient(mer_ctx* c) {
     // wD, drawn from the four gradient streams shifted by soff, loss accumulated into `loss`.
     auto evaluate = [&](uint32_t soff, int wF, int wD, double* loss) {
         cudaMemsetAsync(loss, 0, sizeof(double) * NP, s[0]);
-        n++;
         // ---- stage 1 ----
         fork(4);
         PassArgs P = prop_args(0);

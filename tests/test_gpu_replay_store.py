@@ -23,12 +23,12 @@ def _run(ws, flags, retrace, iters=3):
         ctx.set_params(p, w.init_tex)
         ids.append(p)
     ctx.iterate(iters, use_graph=True)
+    launches = ctx.launch_count()       # per iteration, gradient part and update
     ctx.gradient_step()
     out = []
     for p in ids:
         F, dF = (x.cpu().numpy().astype(np.float64) for x in ctx.grads(p))
         out.append((F, dF, ctx.get_params(p).cpu().numpy(), ctx.stats(p)["loss"]))
-    launches = ctx.launch_count()
     ctx.close()
     return out, launches
 
@@ -46,6 +46,8 @@ def test_stored_replay_equals_retrace(case):
     a, la = _run(ws, flags, retrace=False)
     b, lb = _run(ws, flags, retrace=True)
     assert la < lb          # the stored replays launch no traversal
+    if case != "batch":     # depth 5: four passes of 2D+1 launches, replays of D (or 2D+1), 9 others
+        assert (la, lb) == (4 * 11 + 2 * 5 + 9, 6 * 11 + 9), (la, lb)
     for (Fa, dFa, pa, lsa), (Fb, dFb, pb, lsb) in zip(a, b):
         assert np.abs(Fa).max() > 0 and np.abs(dFa).max() > 0
         assert rel_l2(Fa, Fb) < 1e-5 and rel_l2(dFa, dFb) < 1e-5, (rel_l2(Fa, Fb), rel_l2(dFa, dFb))
