@@ -229,7 +229,10 @@ void mer_volume_destroy(mer_volume* vol);
 mer_status mer_volume_render(mer_volume* vol, const float* params_dev, int32_t spp, uint32_t stream,
                              uint32_t iteration, float* img_dev, void* cuda_stream);
 /* grad_dev (voxel float4s, caller-zeroed) += d/dparams of sum_p dimg[p] . I_p by replay of the
- * same counters (the ray's radiance pass, then the replay; no stored samples) */
+ * same counters: a radiance pass that records (sigma_k, dimg . e_k) per march step into a buffer
+ * the volume owns (allocated on the first call, 8 B per step of each ray in flight; so adjoint
+ * calls and optimiser iterations on one volume must be ordered on one stream or synchronised),
+ * then the replay from those records */
 mer_status mer_volume_adjoint(mer_volume* vol, const float* params_dev, const float* dimg_dev, int32_t spp,
                               uint32_t stream, uint32_t iteration, float* grad_dev, void* cuda_stream);
 /* FD pair (Eq. est_triv): the same counters at paramsA and paramsB; grad_dev += g_A - g_B */
