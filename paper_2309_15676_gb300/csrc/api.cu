@@ -85,6 +85,7 @@ struct mer_ctx {
     cudaStream_t sx[3] = {nullptr, nullptr, nullptr};   // extra internal streams for concurrent passes
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_loss[2] = {nullptr, nullptr};   // proportional / FD adjoint images ready
     // update
     UpdSeg* d_segs = nullptr;
     int64_t* d_blk_off = nullptr;
@@ -361,14 +362,14 @@ int pass(mer_ctx* c, cudaStream_t st, PassArgs A, int nb, int mode, int maxD) {
     return n;
 }
 
-// the gradient part of one iteration for all problems (steps a1-a10), as a graph of passes:
-//   stage 1 (concurrent): proportional primal image   [main stream, wave set 0]
-//                         FD primal image pair          [stream x0,  wave set 1]
-//                         proportional PRB radiance     [stream x1,  wave set 2]
-//                         FD PRB radiance pair          [stream x2,  wave set 3]
-//   stage 2: L2 loss and adjoint images (needs both images)
-//   stage 3 (concurrent): proportional replay + scatter into F   [main, set 0, L_total of set 2]
-//                         FD replay pair + scatter into dF       [x0,   set 1, L_total of set 3]
+// the gradient part of one iteration for all problems (steps a1-a10), as a graph of passes in
+// two independent chains that join before the update:
+//   proportional: primal image [main stream, wave set 0] -> its loss and adjoint image (main)
+//                 PRB radiance [stream x1, wave set 2]   -> (both done) replay [x1, set 0, L_total
+//                 and hits of set 2] + scatter into F
+//   FD pair:      primal image pair [x0, set 1] -> the pair's adjoint images (x0)
+//                 PRB radiance pair [x2, set 3] -> (both done) replay pair [x2, set 1, L_total and
+//                 hits of set 3] + scatter into dF
 // Branches fork and join through events, so inside stream capture they become parallel graph
 // branches. While per-kernel timing is on, everything runs on the main stream.
 int enqueue_gradient(mer_ctx* c) {
@@ -416,53 +417,51 @@ int enqueue_gradient(mer_ctx* c) {
     // wD, drawn from the four gradient streams shifted by soff, loss accumulated into `loss`.
     auto evaluate = [&](uint32_t soff, int wF, int wD, double* loss) {
         cudaMemsetAsync(loss, 0, sizeof(double) * NP, s[0]);
-        // ---- stage 1 ----
         fork(4);
+        // ---- proportional chain ----
         PassArgs P = prop_args(0);
         P.stream = MER_STREAM_PROP_PRIMAL + soff;
         n += pass(c, s[0], P, 1, MODE_PRIMAL, c->maxD_prop);
         n += run_resolve(P, 1, nullptr, nullptr, 0, G, s[0]);
+        n += run_l2(c->d_probs, c->d_pix_pref, NP, c->total_pix, L2_PROP, loss, G, s[0]);
+        if (split) cudaEventRecord(c->ev_loss[0], s[0]);
         PassArgs PR = prop_args(2);
         PR.stream = MER_STREAM_PROP_ADJ + soff;
         PR.lacc = c->w[2].ltot;                  // per-path radiance L_total of the replayed paths
         hit_store(PR, c->w[2]);
         n += pass(c, s[2], PR, 1, MODE_ADJ_FWD, c->maxD_prop);
+        if (split) cudaStreamWaitEvent(s[2], c->ev_loss[0], 0);
+        // proportional gradient <F_i>: replay from the same counters (in wave set 0, after the
+        // primal pass left it), scatter into F (cleared right before, so that the reductions
+        // find it in L2)
+        P.stream = MER_STREAM_PROP_ADJ + soff;
+        P.ltot = c->w[2].ltot;
+        hit_store(P, c->w[2]);
+        n += pass(c, s[2], P, 1, MODE_REPLAY, c->maxD_prop);
+        zero(wF, s[2]);
+        n += run_scatter(c->w[0].cnt, c->w[0].rec, c->w[0].rcap, c->d_probs, NP, nullptr, wF, G, s[2]);
+        // ---- FD chain (Eq. est_triv) ----
         if (have_fd) {
             PassArgs D = fd_args(1);
             D.stream = MER_STREAM_FD_PRIMAL + soff;
             n += pass(c, s[1], D, 2, MODE_PRIMAL, c->maxD_fd);
             n += run_resolve(D, 2, nullptr, nullptr, 0, G, s[1]);
+            n += run_l2(c->d_probs, c->d_pix_pref, NP, c->total_pix, L2_FD, loss, G, s[1]);
+            if (split) cudaEventRecord(c->ev_loss[1], s[1]);
             PassArgs DR = fd_args(3);
             DR.stream = MER_STREAM_FD_ADJ + soff;
             DR.lacc = c->w[3].ltot;
             hit_store(DR, c->w[3]);
             n += pass(c, s[3], DR, 2, MODE_ADJ_FWD, c->maxD_fd);
-        }
-        join(4);
-        // ---- stage 2: loss and adjoint images of every problem ----
-        n += run_l2(c->d_probs, c->d_pix_pref, NP, c->total_pix, have_fd, loss, G, s[0]);
-        // ---- stage 3 ----
-        fork(2);
-        // proportional gradient <F_i>: replay from the same counters, scatter into F (the
-        // texture is cleared right before its scatter, so that the reductions find it in L2)
-        P = prop_args(0);
-        P.stream = MER_STREAM_PROP_ADJ + soff;
-        P.ltot = c->w[2].ltot;
-        hit_store(P, c->w[2]);
-        n += pass(c, s[0], P, 1, MODE_REPLAY, c->maxD_prop);
-        zero(wF, s[0]);
-        n += run_scatter(c->w[0].cnt, c->w[0].rec, c->w[0].rcap, c->d_probs, NP, nullptr, wF, G, s[0]);
-        // finite-difference gradient <dF_i> (Eq. est_triv): the same for the pair, scatter into dF
-        if (have_fd) {
-            PassArgs D = fd_args(1);
+            if (split) cudaStreamWaitEvent(s[3], c->ev_loss[1], 0);
             D.stream = MER_STREAM_FD_ADJ + soff;
             D.ltot = c->w[3].ltot;
             hit_store(D, c->w[3]);
-            n += pass(c, s[1], D, 2, MODE_REPLAY, c->maxD_fd);
-            zero(wD, s[1]);
-            n += run_scatter(c->w[1].cnt, c->w[1].rec, c->w[1].rcap, c->d_probs, NP, nullptr, wD, G, s[1]);
+            n += pass(c, s[3], D, 2, MODE_REPLAY, c->maxD_fd);
+            zero(wD, s[3]);
+            n += run_scatter(c->w[1].cnt, c->w[1].rec, c->w[1].rcap, c->d_probs, NP, nullptr, wD, G, s[3]);
         }
-        join(2);
+        join(4);
     };
     evaluate(0u, 0, 1, c->d_loss);
     // MER_META_UNCORRELATED: a second, independent evaluation (own streams) for the variances
@@ -672,6 +671,7 @@ mer_status mer_create(const mer_config* cfg, void* cuda_stream, mer_ctx** out) {
     for (int i = 0; i < 3 && !e; ++i) {
         e = cudaStreamCreateWithFlags(&c->sx[i], cudaStreamNonBlocking);
         if (!e) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+        if (!e && i < 2) e = cudaEventCreateWithFlags(&c->ev_loss[i], cudaEventDisableTiming);
     }
     if (!e) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (!e) e = cudaMemset(c->d_loss, 0, sizeof(double) * 2 * MER_MAX_PROBLEMS);
@@ -705,6 +705,7 @@ void mer_destroy(mer_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     for (int i = 0; i < 3; ++i) {
         if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+        if (i < 2 && c->ev_loss[i]) cudaEventDestroy(c->ev_loss[i]);
         if (c->sx[i]) cudaStreamDestroy(c->sx[i]);
     }
     if (c->blas) cublasDestroy(c->blas);

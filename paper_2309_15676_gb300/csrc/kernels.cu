@@ -345,10 +345,10 @@ int run_scatter(uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev
 
 // Image loss (step a7) and its adjoint image, per problem: L2, L = 1/(3N) sum (I - T)^2 with
 // dL/dI = 2 (I - T) / (3N), or MRSE, each term divided by (T^2 + 0.01), for the proportional
-// image (loss accumulated per problem in FP64) and, with_fd, the two images of the FD pair.
-// Pixels of all problems are enumerated through the prefix pix_pref.
+// image (parts & L2_PROP; loss accumulated per problem in FP64) and the two images of the FD pair
+// (parts & L2_FD). Pixels of all problems are enumerated through the prefix pix_pref.
 __global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs, const int64_t* __restrict__ pix_pref,
-                                            int n_probs, int64_t total_pix, int with_fd, double* loss_acc) {
+                                            int n_probs, int64_t total_pix, int parts, double* loss_acc) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nw = (total_pix + 31) & ~(int64_t)31;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nw; p += stride) {
@@ -366,15 +366,18 @@ __global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs
                 const int64_t k = lp * 3 + c;
                 const float t = P.target[k];
                 const float w = rel ? 1.0f / (t * t + 0.01f) : 1.0f;
-                const float r = P.img[k] - t;
-                P.dimg[k] = sc * r * w;
-                l += (double)r * (double)r * (double)w;
-                if (with_fd && P.imgA) {
+                if (parts & L2_PROP) {
+                    const float r = P.img[k] - t;
+                    P.dimg[k] = sc * r * w;
+                    l += (double)r * (double)r * (double)w;
+                }
+                if ((parts & L2_FD) && P.imgA) {
                     P.dimgA[k] = sc * (P.imgA[k] - t) * w;
                     P.dimgB[k] = sc * (P.imgB[k] - t) * w;
                 }
             }
         }
+        if (!(parts & L2_PROP)) continue;    // (uniform) the FD images carry no loss
         // warp reduce when the whole warp belongs to one problem, else per lane
         const int q0 = __shfl_sync(FULLM, q, 0);
         const bool same = __all_sync(FULLM, q == q0);
@@ -387,9 +390,9 @@ __global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs
     }
 }
 
-int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int with_fd,
+int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int parts,
            double* loss_acc, int grid, cudaStream_t st) {
-    MER_TIMED(KC_L2, st, k_l2<<<grid, 256, 0, st>>>(probs, pix_pref, n_probs, total_pix, with_fd, loss_acc));
+    MER_TIMED(KC_L2, st, k_l2<<<grid, 256, 0, st>>>(probs, pix_pref, n_probs, total_pix, parts, loss_acc));
     return 1;
 }
 

@@ -51,7 +51,10 @@ int run_zero_grads(const ProblemDev* probs, int n_probs, int which, int grid, cu
 int run_scatter(uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev* probs, int n_probs,
                 float* grad_over, int which, int grid, cudaStream_t st);
 // per-problem L2 loss and adjoint images of all problems (pix_pref: prefix of n_pix over problems)
-int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int with_fd,
+// parts of the image loss kernel: the proportional image's adjoint image and loss, the FD pair's
+// two adjoint images
+constexpr int L2_PROP = 1, L2_FD = 2;
+int run_l2(const ProblemDev* probs, const int64_t* pix_pref, int n_probs, int64_t total_pix, int parts,
            double* loss_acc, int grid, cudaStream_t st);
 int run_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int64_t n, uint32_t* out, cudaStream_t st);
 

@@ -46,8 +46,8 @@ def test_stored_replay_equals_retrace(case):
     a, la = _run(ws, flags, retrace=False)
     b, lb = _run(ws, flags, retrace=True)
     assert la < lb          # the stored replays launch no traversal
-    if case != "batch":     # depth 5: four passes of 2D+1 launches, replays of D (or 2D+1), 9 others
-        assert (la, lb) == (4 * 11 + 2 * 5 + 9, 6 * 11 + 9), (la, lb)
+    if case != "batch":     # depth 5: four passes of 2D+1 launches, replays of D (or 2D+1), 10 others
+        assert (la, lb) == (4 * 11 + 2 * 5 + 10, 6 * 11 + 10), (la, lb)
     for (Fa, dFa, pa, lsa), (Fb, dFb, pb, lsb) in zip(a, b):
         assert np.abs(Fa).max() > 0 and np.abs(dFa).max() > 0
         assert rel_l2(Fa, Fb) < 1e-5 and rel_l2(dFa, dFb) < 1e-5, (rel_l2(Fa, Fb), rel_l2(dFa, dFb))
