@@ -187,6 +187,19 @@ __device__ __forceinline__ void vol_replay(const VolDev& V, v3 o, v3 d, float u,
     }
 }
 
+// Pixel of the i-th ray of a launch: views whose sides are multiples of 16 are walked in 16 x 16
+// tiles (a block of 256 rays is one compact bundle that shares voxels across both image axes),
+// others row by row.
+__device__ __forceinline__ uint32_t vol_pixel(const VolDev& V, uint32_t i) {
+    if ((V.width & 15) || (V.height & 15)) return i;
+    const uint32_t per_view = (uint32_t)V.width * (uint32_t)V.height;
+    const uint32_t view = i / per_view, r = i - view * per_view;
+    const uint32_t tiles_x = (uint32_t)V.width >> 4;
+    const uint32_t tile = r >> 8, k = r & 255u;
+    const uint32_t ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    return view * per_view + ((ty << 4) + (k >> 4)) * (uint32_t)V.width + (tx << 4) + (k & 15u);
+}
+
 // The parameter vectors and iteration of a launch: given explicitly, or (ps != nullptr) the
 // optimiser's two slots, pi_i = slot[ps->cur] and pi_{i-1} = the other, at iteration ps->iteration,
 // read on the device so that one captured graph serves every iteration.
@@ -224,7 +237,8 @@ __global__ void __launch_bounds__(256) k_vol_render(VolDev V, VolSel S, int spp,
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float inv = 1.0f / (float)spp;
     float* img[2] = {imgA, imgB};
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += stride) {
+    for (int64_t pi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pi < N; pi += stride) {
+        const int64_t p = vol_pixel(V, (uint32_t)pi);
         v3 acc[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) acc[j] = mk(0, 0, 0);
@@ -268,8 +282,9 @@ __global__ void __launch_bounds__(256) k_vol_adjoint(VolDev V, VolSel S, const f
     const float inv = 1.0f / (float)spp;
     const float* dimg[2] = {dA, dB};
     for (int64_t i = q; i < total; i += stride) {
-        const int64_t p = i / spp;
-        const uint32_t s = (uint32_t)(i - p * spp);
+        const int64_t pi = i / spp;
+        const uint32_t s = (uint32_t)(i - pi * spp);
+        const int64_t p = vol_pixel(V, (uint32_t)pi);
         v3 o, d;
         float u;
         vol_ray(V, (uint32_t)p, s, iter, stream, o, d, u);
