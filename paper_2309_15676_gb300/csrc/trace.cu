@@ -337,6 +337,18 @@ __device__ __forceinline__ void camera_ray(const ProblemDev& P, uint32_t pixel, 
                   mk(P.cam_u[0], P.cam_u[1], P.cam_u[2]) * sy);
 }
 
+// Pixel of a problem's local path index (modulo its pixel count): images whose sides are multiples
+// of 16 are walked in 16 x 16 tiles, so that a warp's camera rays are a 16 x 2 patch (coherent
+// traversal, and the queue compaction carries some of that order to later depths); others row by
+// row. Counters, images and adjoint images are indexed by the pixel itself.
+__device__ __forceinline__ uint32_t path_pixel(const ProblemDev& P, uint32_t local) {
+    if ((P.width & 15) || (P.height & 15)) return local;
+    const uint32_t tiles_x = (uint32_t)P.width >> 4;
+    const uint32_t tile = local >> 8, k = local & 255u;
+    const uint32_t ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    return ((ty << 4) + (k >> 4)) * (uint32_t)P.width + (tx << 4) + (k & 15u);
+}
+
 struct PathId {
     int q, e;
     uint32_t pixel, sample, iter;
@@ -355,7 +367,7 @@ __device__ __forceinline__ PathId decode_path(const PassArgs& A, int64_t g) {
         local = g - A.path_off[id.e];
     }
     const ProblemDev& P = A.probs[id.q];
-    id.pixel = (uint32_t)(local % P.n_pix);
+    id.pixel = path_pixel(P, (uint32_t)(local % P.n_pix));
     id.sample = (uint32_t)(local / P.n_pix) + (uint32_t)A.sample_base;
     id.iter = A.iter_override >= 0 ? (uint32_t)A.iter_override : (uint32_t)A.pstate[id.q].iteration;
     id.spp = A.spp_override > 0 ? A.spp_override : (A.fd_kind ? P.spp_fd : P.spp_prop);
@@ -973,7 +985,7 @@ __global__ void k_resolve(PassArgs A, float* img0, float* img1, int accumulate) 
         for (int b = 0; b < NB; ++b) {
             float* img = A.inl_prob >= 0 ? (b == 0 ? img0 : img1) : (A.fd_kind ? (b ? P.imgB : P.imgA) : P.img);
             if (!img) continue;
-            img += local * 3;
+            img += (int64_t)path_pixel(P, (uint32_t)local) * 3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float acc = 0.0f;
@@ -987,9 +999,13 @@ __global__ void k_resolve(PassArgs A, float* img0, float* img1, int accumulate) 
 // per-sample radiance out[(s*n_pix + p)*3 + c] of a single-problem pass
 __global__ void k_samples_out(PassArgs A, float* out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t base = (int64_t)A.sample_base * A.probs[A.inl_prob].n_pix;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.n_paths; g += stride)
-        for (int c = 0; c < 3; ++c) out[(base + g) * 3 + c] = A.lacc[(size_t)c * A.qcap + g];
+    const ProblemDev& P = A.probs[A.inl_prob];
+    const int64_t base = (int64_t)A.sample_base * P.n_pix;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < A.n_paths; g += stride) {
+        const int64_t s = g / P.n_pix, local = g - s * P.n_pix;
+        const int64_t o = base + s * P.n_pix + path_pixel(P, (uint32_t)local);
+        for (int c = 0; c < 3; ++c) out[o * 3 + c] = A.lacc[(size_t)c * A.qcap + g];
+    }
 }
 
 // ---------------------------------------------------------------------------------
