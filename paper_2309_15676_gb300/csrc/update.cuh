@@ -31,6 +31,19 @@ struct UpdSeg {
     mer_hyper hyper;
 };
 
+// beta^n for an integer n >= 0 by binary exponentiation (about 2 log2 n double multiplies, a few
+// ulp): every exponent of the update's start-up and bias corrections is a step count, and the
+// general pow is slow in the one FP64 thread that computes the coefficients each iteration
+__host__ __device__ inline double ipow(double beta, long long n) {
+    double r = 1.0, b = beta;
+    while (n > 0) {
+        if (n & 1) r *= b;
+        b *= b;
+        n >>= 1;
+    }
+    return r;
+}
+
 // prod_{j<=k} max(beta, j/(j+1)) in closed form: beta^min(k+1, K) * (k >= K ? K/(k+1) : 1),
 // K the first j with j/(j+1) > beta (MER_META_GROWING_BETA)
 __host__ __device__ inline double growing_prod(double beta, int k) {
@@ -39,7 +52,7 @@ __host__ __device__ inline double growing_prod(double beta, int k) {
     while (K > 0 && (double)(K - 1) / (double)K > beta) --K;
     while ((double)K / (double)(K + 1) <= beta) ++K;
     const long long reps = (long long)k + 1 < K ? (long long)k + 1 : K;
-    double p = pow(beta, (double)reps);
+    double p = ipow(beta, reps);
     if ((long long)k >= K) p *= (double)K / (double)(k + 1);
     return p;
 }
@@ -50,19 +63,19 @@ __host__ __device__ inline UpdCoef update_coef(const mer_hyper& h, int iteration
                                                double n2) {
     UpdCoef k;
     k.pad = 0;
-    const double t = (double)(iteration + 1);
-    k.c1 = (float)(1.0 / (1.0 - pow((double)h.beta1, t)));    // Adam (and NAIVE_ADAM) bias corrections
-    k.c2 = (float)(1.0 / (1.0 - pow((double)h.beta2, t)));
+    const long long t = (long long)iteration + 1;
+    k.c1 = (float)(1.0 / (1.0 - ipow((double)h.beta1, t)));   // Adam (and NAIVE_ADAM) bias corrections
+    k.c2 = (float)(1.0 / (1.0 - ipow((double)h.beta2, t)));
     if (h.mode == MER_MODE_META) {
         const double bf = (double)h.beta_f, bd = (double)h.beta_d;
         if (h.flags & MER_META_GROWING_BETA) {
             const double b = fmax(bf, (double)count_f / (double)(count_f + 1));
             k.cF = (float)((1.0 - b) / (1.0 - growing_prod(bf, count_f)));
         } else {
-            k.cF = (float)((1.0 - bf) / (1.0 - pow(bf, (double)(count_f + 1))));
+            k.cF = (float)((1.0 - bf) / (1.0 - ipow(bf, (long long)count_f + 1)));
         }
         k.stepD = (iteration >= 1 && n2 > 0.0) ? 1 : 0;
-        k.cD = k.stepD ? (float)((1.0 - bd) / (1.0 - pow(bd, (double)(count_d + 1)))) : 0.0f;
+        k.cD = k.stepD ? (float)((1.0 - bd) / (1.0 - ipow(bd, (long long)count_d + 1))) : 0.0f;
         k.norm2 = (float)n2;
         k.inv_norm = k.stepD ? (float)(1.0 / sqrt(n2)) : 0.0f;
     } else {
