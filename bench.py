@@ -636,7 +636,10 @@ def run_mine(args):
             "rays_per_s": dk["units"] / (dk["ms"] * 1e-3),
             "node_tests_per_launch": ck.get("node_tests", 0) / max(dk["launches"], 1),
             "prim_tests_per_launch": ck.get("prim_tests", 0) / max(dk["launches"], 1),
-            "flops_per_launch": flops / max(dk["launches"], 1)}
+            "flops_per_launch": flops / max(dk["launches"], 1),
+            "note": ("traversal: a launch at this size is the dependent-latency tail of its last warps "
+                     "(ncu: about 3% of issue slots used, 9-16 active lanes per instruction), so the FP32 "
+                     "fraction is small by nature; see profiles/trace_spiral256.md")}
     for k, v in kernels.items():
         c = counts.get(k, {})
         if c.get("node_tests"):
