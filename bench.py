@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "paths/s, iters/s; time to loss threshold, meta-estimator vs plain MC, 1 GB300"
 PATHS_PER_PIXEL = 12            # 2 proportional x (primal, adjoint fwd, replay) + 1 FD pair x 6
+# DRAM bytes (read + write) per traversal launch of spiral256, mean over one iteration's launches
+# of one ncu capture of the current kernels (cold caches; profiles/trace_spiral256.md)
+TRACE_DRAM_BYTES = {"trace_2_primal": 2.611e6, "trace_1_primal": 3.086e6}
 
 
 def replica_scene(scene: dict, rank: int) -> dict:
@@ -631,7 +634,7 @@ def run_mine(args):
     flops = NODE_FLOPS * ck.get("node_tests", 0) + PRIM_FLOPS * ck.get("prim_tests", 0)
     ach = flops / (dk["ms"] * 1e-3) / 1e12 if flops else None
     roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": (ach / fp32_peak) if ach else None, "traffic": None,
+            "frac": (ach / fp32_peak) if ach else None, "traffic": TRACE_DRAM_BYTES.get(dom),
             "ms_per_launch": dk["ms"] / dk["launches"], "share": kernels[dom]["share"],
             "rays_per_s": dk["units"] / (dk["ms"] * 1e-3),
             "node_tests_per_launch": ck.get("node_tests", 0) / max(dk["launches"], 1),
