@@ -660,16 +660,28 @@ def run_mine(args):
     tgt_host = target_img.cpu().pin_memory()
     ctx.checkpoint_load(blob)
     torch.cuda.synchronize()
+    # every step: H2D of the step's input (the target, from pinned memory) and D2H of its result
+    # (the loss, into pinned memory); one step in flight, the host reads step k's loss after
+    # enqueueing step k + 1
+    loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    losses = []
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.set_target_host(pid, tgt_host)          # H2D of the step's input
+    for k in range(args.steps):
+        ctx.set_target_async(pid, tgt_host)
         ctx.iterate(1, use_graph=True)
-        ctx.stats(pid)                              # D2H of the step's result (loss)
-    torch.cuda.synchronize()
+        ctx.loss_async(pid, loss_host[k % 2:k % 2 + 1])
+        done[k % 2].record()
+        if k > 0:
+            done[(k - 1) % 2].synchronize()
+            losses.append(float(loss_host[(k - 1) % 2]))
+    done[(args.steps - 1) % 2].synchronize()
+    losses.append(float(loss_host[(args.steps - 1) % 2]))
     e2e_s = time.perf_counter() - t0
+    assert len(losses) == args.steps and all(math.isfinite(x) and x > 0 for x in losses)
     e2e = {"value": world * paths_per_iter * args.steps / e2e_s, "unit": "paths/s",
-           "h2d_bytes_per_step": int(tgt_host.numel() * 4), "d2h_bytes_per_step": 48,
-           "iters_per_s": world * args.steps / e2e_s}
+           "h2d_bytes_per_step": int(tgt_host.numel() * 4), "d2h_bytes_per_step": 8,
+           "iters_per_s": world * args.steps / e2e_s, "last_loss": losses[-1]}
     ctx.close()
 
     # ---- the same iterations with replays that re-trace every ray (no per-vertex hit store) ----

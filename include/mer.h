@@ -260,6 +260,15 @@ mer_status mer_wait_selftest(double limit_s, double* waited_s);
 mer_status mer_params_force(mer_ctx* ctx, int32_t pid, const float* hwc, int32_t on_device);
 /* Set the target image ([height][width][3]). */
 mer_status mer_target_set(mer_ctx* ctx, int32_t pid, const float* img, int32_t on_device);
+/* Asynchronous forms for a host loop that keeps steps in flight (both enqueue on the context
+ * stream, fenced to the caller's stream, and return at once):
+ *  mer_target_set_async: target from host memory img_host ([height][width][3], page-locked for
+ *    the copy to be asynchronous), which must stay unchanged until the context's work up to this
+ *    call has completed;
+ *  mer_loss_async: *loss_host (host memory, page-locked) receives the problem's loss of its last
+ *    gradient step once the context's work up to this call has completed. */
+mer_status mer_target_set_async(mer_ctx* ctx, int32_t pid, const float* img_host);
+mer_status mer_loss_async(mer_ctx* ctx, int32_t pid, double* loss_host);
 /* Render the target image from the given parameters (device HWC texture) with spp samples
  * of stream MER_STREAM_TARGET at iteration 0, and store it as the target. */
 mer_status mer_target_render(mer_ctx* ctx, int32_t pid, const float* tex_dev, int32_t spp);

@@ -106,6 +106,8 @@ SIGNATURES = {
     "mer_volume_opt_state": (ct.c_int, [_vp, ct.POINTER(StateView)]),
     "mer_volume_opt_launches": (ct.c_int, [_vp, ct.POINTER(ct.c_int32)]),
     "mer_target_set": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
+    "mer_target_set_async": (ct.c_int, [_vp, ct.c_int32, _vp]),
+    "mer_loss_async": (ct.c_int, [_vp, ct.c_int32, _vp]),
     "mer_target_render": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32]),
     "mer_render": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp]),
     "mer_render_samples": (ct.c_int, [_vp, ct.c_int32, _vp, ct.c_int32, ct.c_uint32, ct.c_uint32, _vp]),

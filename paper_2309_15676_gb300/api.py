@@ -190,6 +190,16 @@ class Context:
         """Target upload from a (pinned) host tensor."""
         self._ck(self.L.mer_target_set(self.h, pid, _ptr(img_pinned), 0))
 
+    def set_target_async(self, pid: int, img_pinned: torch.Tensor):
+        """Target upload from a pinned host tensor without waiting; the tensor must stay unchanged
+        until the work enqueued so far has completed."""
+        self._ck(self.L.mer_target_set_async(self.h, pid, _ptr(img_pinned)))
+
+    def loss_async(self, pid: int, out_pinned: torch.Tensor):
+        """Enqueue a copy of the problem's last loss into a pinned float64 host tensor (one element);
+        valid once the caller's stream has reached this point (e.g. after an event recorded next)."""
+        self._ck(self.L.mer_loss_async(self.h, pid, _ptr(out_pinned)))
+
     def render_target(self, pid: int, tex, spp: int):
         t = _dev_f32(tex, self.device)
         self._ck(self.L.mer_target_render(self.h, pid, _ptr(t), spp))

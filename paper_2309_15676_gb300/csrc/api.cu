@@ -1129,6 +1129,22 @@ mer_status mer_target_set(mer_ctx* c, int32_t pid, const float* img, int32_t on_
     return copy_in(c, p->target, img, (size_t)p->n_pix * 3, on_device);
 }
 
+mer_status mer_target_set_async(mer_ctx* c, int32_t pid, const float* img) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !img) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_target_set_async");
+    Guard g(c);
+    CK(c, cudaMemcpyAsync(p->target, img, sizeof(float) * 3 * (size_t)p->n_pix, cudaMemcpyHostToDevice, c->st));
+    return MER_OK;
+}
+
+mer_status mer_loss_async(mer_ctx* c, int32_t pid, double* loss_host) {
+    Problem* p = get_prob(c, pid);
+    if (!p || !loss_host) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_loss_async");
+    Guard g(c);
+    CK(c, cudaMemcpyAsync(loss_host, c->d_loss + p->id, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    return MER_OK;
+}
+
 mer_status mer_render(mer_ctx* c, int32_t pid, const float* tex, int32_t spp, uint32_t stream, uint32_t iteration,
                       float* img) {
     Problem* p = get_prob(c, pid);
@@ -1310,7 +1326,7 @@ mer_status mer_stats(mer_ctx* c, int32_t pid, mer_iter_stats* out) {
     CK(c, cudaMemcpyAsync(&la, c->d_loss + pid, sizeof la, cudaMemcpyDeviceToHost, c->st));
     CK(c, cudaStreamSynchronize(c->st));
     out->iteration = ps.iteration;
-    out->loss = la / (3.0 * p->n_pix);
+    out->loss = la;
     out->dpi_norm2 = ps.dpi_norm2;
     out->count_f = ps.count_f;
     out->count_d = ps.count_d;

@@ -345,7 +345,7 @@ int run_scatter(uint32_t* cnt, const Record* rec, int64_t rcap, const ProblemDev
 
 // Image loss (step a7) and its adjoint image, per problem: L2, L = 1/(3N) sum (I - T)^2 with
 // dL/dI = 2 (I - T) / (3N), or MRSE, each term divided by (T^2 + 0.01), for the proportional
-// image (parts & L2_PROP; loss accumulated per problem in FP64) and the two images of the FD pair
+// image (parts & L2_PROP; the loss accumulated per problem in FP64) and the two images of the FD pair
 // (parts & L2_FD). Pixels of all problems are enumerated through the prefix pix_pref.
 __global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs, const int64_t* __restrict__ pix_pref,
                                             int n_probs, int64_t total_pix, int parts, double* loss_acc) {
@@ -383,9 +383,9 @@ __global__ void __launch_bounds__(256) k_l2(const ProblemDev* __restrict__ probs
         const bool same = __all_sync(FULLM, q == q0);
         if (same) {
             for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(FULLM, l, o);
-            if ((threadIdx.x & 31) == 0 && q0 >= 0) atomicAdd(loss_acc + q0, l);
+            if ((threadIdx.x & 31) == 0 && q0 >= 0) atomicAdd(loss_acc + q0, l / (3.0 * (double)probs[q0].n_pix));
         } else if (valid) {
-            atomicAdd(loss_acc + q, l);
+            atomicAdd(loss_acc + q, l / (3.0 * (double)probs[q].n_pix));
         }
     }
 }

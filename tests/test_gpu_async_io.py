@@ -1,0 +1,38 @@
+"""The asynchronous host I/O of a step: mer_target_set_async from pinned memory gives the same
+iterations as mer_target_set, and mer_loss_async delivers the loss mer_stats reports."""
+import numpy as np
+import pytest
+
+from paper_2309_15676_gb300 import synth
+
+from .gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_async_target_and_loss_match_synchronous_calls():
+    torch = need_gpu()
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    w = synth.workload_box(16, 16, 8, max_depth=3)
+    target = np.random.default_rng(2).uniform(0.1, 0.6, (16, 16, 3)).astype(np.float32)
+    out = []
+    for asynchronous in (True, False):
+        ctx = Context(0)
+        pid = ctx.add_scene(w.scene, HyperParams(lr=0.02))
+        ctx.set_params(pid, w.init_tex)
+        if asynchronous:
+            pinned = torch.from_numpy(target).pin_memory()
+            ctx.set_target_async(pid, pinned)
+        else:
+            ctx.set_target(pid, target)
+        ctx.iterate(3, use_graph=True)
+        buf = torch.zeros(1, dtype=torch.float64).pin_memory()
+        ctx.loss_async(pid, buf)
+        torch.cuda.synchronize()
+        st = ctx.stats(pid)
+        assert buf.item() == st["loss"] and st["loss"] > 0
+        out.append((st["loss"], ctx.get_params(pid).cpu().numpy()))
+        ctx.close()
+    (la, pa), (lb, pb) = out
+    assert abs(la - lb) <= 1e-9 * lb
+    assert np.allclose(pa, pb, rtol=0, atol=1e-5)
