@@ -66,3 +66,37 @@ def test_ragged_image_and_two_texel_texture(size):
     else:
         assert np.abs(got).max() == 0.0
     ctx.close()
+
+
+def test_context_at_its_problem_limit():
+    """MER_MAX_PROBLEMS (256) tiny problems in one context: a 257th is refused, and the first and the
+    last problem's gradients in the full batch equal the same problem's alone."""
+    torch = need_gpu()
+    from paper_2309_15676_gb300._lib import MerError
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    ws = [synth.workload_box(8, 8, 4, max_depth=2, key_id=k) for k in range(256)]
+    tgt = np.full((8, 8, 3), 0.3, np.float32)
+    ctx = Context(0)
+    ids = []
+    for w in ws:
+        p = ctx.add_scene(w.scene, HyperParams())
+        ctx.set_target(p, tgt)
+        ctx.set_params(p, w.init_tex)
+        ids.append(p)
+    with pytest.raises(MerError):
+        ctx.add_scene(ws[0].scene, HyperParams())
+    ctx.iterate(1, use_graph=True)
+    ctx.gradient_step()
+    batched = {q: ctx.grads(ids[q])[0].cpu().numpy().astype(np.float64) for q in (0, 255)}
+    ctx.close()
+    for q, F in batched.items():
+        c1 = Context(0)
+        p1 = c1.add_scene(ws[q].scene, HyperParams())
+        c1.set_target(p1, tgt)
+        c1.set_params(p1, ws[q].init_tex)
+        c1.iterate(1, use_graph=True)
+        c1.gradient_step()
+        F1 = c1.grads(p1)[0].cpu().numpy().astype(np.float64)
+        c1.close()
+        assert np.abs(F1).max() > 0
+        assert np.linalg.norm(F - F1) <= 1e-5 * np.linalg.norm(F1), q
