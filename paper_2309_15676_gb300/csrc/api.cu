@@ -78,7 +78,6 @@ struct mer_ctx {
     int32_t n_fd = 0;
     int64_t P_prop = 0, P_fd = 0, total_pix = 0;
     int32_t maxD_prop = 0, maxD_fd = 0, maxD = 0;
-    // wavefront buffers: set 0 (proportional passes, API calls) and set 1 (FD-pair passes)
     // wave sets: 0 proportional primal + replay (and API calls), 1 FD primal + replay,
     // 2 proportional PRB radiance pass, 3 FD PRB radiance pass
     Wave w[4];
