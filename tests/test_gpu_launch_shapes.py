@@ -1,0 +1,62 @@
+"""Launch shapes change speed, not results: the autotuner leaves the optimisation state as it was
+(parameters bit for bit, iteration count), a tuned context continues like an untuned one, and
+contexts with other shapes (BVH top levels staged in shared memory, 256-thread blocks, a per-SM
+block cap) give the same iterations up to the order of float reductions."""
+import numpy as np
+import pytest
+
+from paper_2309_15676_gb300 import synth
+
+from .gpu_common import need_gpu, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(ctx, w, target):
+    from paper_2309_15676_gb300.api import HyperParams
+    pid = ctx.add_scene(w.scene, HyperParams(lr=0.02))
+    ctx.set_target(pid, target)
+    ctx.set_params(pid, w.init_tex)
+    return pid
+
+
+def test_autotune_keeps_state_and_results():
+    need_gpu()
+    from paper_2309_15676_gb300.api import Context
+    w = synth.workload_spiral(48, 40, 64, 16, 32, max_depth=4)
+    target = np.random.default_rng(5).uniform(0.1, 0.8, (40, 48, 3)).astype(np.float32)
+    a, b = Context(0), Context(0)
+    pa, pb = _setup(a, w, target), _setup(b, w, target)
+    a.iterate(2, use_graph=True)
+    b.iterate(2, use_graph=True)
+    before = a.get_params(pa).cpu().numpy().copy()
+    it = a.stats(pa)["iteration"]
+    desc = a.autotune(2)
+    assert isinstance(desc, str) and desc
+    assert np.array_equal(a.get_params(pa).cpu().numpy(), before) and a.stats(pa)["iteration"] == it
+    a.iterate(2, use_graph=True)
+    b.iterate(2, use_graph=True)
+    assert np.allclose(a.get_params(pa).cpu().numpy(), b.get_params(pb).cpu().numpy(), rtol=0, atol=1e-5)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("shape", [dict(smem_nodes=128), dict(block_size=256), dict(blocks_per_sm=2)])
+def test_launch_shapes_give_the_same_iterations(shape):
+    need_gpu()
+    from paper_2309_15676_gb300.api import Context
+    w = synth.workload_spiral(48, 40, 64, 16, 32, max_depth=4)
+    target = np.random.default_rng(6).uniform(0.1, 0.8, (40, 48, 3)).astype(np.float32)
+    out = []
+    for kw in ({}, shape):
+        ctx = Context(0, **kw)
+        pid = _setup(ctx, w, target)
+        ctx.iterate(2, use_graph=True)
+        ctx.gradient_step()
+        F, dF = (x.cpu().numpy().astype(np.float64) for x in ctx.grads(pid))
+        out.append((F, dF, ctx.get_params(pid).cpu().numpy()))
+        ctx.close()
+    (Fa, dFa, pa), (Fb, dFb, pb) = out
+    assert np.abs(Fa).max() > 0
+    assert rel_l2(Fb, Fa) < 1e-5 and rel_l2(dFb, dFa) < 1e-5, (rel_l2(Fb, Fa), rel_l2(dFb, dFa))
+    assert np.allclose(pa, pb, rtol=0, atol=1e-5)
