@@ -63,3 +63,32 @@ def test_empty_volume_shows_background():
     sc = _small(bg=(0.25, 0.5, 0.75))
     img = orc.vol_render_image(orc.Volume(sc), np.zeros((6, 6, 6, 4)), 1, 0, 0)
     assert np.allclose(img, np.array([0.25, 0.5, 0.75]), rtol=0, atol=1e-15)
+
+
+def test_emission_gradient_sums_to_the_pixel_opacity():
+    """With a uniform density the emission gradient of one pixel and channel, summed over all voxels,
+    is sum_k T_k a_k = 1 - T_end whatever the emission: the trilinear weights of every sample sum to
+    one (clamped taps included) and the opacity is what a render with unit emission and a black
+    background returns for the same counters."""
+    n = 6
+    sc = _small(n=n)
+    vol = orc.Volume(sc)
+    rng = np.random.default_rng(11)
+    p = rng.uniform(0.1, 2.0, (n, n, n, 4))
+    p[..., 3] = 0.9                                    # uniform density
+    ones = p.copy()
+    ones[..., :3] = 1.0
+    opacity = orc.vol_render_image(vol, ones, 3, 5, 1)   # unit emission, black background
+    shape = vol.image_shape
+    checked = 0
+    for flat in rng.choice(int(np.prod(shape[:3])), 12, replace=False):
+        v, y, x = np.unravel_index(flat, shape[:3])
+        for ch in range(3):
+            dimg = np.zeros(shape)
+            dimg[v, y, x, ch] = 1.0
+            g = orc.vol_adjoint_image(vol, p, 3, 5, 1, dimg)
+            assert abs(g[..., ch].sum() - opacity[v, y, x, ch]) <= 1e-12, (v, y, x, ch)
+            other = [c for c in range(3) if c != ch]
+            assert np.all(g[..., other] == 0.0)
+            checked += opacity[v, y, x, ch] > 0
+    assert checked > 0
