@@ -291,3 +291,39 @@ def test_uncorrelated_variance_samples():
     s3 = meta.MetaState.zeros((n,))
     meta.meta_update(pi, Fv, np.zeros(n), s3, h, 0.0)
     assert np.allclose(s2.m2f, s3.m2f) and np.allclose(s2.mean, F)
+
+
+@pytest.mark.parametrize("clip", [True, False])
+def test_meta_variance_recurrence_matches_monte_carlo(clip):
+    """Eq. varmeta against simulation: each element is an independent trial of a drifting target
+    theta_i, with F_i = theta_i + N(0, sF^2) and dF_i = theta_i - theta_{i-1} + N(0, sD^2), all
+    noises independent. Fed the true variances, the recurrence's Var must equal the empirical
+    variance of <F_i>_M - theta_i over the trials, the estimate must be unbiased, and the weight
+    (unclipped) must be the one that minimises that variance. Iteration 0 takes the clip in both
+    cases (alpha_0 = 0: the zero initial state carries no information)."""
+    rng = np.random.default_rng(31)
+    n, iters = 400_000, 6
+    sF2, sD2 = 1.0, 0.09
+    h = meta.Hyper()
+    st = meta.MetaState.zeros((n,))
+    theta = np.zeros(n)
+    for i in range(iters):
+        theta_prev = theta
+        theta = theta_prev + 0.3 * np.sin(i + 1.0)
+        F = theta + rng.normal(0.0, np.sqrt(sF2), n)
+        dF = (theta - theta_prev + rng.normal(0.0, np.sqrt(sD2), n)) if i > 0 else np.zeros(n)
+        var_d = np.full(n, sD2 if i > 0 else 0.0)
+        mean_prev, var_prev = st.mean.copy(), st.var.copy()
+        meta.meta_combine(st, F, dF, np.full(n, sF2), var_d, h, clip=clip or i == 0)
+        err = st.mean - theta
+        emp = err.var()
+        assert abs(err.mean()) <= 5.0 * np.sqrt(emp / n), (i, err.mean())
+        assert abs(emp - st.var[0]) <= 5.0 * np.sqrt(2.0 / n) * st.var[0], (i, emp, st.var[0])
+        if i > 0 and not clip:
+            # the same draws recombined with other weights give a larger empirical variance
+            a = st.alpha_prev[0]
+            for da in (-0.1, 0.1):
+                b = a + da
+                other = b * (mean_prev + dF) + (1.0 - b) * F - theta
+                assert other.var() > emp
+            assert np.isclose(a, sF2 / (sF2 + var_prev[0] + sD2), rtol=1e-12)
