@@ -1573,8 +1573,6 @@ mer_status mer_autotune(mer_ctx* c, int32_t trial_iters, char* desc, size_t desc
     float best = 1e30f;
     LaunchShape best_shape = c->shape;
     int best_per_sm = c->cfg.blocks_per_sm;
-    const LaunchShape orig = c->shape;
-    const int orig_per_sm = c->cfg.blocks_per_sm;
     for (int b : blocks)
         for (int ps : per_sm)
             for (int sm : smem) {
@@ -1584,15 +1582,18 @@ mer_status mer_autotune(mer_ctx* c, int32_t trial_iters, char* desc, size_t desc
                 c->shape.smem_nodes = sm;
                 c->cfg.blocks_per_sm = ps;
                 c->graph_dirty = true;
-                // warm-up (also captures the graph)
-                if (mer_iterate(c, 1, 1)) continue;
+                // warm-up (also captures the graph); a shape that fails is skipped
+                if (mer_iterate(c, 1, 1)) {
+                    mer_checkpoint_load(c, saved.data(), saved.size());
+                    continue;
+                }
                 cudaEventRecord(e0, c->st);
-                mer_iterate(c, trial_iters, 1);
+                const mer_status ts = mer_iterate(c, trial_iters, 1);
                 cudaEventRecord(e1, c->st);
                 cudaEventSynchronize(e1);
                 float ms = 0.0f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (cudaGetLastError() == cudaSuccess && ms < best) {
+                if (ts == MER_OK && cudaGetLastError() == cudaSuccess && ms < best) {
                     best = ms;
                     best_shape = c->shape;
                     best_per_sm = ps;
@@ -1601,8 +1602,6 @@ mer_status mer_autotune(mer_ctx* c, int32_t trial_iters, char* desc, size_t desc
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    (void)orig;
-    (void)orig_per_sm;
     c->shape = best_shape;
     c->cfg.blocks_per_sm = best_per_sm;
     c->graph_dirty = true;
