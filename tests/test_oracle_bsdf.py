@@ -86,3 +86,32 @@ def test_sampler_matches_pdf(oracle_lib, th):
             acc[i] = 1.0 / orc.bsdf(1, th, N, wo, wi)[2]
     mean, se = acc.mean(), acc.std() / np.sqrt(n)
     assert abs(mean - 2 * np.pi) < 5 * se + 1e-3, (mean, se)
+
+
+@pytest.mark.parametrize("rough", [0.2, 0.5])
+def test_white_metal_directional_albedo(oracle_lib, rough):
+    """With metal = 1 and base colour 1, F0 = 1 so Fresnel is 1 and only the specular lobe remains;
+    with the Smith masking G1(o) = cos_o / int D(h) max(0, o.h) dw_h the directional albedo
+    int f cos_i dw_i = G1(o)/cos_o int D (o.h) G1(i) dw_h is at most 1 and falls short of 1 only by
+    the shadowing G1(i) < 1, which is small for a smooth surface. Estimated as E[f cos_i / pdf]
+    with the lobe's own sampler (every sample is specular when metal = 1). A dropped cos_o, a wrong
+    1/4 or a Jacobian error in the sampler's pdf moves the estimate out of these bounds."""
+    th = np.array([1.0, 1.0, 1.0, 1.0, rough])
+    rng = np.random.default_rng(17)
+    t = np.cross(N, [1.0, 0.0, 0.0])
+    t /= np.linalg.norm(t)
+    n = 20000
+    low = {0.2: 0.98, 0.5: 0.80}[rough]
+    for deg in (0.0, 30.0, 60.0):
+        a = np.radians(deg)
+        wo = np.cos(a) * N + np.sin(a) * t
+        acc = np.zeros((n, 3))
+        for i, (ul, u1, u2) in enumerate(rng.random((n, 3))):
+            ok, wi = orc.bsdf_sample(1, th, N, wo, ul, u1, u2)
+            if ok:
+                f, _, pdf = orc.bsdf(1, th, N, wo, wi)
+                acc[i] = f * (wi @ N) / pdf
+        mean, se = acc.mean(0), acc.std(0) / np.sqrt(n)
+        assert np.allclose(mean, mean[0], rtol=1e-12)           # grey: F = 1 in every channel
+        assert mean[0] <= 1.0 + 5 * se[0], (deg, mean[0], se[0])
+        assert mean[0] >= low, (deg, mean[0], se[0])
