@@ -133,3 +133,54 @@ def test_glossy_plane_constant_env_is_env_times_albedo(oracle_lib, th):
     albedo = np.array([integrate.quad(f_cos, 0.0, np.pi / 2, args=(c,), epsabs=1e-12, epsrel=1e-10, limit=200)[0]
                        for c in range(3)])
     assert np.all(np.abs(mean - env * albedo) <= 5.0 * se + 1e-6), (mean, env * albedo, se)
+
+
+def _glossy_plane_under_quad_light(le, res, eye):
+    """A principled plane (y = 0, normal +y) seen at its centre from `eye`, and one quad light
+    (centre (0.5, 0.8, 0), side 0.4) facing down at it; no environment."""
+    mb = synth._MeshBuilder()
+    mb.quad((-0.6, 0, 0.6), (1.2, 0, 0), (0, 0, -1.2), mat=0)
+    p0, e1, e2, le = synth._light_quad((0.5, 0.8, 0.0), 0.4, le)
+    mb.quad(p0, e1, e2, mat=1, light=0)
+    up = (0, 0, -1) if eye[0] == 0.0 else (0, 1, 0)
+    return synth._scene(mb.arrays(), mat_type=[synth.PRINCIPLED, synth.LAMBERT], mat_textured=[1, 0],
+                        mat_const=[[0.5] * 5, [0.0] * 5], quads=[synth._quad_row(p0, e1, e2, le)], env=None,
+                        eye=eye, target=(0.0, 0.0, -0.001), up=up, fov_deg=50,
+                        width=res, height=res, tex_c=5, tex_h=8, tex_w=8, max_depth=2)
+
+
+# eye straight above (the light is off the specular lobe: light sampling dominates), and eye at
+# the mirror image of the light (the lobe points at the light: both strategies carry weight)
+@pytest.mark.parametrize("eye,th", [((0.0, 1.0, 0.0), [0.2, 0.5, 0.8, 0.3, 0.4]),
+                                    ((-0.5, 0.8, 0.0), [0.2, 0.5, 0.8, 0.7, 0.3]),
+                                    ((-0.5, 0.8, 0.0), [0.6, 0.4, 0.2, 0.2, 0.6])])
+def test_glossy_plane_under_quad_light_is_the_area_integral(oracle_lib, eye, th):
+    """Direct light only (D = 2) from an area light on a principled surface: the expected value at
+    the point the centre pixels see is the integral over the light's area of
+    Le f(wo, wi) cos_i cos_l / r^2, here by 2D quadrature of the BSDF. It pins the area-to-solid-
+    angle conversion of the light's density and the MIS of light and BSDF sampling for a glossy
+    lobe. The four centre pixels of a 256^2 image cover a region symmetric about that point to
+    first order, so the footprint moves the mean only at second order (about 1e-4 relative, a tenth
+    of the tolerance)."""
+    le = np.array([4.0, 5.0, 6.0])
+    res = 256
+    sc = orc.Scene(_glossy_plane_under_quad_light(tuple(le), res, eye))
+    th = np.array(th)
+    tex = np.tile(th, (8, 8, 1))
+    n = 200_000
+    c0 = res // 2
+    pix = np.array([(c0 - 1) * res + c0 - 1, (c0 - 1) * res + c0, c0 * res + c0 - 1, c0 * res + c0], np.uint32)
+    L = orc.render_samples(sc, tex, np.tile(pix, n // 4), np.repeat(np.arange(n // 4, dtype=np.uint32), 4), 3, 0)
+    mean, se = L.mean(0), L.std(0) / np.sqrt(n)
+    up = np.array([0.0, 1.0, 0.0])
+    wo = np.array(eye) / np.linalg.norm(eye)
+    expected = []
+    for c in range(3):
+        def integrand(z, x):
+            d = np.array([x, 0.8, z])
+            r2 = d @ d
+            wi = d / np.sqrt(r2)
+            return le[c] * orc.bsdf(1, th, up, wo, wi)[0][c] * wi[1] * wi[1] / r2   # cos_i = cos_l = wi_y
+        expected.append(integrate.dblquad(integrand, 0.3, 0.7, -0.2, 0.2, epsabs=1e-10, epsrel=1e-8)[0])
+    expected = np.array(expected)
+    assert np.all(np.abs(mean - expected) <= 5.0 * se), (mean, expected, se)
