@@ -149,7 +149,9 @@ typedef struct mer_scene_desc {
     float eye[3], target[3], up[3];
     float fov_deg;            /* vertical field of view */
     int32_t width, height;
-    int32_t tex_c, tex_h, tex_w; /* parameter texture shape (C in {3, 5}) */
+    int32_t tex_c, tex_h, tex_w; /* parameter texture shape: C in {3, 5}, 1..4094 texels per side
+                                  * (a gradient record packs texel coordinates in 12 bits);
+                                  * otherwise MER_ERR_INVALID_ARG */
     float clamp_lo[8], clamp_hi[8]; /* per-channel parameter range applied after each step */
     int32_t max_depth;        /* path segments (1 = emitters only, 2 = direct light) */
     int32_t spp_prop, spp_fd; /* samples per pixel and iteration */
