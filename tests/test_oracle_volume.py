@@ -92,3 +92,36 @@ def test_emission_gradient_sums_to_the_pixel_opacity():
             assert np.all(g[..., other] == 0.0)
             checked += opacity[v, y, x, ch] > 0
     assert checked > 0
+
+
+def test_jittered_march_counts_the_chord():
+    """Uniform density s and emission 1 over a black background: each sample returns 1 - T_end with
+    T_end = exp(-s delta K), K the number of march samples inside the box. With a 1x1 image and a
+    field of view of 1e-3 degrees every sample's ray is the eye-to-target ray, whose chord l through
+    [-1, 1]^3 is a slab intersection here in numpy. A march started at a uniform jitter within the
+    first step takes floor(l/delta) or ceil(l/delta) samples, l/delta on average; a start without
+    jitter or at a fixed offset gives a biased mean."""
+    n = 6
+    rng = np.random.default_rng(19)
+    for eye, tg in (([2.7, 1.3, -2.1], [0.15, -0.2, 0.3]), ([-0.4, 2.9, 1.1], [0.3, 0.1, -0.5]),
+                    ([3.0, -0.6, 0.2], [-0.2, 0.45, 0.05])):
+        sc = _small(n=n)
+        sc["n_views"], sc["width"], sc["height"] = 1, 1, 1
+        sc["cameras"] = np.asarray([eye + tg + [0.0, 1.0, 0.0] + [1e-3]], np.float32)
+        vol = orc.Volume(sc)
+        p = np.zeros((n, n, n, 4))
+        p[..., :3] = 1.0
+        p[..., 3] = 0.7
+        N = 20000
+        L = orc.vol_render_samples(vol, p, np.zeros(N, np.uint32), np.arange(N, dtype=np.uint32),
+                                   int(rng.integers(100)), 0)
+        delta = float(np.float32(sc["step"]))
+        K = -np.log(1.0 - L[:, 0]) / (0.7 * delta)
+        e = np.float32(eye).astype(np.float64)
+        t = np.float32(tg).astype(np.float64)
+        d = (t - e) / np.linalg.norm(t - e)
+        ta, tb = (-1.0 - e) / d, (1.0 - e) / d
+        chord = np.min(np.maximum(ta, tb)) - np.max(np.minimum(ta, tb))
+        x = chord / delta
+        assert np.all(np.isclose(K, np.floor(x), atol=1e-6) | np.isclose(K, np.ceil(x), atol=1e-6))
+        assert abs(K.mean() - x) <= 5.0 * K.std() / np.sqrt(N) + 1e-6, (K.mean(), x)
