@@ -1,5 +1,6 @@
 """Oracle gradient preconditioner against the stencil it inverts."""
 import numpy as np
+import pytest
 
 from oracle import precond
 
@@ -26,3 +27,23 @@ def test_identity_constant_and_channels():
     assert np.allclose(a[..., 2:3], b, atol=1e-15)
     # smoothing: the preconditioned gradient has less energy at high frequencies
     assert np.sum(precond.laplacian(a[..., 0]) ** 2) < np.sum(precond.laplacian(g[..., 0]) ** 2)
+
+
+def test_matches_the_grid_graph_laplacian_of_a_graph_library():
+    """L is the graph Laplacian D - A of the W x H grid graph (4-neighbour, Neumann boundary =
+    no edges leaving the grid): built here by networkx, independently of the oracle, then the
+    system (I + lam L) x = g solved by a sparse direct solver."""
+    nx = pytest.importorskip("networkx")
+    from scipy.sparse import identity
+    from scipy.sparse.linalg import spsolve
+    rng = np.random.default_rng(2)
+    for H, W, lam in ((5, 7, 2.0), (9, 4, 11.0)):
+        G = nx.grid_2d_graph(H, W)
+        order = [(y, x) for y in range(H) for x in range(W)]       # row-major texels
+        Lg = nx.laplacian_matrix(G, nodelist=order).astype(np.float64).tocsc()
+        g = rng.normal(size=(H, W, 2))
+        for c in range(2):
+            v = g[..., c].reshape(-1)
+            assert np.allclose(precond.laplacian(g[..., c]).reshape(-1), Lg @ v, rtol=0, atol=1e-13)
+            x = spsolve((identity(H * W, format="csc") + lam * Lg), v)
+            assert np.allclose(precond.precondition(g, lam)[..., c].reshape(-1), x, rtol=0, atol=1e-11)
