@@ -722,7 +722,7 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
         (d->n_spheres > 0 && (!d->spheres || !d->sph_mat)) || !d->mat_type || !d->mat_textured || !d->mat_const ||
         (d->n_quads > 0 && !d->quads))
         return fail(c, MER_ERR_INVALID_ARG, "missing scene arrays");
-    if (d->width <= 0 || d->height <= 0 || (int64_t)d->width * d->height > (1ll << 31))
+    if (d->width <= 0 || d->height <= 0 || (int64_t)d->width * d->height > (int64_t)INT32_MAX)
         return fail(c, MER_ERR_INVALID_ARG, "bad image size");
     if (!(d->tex_c == 3 || d->tex_c == 5) || d->tex_w <= 0 || d->tex_h <= 0 || d->tex_w > 4094 || d->tex_h > 4094)
         return fail(c, MER_ERR_INVALID_ARG, "texture must be C in {3,5}, 1..4094 texels per side");
