@@ -147,7 +147,8 @@ typedef struct mer_scene_desc {
     int32_t has_env;
     float env[3];             /* constant environment radiance */
     float eye[3], target[3], up[3];
-    float fov_deg;            /* vertical field of view */
+    float fov_deg;            /* vertical field of view, degrees in (0, 180); eye != target and up not
+                               * parallel to target - eye, else MER_ERR_INVALID_ARG */
     int32_t width, height;
     int32_t tex_c, tex_h, tex_w; /* parameter texture shape: C in {3, 5}, 1..4094 texels per side
                                   * (a gradient record packs texel coordinates in 12 bits);
@@ -219,7 +220,8 @@ typedef struct mer_volume_desc {
     int32_t nx, ny, nz;
     float lo[3], hi[3];
     int32_t n_views, width, height;
-    const float* cameras;     /* HOST [n_views][10]: eye xyz, target xyz, up xyz, fov_deg */
+    const float* cameras;     /* HOST [n_views][10]: eye xyz, target xyz, up xyz, fov_deg (vertical,
+                               * in (0, 180)); a degenerate camera gives MER_ERR_INVALID_ARG */
     float step;               /* march step, world units (> 0) */
     float background[3];
     uint32_t seed, key_id;    /* Philox key */

@@ -933,7 +933,8 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
         r[1] = f[2] * up[0] - f[0] * up[2];
         r[2] = f[0] * up[1] - f[1] * up[0];
         const double lr = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-        if (!(lf > 0) || !(lr > 0)) return bail(fail(c, MER_ERR_INVALID_ARG, "degenerate camera"));
+        if (!(lf > 0) || !(lr > 0) || !(d->fov_deg > 0.0f && d->fov_deg < 180.0f))
+            return bail(fail(c, MER_ERR_INVALID_ARG, "degenerate camera"));
         for (double& x : r) x /= lr;
         u[0] = r[1] * f[2] - r[2] * f[1];
         u[1] = r[2] * f[0] - r[0] * f[2];

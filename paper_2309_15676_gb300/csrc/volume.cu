@@ -361,6 +361,15 @@ extern "C" mer_status mer_volume_create(const mer_volume_desc* d, int32_t device
     if ((int64_t)d->nx * d->ny * d->nz >= ((int64_t)1 << 31) ||
         (int64_t)d->n_views * d->width * d->height >= ((int64_t)1 << 32))
         return mer_internal_fail(MER_ERR_INVALID_ARG, "volume or image too large");
+    for (int i = 0; i < d->n_views; ++i) {
+        // eye != target, up not parallel to the view direction, field of view in (0, 180) degrees
+        const float* c = d->cameras + 10 * i;
+        const double f[3] = {(double)c[3] - c[0], (double)c[4] - c[1], (double)c[5] - c[2]};
+        const double r[3] = {f[1] * c[8] - f[2] * c[7], f[2] * c[6] - f[0] * c[8], f[0] * c[7] - f[1] * c[6]};
+        if (!(f[0] * f[0] + f[1] * f[1] + f[2] * f[2] > 0.0) || !(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] > 0.0) ||
+            !(c[9] > 0.0f && c[9] < 180.0f))
+            return mer_internal_fail(MER_ERR_INVALID_ARG, "degenerate volume camera");
+    }
     if (cudaSetDevice(device) != cudaSuccess) return mer_internal_fail(MER_ERR_CUDA, "bad device");
     mer_volume* v = new mer_volume();
     v->device = device;

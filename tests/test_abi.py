@@ -71,3 +71,23 @@ int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mer_hyper), si
     assert sizes == [ct.sizeof(_lib.Hyper), ct.sizeof(_lib.SceneDesc), ct.sizeof(_lib.Config),
                      ct.sizeof(_lib.IterStats), ct.sizeof(_lib.StateView), ct.sizeof(_lib.VolumeDesc),
                      ct.sizeof(_lib.UpdateArrays), ct.sizeof(_lib.KernelTime)]
+
+
+def test_volume_create_refuses_degenerate_cameras_before_device_work(lib):
+    """mer_volume_create validates every camera (eye != target, up not parallel to the view
+    direction, field of view in (0, 180) degrees) before any CUDA call, on any machine."""
+    from paper_2309_15676_gb300 import _lib
+    good = [3.0, 1.0, 2.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 40.0]
+    bad = [[0.0, 0.0, 0.0] + good[3:],                              # eye == target
+           good[:6] + [-3.0, -1.0, -2.0] + [40.0],                  # up parallel to the view
+           good[:9] + [0.0], good[:9] + [180.0], good[:9] + [float("nan")]]
+    for cam in bad:
+        cams = (ct.c_float * 20)(*(good + cam))                     # the second view is the bad one
+        d = _lib.VolumeDesc(nx=4, ny=4, nz=4, n_views=2, width=8, height=8, step=0.5)
+        for k in range(3):
+            d.lo[k], d.hi[k] = -1.0, 1.0
+        d.cameras = ct.cast(cams, _lib._fp)
+        out = ct.c_void_p()
+        assert lib.mer_volume_create(ct.byref(d), 0, ct.byref(out)) == 1, cam
+        assert out.value is None
+        assert b"degenerate volume camera" in lib.mer_last_error(None)
