@@ -1,5 +1,6 @@
 """The product path has no CPU fallback: without the built CUDA library the binding raises at the
-first call instead of computing anything, and no module of the package imports the oracle."""
+first call instead of computing anything, no module of the package imports the oracle, and the
+oracle and the CUDA sources share no code."""
 import ast
 import os
 
@@ -36,3 +37,23 @@ def test_package_does_not_import_the_oracle():
                 mods = [node.module or ""]
             offenders += [(name, m) for m in mods if m.split(".")[0] == "oracle"]
     assert not offenders, offenders
+
+
+def test_oracle_and_cuda_path_share_no_source():
+    """The oracle's C includes only the C standard library, nothing in the CUDA sources mentions
+    the oracle, and the oracle's Python imports nothing from the product package."""
+    import re
+    ORC = os.path.join(ROOT, "oracle")
+    inc = re.findall(r'#include\s*[<"]([^>"]+)[>"]', open(os.path.join(ORC, "oracle.c")).read())
+    assert set(inc) <= {"math.h", "stdint.h", "stdlib.h", "string.h", "stdio.h"}, inc
+    csrc = os.path.join(PKG, "csrc")
+    for name in os.listdir(csrc):
+        assert "oracle" not in open(os.path.join(csrc, name), errors="replace").read().lower(), name
+    for name in sorted(os.listdir(ORC)):
+        if name.endswith(".py"):
+            tree = ast.parse(open(os.path.join(ORC, name)).read())
+            for node in ast.walk(tree):
+                if isinstance(node, ast.ImportFrom) and node.module:
+                    assert not node.module.startswith("paper_2309_15676_gb300"), (name, node.module)
+                if isinstance(node, ast.Import):
+                    assert not any(a.name.startswith("paper_2309_15676_gb300") for a in node.names), name
