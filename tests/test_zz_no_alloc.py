@@ -7,7 +7,6 @@ that a run stopping at the first failure has already run every other test.
 """
 import ctypes as ct
 
-import numpy as np
 import pytest
 
 from .gpu_common import need_gpu
