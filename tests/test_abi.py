@@ -91,3 +91,39 @@ def test_volume_create_refuses_degenerate_cameras_before_device_work(lib):
         assert lib.mer_volume_create(ct.byref(d), 0, ct.byref(out)) == 1, cam
         assert out.value is None
         assert b"degenerate volume camera" in lib.mer_last_error(None)
+
+
+def test_a_c99_program_links_and_calls_the_library(lib):
+    """The header is plain C: a strict C99 program includes it, links against the built library and
+    calls context-free entry points whose argument checks come before any device work."""
+    import subprocess
+    import tempfile
+    from paper_2309_15676_gb300 import _lib
+    prog = r'''
+#include <stdio.h>
+#include <string.h>
+#include "mer.h"
+int main(void) {
+    mer_hyper h;
+    memset(&h, 0, sizeof h);
+    if (mer_hyper_default(&h) != MER_OK || h.mode != MER_MODE_META) return 1;
+    if (mer_hyper_default(NULL) != MER_ERR_INVALID_ARG) return 2;
+    if (mer_philox(0u, 0u, NULL, 5, NULL, NULL) != MER_ERR_INVALID_ARG) return 3;
+    mer_volume* v = NULL;
+    if (mer_volume_create(NULL, 0, &v) != MER_ERR_INVALID_ARG || v != NULL) return 4;
+    if (mer_last_error(NULL) == NULL) return 5;
+    mer_destroy(NULL);
+    printf("ok %s\n", mer_last_error(NULL));
+    return 0;
+}'''
+    libdir = os.path.dirname(_lib.LIB_PATH)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "consumer.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "consumer")
+        r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                            os.path.join(ROOT, "include"), c, "-o", exe, "-L", libdir, "-lmer",
+                            "-Wl,-rpath," + libdir], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        r = subprocess.run([exe], capture_output=True, text=True)
+        assert r.returncode == 0 and r.stdout.startswith("ok"), (r.returncode, r.stdout, r.stderr)
