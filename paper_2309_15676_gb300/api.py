@@ -63,12 +63,54 @@ def _cur_stream(device):
     return ct.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
-def _dev_f32(x, device):
+def _numel(x) -> int:
+    return x.numel() if isinstance(x, torch.Tensor) else int(np.asarray(x).size)
+
+
+def _need(x, numel, what):
+    """Refuses an array whose element count is not `numel` (the library receives bare pointers: a
+    short array would be read past its end)."""
+    if _numel(x) != numel:
+        raise ValueError(f"{what}: {numel} values expected, got {_numel(x)}")
+    return x
+
+
+def _dev_f32(x, device, numel=None, what="array"):
+    """x as a contiguous float32 tensor on `device`, its element count checked before any copy."""
+    if numel is not None:
+        _need(x, numel, what)
     if isinstance(x, torch.Tensor):
         t = x.to(device=device, dtype=torch.float32)
     else:
         t = torch.as_tensor(np.asarray(x, np.float32), device=device)
     return t.contiguous()
+
+
+def _out_f32(t, device, numel, what="output"):
+    """A caller-supplied output buffer: float32, contiguous, on `device`, with `numel` elements."""
+    if not (isinstance(t, torch.Tensor) and t.dtype == torch.float32 and t.device == torch.device(device)
+            and t.is_contiguous() and t.numel() == numel):
+        raise ValueError(f"{what}: a contiguous float32 tensor of {numel} elements on {device} expected")
+    return t
+
+
+def _dev_buf(t, dtype, numel, what, device=None):
+    """A caller-supplied device tensor handed to the library as is: contiguous, `dtype`, `numel`
+    values (at least `-numel` if negative), on a CUDA device (`device` if given)."""
+    ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+          and (t.numel() == numel if numel >= 0 else t.numel() >= -numel)
+          and (device is None or t.device == device))
+    if not ok:
+        raise ValueError(f"{what}: a contiguous CUDA {dtype} tensor of {abs(numel)} elements expected")
+    return t
+
+
+def _host_buf(t, dtype, numel, what):
+    """A caller-supplied host tensor for the asynchronous copies: contiguous, `dtype`, `numel` values."""
+    if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == dtype and t.is_contiguous()
+            and t.numel() == numel):
+        raise ValueError(f"{what}: a contiguous host {dtype} tensor of {numel} elements expected")
+    return t
 
 
 class _Arr:
@@ -165,14 +207,22 @@ class Context:
         self.images.append((int(scene["height"]), int(scene["width"])))
         return pid.value
 
+    def _ntex(self, pid: int) -> int:
+        h, w, c = self.shapes[pid]
+        return h * w * c
+
+    def _nimg(self, pid: int) -> int:
+        h, w = self.images[pid]
+        return h * w * 3
+
     def set_params(self, pid: int, tex):
-        t = _dev_f32(tex, self.device)
+        t = _dev_f32(tex, self.device, self._ntex(pid), "texture")
         self._ck(self.L.mer_params_set(self.h, pid, _ptr(t), 1))
         torch.cuda.current_stream(self.device).synchronize()
 
     def force_params(self, pid: int, tex):
         """Replace the parameters the last update produced by `tex` (prescribed trajectory)."""
-        t = _dev_f32(tex, self.device)
+        t = _dev_f32(tex, self.device, self._ntex(pid), "texture")
         torch.cuda.current_stream(self.device).synchronize()
         self._ck(self.L.mer_params_force(self.h, pid, _ptr(t), 1))
 
@@ -182,63 +232,76 @@ class Context:
         return out
 
     def set_target(self, pid: int, img):
-        t = _dev_f32(img, self.device)
+        t = _dev_f32(img, self.device, self._nimg(pid), "target image")
         self._ck(self.L.mer_target_set(self.h, pid, _ptr(t), 1))
         torch.cuda.current_stream(self.device).synchronize()
 
     def set_target_host(self, pid: int, img_pinned: torch.Tensor):
         """Target upload from a (pinned) host tensor."""
+        _host_buf(img_pinned, torch.float32, self._nimg(pid), "target image")
         self._ck(self.L.mer_target_set(self.h, pid, _ptr(img_pinned), 0))
 
     def set_target_async(self, pid: int, img_pinned: torch.Tensor):
         """Target upload from a pinned host tensor without waiting; the tensor must stay unchanged
         until the work enqueued so far has completed."""
+        _host_buf(img_pinned, torch.float32, self._nimg(pid), "target image")
         self._ck(self.L.mer_target_set_async(self.h, pid, _ptr(img_pinned)))
 
     def loss_async(self, pid: int, out_pinned: torch.Tensor):
         """Enqueue a copy of the problem's last loss into a pinned float64 host tensor (one element);
         valid once the caller's stream has reached this point (e.g. after an event recorded next)."""
+        _host_buf(out_pinned, torch.float64, 1, "loss")
         self._ck(self.L.mer_loss_async(self.h, pid, _ptr(out_pinned)))
 
     def render_target(self, pid: int, tex, spp: int):
-        t = _dev_f32(tex, self.device)
+        t = _dev_f32(tex, self.device, self._ntex(pid), "texture")
         self._ck(self.L.mer_target_render(self.h, pid, _ptr(t), spp))
         torch.cuda.current_stream(self.device).synchronize()
 
     # ---- renders and adjoints ----
     def render(self, pid, tex=None, spp=1, stream=STREAM_EVAL, iteration=0, out=None) -> torch.Tensor:
         H, W = self.images[pid]
+        if out is not None:
+            _out_f32(out, self.device, H * W * 3, "image")
+        t = None if tex is None else _dev_f32(tex, self.device, self._ntex(pid), "texture")
         out = out if out is not None else torch.empty((H, W, 3), device=self.device, dtype=torch.float32)
-        t = None if tex is None else _dev_f32(tex, self.device)
         self._ck(self.L.mer_render(self.h, pid, _ptr(t), spp, stream, iteration, _ptr(out)))
         return out
 
     def render_samples(self, pid, tex=None, spp=1, stream=STREAM_EVAL, iteration=0) -> torch.Tensor:
         H, W = self.images[pid]
+        t = None if tex is None else _dev_f32(tex, self.device, self._ntex(pid), "texture")
         out = torch.empty((spp, H * W, 3), device=self.device, dtype=torch.float32)
-        t = None if tex is None else _dev_f32(tex, self.device)
         self._ck(self.L.mer_render_samples(self.h, pid, _ptr(t), spp, stream, iteration, _ptr(out)))
         return out
 
     def render_pair(self, pid, texA, texB, spp=1, stream=STREAM_FD_PRIMAL, iteration=0):
         H, W = self.images[pid]
+        n = self._ntex(pid)
+        _need(texA, n, "texture A"), _need(texB, n, "texture B")
+        ta, tb = _dev_f32(texA, self.device), _dev_f32(texB, self.device)
         a = torch.empty((H, W, 3), device=self.device, dtype=torch.float32)
         b = torch.empty_like(a)
-        ta, tb = _dev_f32(texA, self.device), _dev_f32(texB, self.device)
         self._ck(self.L.mer_render_pair(self.h, pid, _ptr(ta), _ptr(tb), spp, stream, iteration, _ptr(a), _ptr(b)))
         return a, b
 
     def adjoint(self, pid, tex, dimg, spp=1, stream=STREAM_EVAL, iteration=0) -> torch.Tensor:
-        g = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
+        if tex is not None:
+            _need(tex, self._ntex(pid), "texture")
+        _need(dimg, self._nimg(pid), "adjoint image")
         t = None if tex is None else _dev_f32(tex, self.device)
         d = _dev_f32(dimg, self.device)
+        g = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
         self._ck(self.L.mer_adjoint(self.h, pid, _ptr(t), _ptr(d), spp, stream, iteration, _ptr(g)))
         return g
 
     def adjoint_pair(self, pid, texA, texB, dimgA, dimgB, spp=1, stream=STREAM_FD_ADJ, iteration=0):
-        g = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
+        n, m = self._ntex(pid), self._nimg(pid)
+        _need(texA, n, "texture A"), _need(texB, n, "texture B")
+        _need(dimgA, m, "adjoint image A"), _need(dimgB, m, "adjoint image B")
         ta, tb = _dev_f32(texA, self.device), _dev_f32(texB, self.device)
         da, db = _dev_f32(dimgA, self.device), _dev_f32(dimgB, self.device)
+        g = torch.empty(self.shapes[pid], device=self.device, dtype=torch.float32)
         self._ck(self.L.mer_adjoint_pair(self.h, pid, _ptr(ta), _ptr(tb), _ptr(da), _ptr(db), spp, stream, iteration,
                                          _ptr(g)))
         return g
@@ -326,8 +389,13 @@ def meta_step_raw(hyper: HyperParams, pi, pi_next, F, dF, m2f, m2d, mean, var, a
                   iteration, count_f, count_d, dpi_norm2, zero_grads=True, out=None):
     """mer_meta_step_raw on torch device tensors; returns the device tensor holding ||dpi||^2."""
     L = _lib.load()
+    n = _dev_buf(pi, torch.float32, -1, "pi").numel()
     dev = pi.device
-    out = out if out is not None else torch.zeros(1, device=dev, dtype=torch.float64)
+    for name, t in (("pi_next", pi_next), ("F", F), ("dF", dF), ("m2f", m2f), ("m2d", m2d), ("mean", mean),
+                    ("var", var), ("alpha_prev", alpha_prev)):
+        _dev_buf(t, torch.float32, n, name, dev)
+    out = (_dev_buf(out, torch.float64, -1, "out", dev) if out is not None
+           else torch.zeros(1, device=dev, dtype=torch.float64))
     lo_a = (ct.c_float * 8)(*([float(x) for x in lo] + [0.0] * (8 - len(lo))))
     hi_a = (ct.c_float * 8)(*([float(x) for x in hi] + [0.0] * (8 - len(hi))))
     h = hyper.to_c()
@@ -371,13 +439,22 @@ class Volume:
         except Exception:
             pass
 
+    def _nvox(self) -> int:
+        return int(np.prod(self.shape))
+
+    def _nimg(self) -> int:
+        return int(np.prod(self.image_shape))
+
     def render(self, params, spp=1, stream=STREAM_EVAL, iteration=0) -> torch.Tensor:
-        p = _dev_f32(params, self.device)
+        p = _dev_f32(params, self.device, self._nvox(), "voxel parameters")
         img = torch.empty(self.image_shape, device=self.device, dtype=torch.float32)
         check(self.L.mer_volume_render(self.h, _ptr(p), spp, stream, iteration, _ptr(img), _cur_stream(self.device)))
         return img
 
     def adjoint(self, params, dimg, spp=1, stream=STREAM_EVAL, iteration=0, grad=None) -> torch.Tensor:
+        _need(params, self._nvox(), "voxel parameters"), _need(dimg, self._nimg(), "adjoint images")
+        if grad is not None:
+            _out_f32(grad, self.device, self._nvox(), "gradient")
         p, d = _dev_f32(params, self.device), _dev_f32(dimg, self.device)
         g = torch.zeros(self.shape, device=self.device, dtype=torch.float32) if grad is None else grad
         check(self.L.mer_volume_adjoint(self.h, _ptr(p), _ptr(d), spp, stream, iteration, _ptr(g),
@@ -385,6 +462,11 @@ class Volume:
         return g
 
     def adjoint_pair(self, pA, pB, dA, dB, spp=1, stream=STREAM_FD_ADJ, iteration=0, grad=None) -> torch.Tensor:
+        nv, ni = self._nvox(), self._nimg()
+        _need(pA, nv, "voxel parameters A"), _need(pB, nv, "voxel parameters B")
+        _need(dA, ni, "adjoint images A"), _need(dB, ni, "adjoint images B")
+        if grad is not None:
+            _out_f32(grad, self.device, nv, "gradient")
         a, b = _dev_f32(pA, self.device), _dev_f32(pB, self.device)
         da, db = _dev_f32(dA, self.device), _dev_f32(dB, self.device)
         g = torch.zeros(self.shape, device=self.device, dtype=torch.float32) if grad is None else grad
@@ -403,8 +485,8 @@ class VolumeOptimizer:
         self.vol = vol                          # kept alive: the optimiser borrows its description
         self.device = vol.device
         hyper = hyper or HyperParams()
-        t = _dev_f32(target, self.device)
-        p = _dev_f32(init, self.device)
+        _need(target, vol._nimg(), "target images"), _need(init, vol._nvox(), "voxel parameters")
+        t, p = _dev_f32(target, self.device), _dev_f32(init, self.device)
         lo_a = (ct.c_float * 4)(*[float(x) for x in lo])
         hi_a = (ct.c_float * 4)(*[float(x) for x in hi])
         h = hyper.to_c()
@@ -426,7 +508,8 @@ class VolumeOptimizer:
             pass
 
     def set_params(self, params):
-        check(self.L.mer_volume_opt_set_params(self.h, _ptr(_dev_f32(params, self.device))))
+        p = _dev_f32(params, self.device, int(np.prod(self.shape)), "voxel parameters")
+        check(self.L.mer_volume_opt_set_params(self.h, _ptr(p)))
 
     def iterate(self, n: int = 1, use_graph: bool = True):
         check(self.L.mer_volume_opt_iterate(self.h, n, int(use_graph), _cur_stream(self.device)))
@@ -463,8 +546,10 @@ class VolumeOptimizer:
 def image_loss(img: torch.Tensor, target: torch.Tensor, kind: int = 0):
     """(loss device double tensor, dLoss/dimg) of an RGB image (mer_image_loss)."""
     L = _lib.load()
-    img = img.contiguous()
-    target = target.contiguous()
+    img = _dev_buf(img.contiguous(), torch.float32, -3, "image")
+    target = _dev_buf(target.contiguous(), torch.float32, img.numel(), "target", img.device)
+    if img.numel() % 3:
+        raise ValueError("image: RGB values expected (a multiple of 3)")
     dimg = torch.empty_like(img)
     loss = torch.zeros(1, device=img.device, dtype=torch.float64)
     check(L.mer_image_loss(kind, img.numel() // 3, _ptr(img), _ptr(target), _ptr(dimg), _ptr(loss),
@@ -477,8 +562,15 @@ def meta_step_raw_ex(hyper: HyperParams, arrays: dict, C, lo, hi, iteration, cou
     """mer_meta_step_raw_ex on torch device tensors (dict keys as in mer_update_arrays; absent keys
     are NULL); returns the device tensor holding ||dpi||^2."""
     L = _lib.load()
+    n = _dev_buf(arrays["pi"], torch.float32, -1, "pi").numel()
     dev = arrays["pi"].device
-    out = out if out is not None else torch.zeros(1, device=dev, dtype=torch.float64)
+    for name, t in arrays.items():
+        if name not in {f for f, _ in _lib.UpdateArrays._fields_}:
+            raise ValueError(f"unknown update array {name!r}")
+        if t is not None:
+            _dev_buf(t, torch.float32, n, name, dev)
+    out = (_dev_buf(out, torch.float64, -1, "out", dev) if out is not None
+           else torch.zeros(1, device=dev, dtype=torch.float64))
     lo_a = (ct.c_float * 8)(*([float(x) for x in lo] + [0.0] * (8 - len(lo))))
     hi_a = (ct.c_float * 8)(*([float(x) for x in hi] + [0.0] * (8 - len(hi))))
     A = _lib.UpdateArrays()
@@ -494,6 +586,9 @@ def philox(k0: int, k1: int, ctr: torch.Tensor) -> torch.Tensor:
     """Philox4x32-10 of int32/uint32-bit counters [n, 4] (device) under key (k0, k1)."""
     L = _lib.load()
     ctr = ctr.contiguous()
+    if not (ctr.is_cuda and ctr.dim() == 2 and ctr.shape[1] == 4 and ctr.element_size() == 4
+            and not ctr.is_floating_point()):
+        raise ValueError("ctr: a CUDA tensor of 32-bit integer counters [n, 4] expected")
     out = torch.empty_like(ctr)
     check(L.mer_philox(k0 & 0xFFFFFFFF, k1 & 0xFFFFFFFF, _ptr(ctr), ctr.shape[0], _ptr(out), _cur_stream(ctr.device)))
     return out
