@@ -66,6 +66,9 @@ typedef int mer_status;
 /* MER_META_UNCORRELATED draws its independent variance samples from the four gradient streams
  * shifted by this offset (streams 8..11) */
 #define MER_STREAM_VAR_OFFSET 8u
+/* largest stream id a caller may pass (the id fills the counter word's upper 16 bits); larger ids
+ * give MER_ERR_INVALID_ARG */
+#define MER_STREAM_MAX 0xFFFFu
 
 /* Image loss of step a7 (N pixels, 3 channels, target T, image I):
  *  L2    L = 1/(3N) sum (I - T)^2,               dL/dI = 2 (I - T) / (3N)

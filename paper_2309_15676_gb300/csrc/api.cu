@@ -1148,7 +1148,7 @@ mer_status mer_loss_async(mer_ctx* c, int32_t pid, double* loss_host) {
 mer_status mer_render(mer_ctx* c, int32_t pid, const float* tex, int32_t spp, uint32_t stream, uint32_t iteration,
                       float* img) {
     Problem* p = get_prob(c, pid);
-    if (!p || !img || spp < 1) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_render");
+    if (!p || !img || spp < 1 || stream > MER_STREAM_MAX) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_render");
     Guard g(c);
     const int64_t ch = chunk_spp(c, p, spp);
     for (int64_t s0 = 0; s0 < spp; s0 += ch) {
@@ -1173,7 +1173,8 @@ mer_status mer_target_render(mer_ctx* c, int32_t pid, const float* tex, int32_t 
 mer_status mer_render_samples(mer_ctx* c, int32_t pid, const float* tex, int32_t spp, uint32_t stream,
                               uint32_t iteration, float* out) {
     Problem* p = get_prob(c, pid);
-    if (!p || !out || spp < 1) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_render_samples");
+    if (!p || !out || spp < 1 || stream > MER_STREAM_MAX)
+        return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_render_samples");
     Guard g(c);
     const int64_t ch = chunk_spp(c, p, spp);
     for (int64_t s0 = 0; s0 < spp; s0 += ch) {
@@ -1192,7 +1193,7 @@ mer_status mer_render_samples(mer_ctx* c, int32_t pid, const float* tex, int32_t
 mer_status mer_render_pair(mer_ctx* c, int32_t pid, const float* texA, const float* texB, int32_t spp, uint32_t stream,
                            uint32_t iteration, float* imgA, float* imgB) {
     Problem* p = get_prob(c, pid);
-    if (!p || !texA || !texB || !imgA || !imgB || spp < 1)
+    if (!p || !texA || !texB || !imgA || !imgB || spp < 1 || stream > MER_STREAM_MAX)
         return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_render_pair");
     Guard g(c);
     const int64_t ch = chunk_spp(c, p, spp);
@@ -1241,14 +1242,15 @@ static mer_status adjoint_impl(mer_ctx* c, Problem* p, int nb, const float* texA
 mer_status mer_adjoint(mer_ctx* c, int32_t pid, const float* tex, const float* dimg, int32_t spp, uint32_t stream,
                        uint32_t iteration, float* grad) {
     Problem* p = get_prob(c, pid);
-    if (!p || !dimg || !grad || spp < 1) return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_adjoint");
+    if (!p || !dimg || !grad || spp < 1 || stream > MER_STREAM_MAX)
+        return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_adjoint");
     return adjoint_impl(c, p, 1, tex, nullptr, dimg, nullptr, spp, stream, iteration, grad);
 }
 
 mer_status mer_adjoint_pair(mer_ctx* c, int32_t pid, const float* texA, const float* texB, const float* dA,
                             const float* dB, int32_t spp, uint32_t stream, uint32_t iteration, float* grad) {
     Problem* p = get_prob(c, pid);
-    if (!p || !texA || !texB || !dA || !dB || !grad || spp < 1)
+    if (!p || !texA || !texB || !dA || !dB || !grad || spp < 1 || stream > MER_STREAM_MAX)
         return fail(c, MER_ERR_INVALID_ARG, "bad arguments to mer_adjoint_pair");
     return adjoint_impl(c, p, 2, texA, texB, dA, dB, spp, stream, iteration, grad);
 }

@@ -486,7 +486,7 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 extern "C" mer_status mer_volume_render(mer_volume* v, const float* params, int32_t spp, uint32_t stream,
                                         uint32_t iteration, float* img, void* cuda_stream) {
-    if (!v || !params || !img || spp < 1 || !aligned16(params))
+    if (!v || !params || !img || spp < 1 || !aligned16(params) || stream > MER_STREAM_MAX)
         return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_render");
     cudaSetDevice(v->device);
     const int64_t N = (int64_t)v->dev.views * v->dev.width * v->dev.height;
@@ -500,7 +500,8 @@ extern "C" mer_status mer_volume_render(mer_volume* v, const float* params, int3
 
 static mer_status vol_adjoint(mer_volume* v, const float* pA, const float* pB, const float* dA, const float* dB,
                               int32_t spp, uint32_t stream, uint32_t iteration, float* grad, void* cuda_stream) {
-    if (!v || !pA || !dA || !grad || spp < 1 || !aligned16(pA) || !aligned16(grad) || (pB && (!dB || !aligned16(pB))))
+    if (!v || !pA || !dA || !grad || spp < 1 || !aligned16(pA) || !aligned16(grad) || (pB && (!dB || !aligned16(pB))) ||
+        stream > MER_STREAM_MAX)
         return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_adjoint");
     cudaSetDevice(v->device);
     VolSel S{};
