@@ -127,3 +127,23 @@ int main(void) {
         assert r.returncode == 0, r.stderr
         r = subprocess.run([exe], capture_output=True, text=True)
         assert r.returncode == 0 and r.stdout.startswith("ok"), (r.returncode, r.stdout, r.stderr)
+
+
+def test_binding_constants_match_the_header():
+    """Every constant the header defines and the binding (or the oracle's stream ids) repeats has
+    the header's value: error codes, modes, stream ids, loss kinds, variant flags, limits."""
+    from oracle import orc
+    from paper_2309_15676_gb300 import _lib, api
+    src = open(os.path.join(ROOT, "include", "mer.h")).read()
+    defs = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define MER_(\w+)\s+(0x[0-9A-Fa-f]+|\d+)u?\b", src)}
+    assert len(defs) >= 30
+    checked = 0
+    for name, v in defs.items():
+        for mod in (api, _lib):
+            if hasattr(mod, name):
+                assert getattr(mod, name) == v, (name, getattr(mod, name), v)
+                checked += 1
+    assert checked >= 20
+    assert {k: n for k, n in _lib.ERRORS.items()} == {v: "MER_" + k for k, v in defs.items() if k.startswith("ERR_")}
+    for s in ("PROP_PRIMAL", "PROP_ADJ", "FD_PRIMAL", "FD_ADJ", "TARGET", "EVAL"):
+        assert getattr(orc, "ST_" + s) == defs["STREAM_" + s], s
