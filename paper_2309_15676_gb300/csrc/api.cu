@@ -744,6 +744,18 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     for (int i = 0; i < d->n_spheres; ++i)
         if (d->sph_mat[i] < 0 || d->sph_mat[i] >= d->n_mats || !(d->spheres[8 * i + 3] > 0.0f))
             return fail(c, MER_ERR_INVALID_ARG, "bad sphere %d", i);
+    for (int i = 0; i < d->n_quads; ++i) {
+        // the light's area density divides by |e1 x e2|; its emission must be a radiance
+        const float* q = d->quads + 12 * i;
+        const double cx = (double)q[4] * q[8] - (double)q[5] * q[7], cy = (double)q[5] * q[6] - (double)q[3] * q[8],
+                     cz = (double)q[3] * q[7] - (double)q[4] * q[6];
+        if (!(cx * cx + cy * cy + cz * cz > 0.0) || !(q[9] >= 0.0f && q[10] >= 0.0f && q[11] >= 0.0f) ||
+            !std::isfinite(q[9] + q[10] + q[11]))
+            return fail(c, MER_ERR_INVALID_ARG, "quad light %d has no area or a bad emission", i);
+    }
+    for (int k = 0; k < d->tex_c; ++k)
+        if (!(d->clamp_lo[k] <= d->clamp_hi[k]))
+            return fail(c, MER_ERR_INVALID_ARG, "parameter range of channel %d is empty", k);
     cudaSetDevice(c->device);
 
     Problem* p = new Problem();
@@ -754,13 +766,9 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
         mer_hyper_default(&p->hyper);
         p->hyper.flags = fl;
     }
-    if (!(p->hyper.precond_lambda >= 0.0f) || !std::isfinite(p->hyper.precond_lambda)) {
+    if (const char* why = hyper_problem(p->hyper)) {
         delete p;
-        return fail(c, MER_ERR_INVALID_ARG, "precond_lambda must be finite and >= 0");
-    }
-    if (p->hyper.flags & ~127) {
-        delete p;
-        return fail(c, MER_ERR_INVALID_ARG, "unknown MER_META_* flag bits");
+        return fail(c, MER_ERR_INVALID_ARG, "%s", why);
     }
     p->meta = p->hyper.mode == MER_MODE_META;
     p->max_depth = d->max_depth;
@@ -1436,6 +1444,7 @@ mer_status mer_meta_step_raw_ex(const mer_hyper* hyper, int64_t n, int32_t C, co
                                 int32_t count_d, double dpi_norm2, int32_t zero_grads, double* out, void* stream) {
     if (!hyper || !arrays || n < 0 || C < 1 || C > 8 || !lo || !hi || !out)
         return fail(nullptr, MER_ERR_INVALID_ARG, "bad arguments to mer_meta_step_raw");
+    if (const char* why = hyper_problem(*hyper)) return fail(nullptr, MER_ERR_INVALID_ARG, "%s", why);
     const mer_update_arrays& A = *arrays;
     const bool meta = hyper->mode == MER_MODE_META;
     const int fl = meta ? hyper->flags : 0;

@@ -28,6 +28,18 @@ constexpr int64_t UPD_CHUNK = (int64_t)UPD_THREADS * UPD_VEC_PER_THREAD * 4;   /
 
 int64_t update_blocks_for(int64_t n) { return (n + UPD_CHUNK - 1) / UPD_CHUNK; }
 
+const char* hyper_problem(const mer_hyper& h) {
+    auto decay = [](float b) { return b >= 0.0f && b < 1.0f; };
+    auto nonneg = [](float x) { return x >= 0.0f && x < INFINITY; };
+    if (h.mode != MER_MODE_META && h.mode != MER_MODE_ADAM) return "unknown optimiser mode";
+    if (h.flags & ~127) return "unknown MER_META_* flag bits";
+    if (!decay(h.beta_f) || !decay(h.beta_d) || !decay(h.beta1) || !decay(h.beta2))
+        return "EMA decays must lie in [0, 1)";
+    if (!nonneg(h.lr) || !nonneg(h.eps) || !nonneg(h.eps_alpha) || !nonneg(h.precond_lambda))
+        return "lr, eps, eps_alpha and precond_lambda must be finite and >= 0";
+    return nullptr;
+}
+
 using Coef = UpdCoef;
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
@@ -400,6 +412,7 @@ extern "C" mer_status mer_meta_step_raw_noalloc(const mer_hyper* hyper, int64_t 
     using namespace mer;
     if (!hyper || n < 0 || C < 1 || C > 8 || !lo || !hi || !dpi_norm2_out)
         return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_meta_step_raw_noalloc");
+    if (const char* why = hyper_problem(*hyper)) return mer_internal_fail(MER_ERR_INVALID_ARG, why);
     const bool meta = hyper->mode == MER_MODE_META;
     if (n > 0 && (!pi || !pi_next || !F || !m2f || !mean || (meta && (!dF || !m2d || !var || !alpha_prev))))
         return mer_internal_fail(MER_ERR_INVALID_ARG, "missing arrays in mer_meta_step_raw_noalloc");

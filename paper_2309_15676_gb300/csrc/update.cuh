@@ -88,6 +88,10 @@ __host__ __device__ inline UpdCoef update_coef(const mer_hyper& h, int iteration
 int64_t update_blocks_for(int64_t n);
 // records a context-free error message (thread-local) and returns code
 int mer_internal_fail(int code, const char* msg);
+// why a hyper-parameter set cannot run (a mode other than META / ADAM, unknown flag bits, a decay
+// outside [0, 1) whose start-up correction would divide by zero, a negative or non-finite rate,
+// epsilon or preconditioning weight), or nullptr
+const char* hyper_problem(const mer_hyper& h);
 cudaError_t launch_update_ctx(const UpdSeg* segs_dev, const int64_t* blk_off_dev, int n_segs, int64_t total_blocks,
                               ProbState* ps, double* partials, cudaStream_t st);
 // ||pnew - pold||^2 over n parameters (one block, fixed order) into ps->dpi_norm2, and the next

@@ -661,9 +661,7 @@ extern "C" mer_status mer_volume_opt_create(mer_volume* vol, const mer_hyper* hy
                                             const float* init, mer_volume_opt** out) {
     if (!vol || !hyper || !lo || !hi || !target || !init || !out || !aligned16(init))
         return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_volume_opt_create");
-    if (hyper->mode != MER_MODE_META && hyper->mode != MER_MODE_ADAM)
-        return mer_internal_fail(MER_ERR_INVALID_ARG, "unknown optimiser mode");
-    if (hyper->flags & ~127) return mer_internal_fail(MER_ERR_INVALID_ARG, "unknown MER_META_* flag bits");
+    if (const char* why = hyper_problem(*hyper)) return mer_internal_fail(MER_ERR_INVALID_ARG, why);
     if (hyper->precond_lambda != 0.0f)
         return mer_internal_fail(MER_ERR_INVALID_ARG, "gradient preconditioning applies to textures only");
     if (loss_kind != MER_LOSS_L2 && loss_kind != MER_LOSS_MRSE)

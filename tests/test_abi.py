@@ -147,3 +147,25 @@ def test_binding_constants_match_the_header():
     assert {k: n for k, n in _lib.ERRORS.items()} == {v: "MER_" + k for k, v in defs.items() if k.startswith("ERR_")}
     for s in ("PROP_PRIMAL", "PROP_ADJ", "FD_PRIMAL", "FD_ADJ", "TARGET", "EVAL"):
         assert getattr(orc, "ST_" + s) == defs["STREAM_" + s], s
+
+
+@pytest.mark.parametrize("field,value,why", [
+    ("beta_f", 1.0, b"decays"), ("beta_d", -0.1, b"decays"), ("beta2", 1.5, b"decays"), ("beta1", float("nan"), b"decays"),
+    ("lr", -1.0, b"finite"), ("lr", float("nan"), b"finite"), ("eps", float("inf"), b"finite"),
+    ("precond_lambda", -2.0, b"finite"), ("mode", 7, b"mode"), ("flags", 1 << 10, b"flag")])
+def test_update_refuses_hyper_parameters_it_cannot_run(lib, field, value, why):
+    """A decay of 1 would divide the start-up correction by zero; negative or non-finite rates and
+    epsilons, unknown modes and flag bits are refused before any device work, by both standalone
+    update entry points (and by the scene and volume-optimiser constructors, which share the check)."""
+    from paper_2309_15676_gb300 import _lib
+    h = _lib.Hyper()
+    assert lib.mer_hyper_default(ct.byref(h)) == 0
+    setattr(h, field, value)
+    lo, hi = (ct.c_float * 8)(), (ct.c_float * 8)(*([1.0] * 8))
+    out = ct.c_double()
+    st = lib.mer_meta_step_raw(ct.byref(h), 0, 3, lo, hi, None, None, None, None, None, None, None, None, None,
+                               0, 0, 0, 0.0, 1, ct.byref(out), None)
+    assert st == 1 and why in lib.mer_last_error(None), (st, lib.mer_last_error(None))
+    st = lib.mer_meta_step_raw_noalloc(ct.byref(h), 0, 3, lo, hi, None, None, None, None, None, None, None, None,
+                                       None, 0, 0, 0, 0.0, 1, ct.byref(out), None)
+    assert st == 1 and why in lib.mer_last_error(None), (st, lib.mer_last_error(None))
