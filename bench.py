@@ -5,12 +5,16 @@ Workload (one optimisation iteration = one step, steps a1-a11 of the hot path):
   spiral256: 256x256 image, procedural spiral tube of 8192 triangles over a ground quad,
   principled BSDF with 256x256x5 fp32 textures (base colour, metalness, roughness; seeded
   value-noise init and target), constant environment + 1 area light, max depth 5,
-  1 FD + 2 proportional spp per iteration (12 path traversals per pixel).
+  1 FD + 2 proportional spp per iteration (12 path traversals per pixel). The adjoint replays
+  every path from its counters and traces its rays again (path replay, no stored vertices).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--detail-out PATH]
 
-Prints one JSON line (rank 0). With torchrun (N > 1) every rank optimises its own replica of
-the problem (different Philox key): weak scaling, no collective on the data path.
+The LAST stdout line is the compact headline JSON (rank 0). The side measurements (per-kernel
+table, hit-store variant, batched, 1024^2 scale, volume, time to threshold) are printed before
+it, one JSON line each ({"bench_leg": name, ...}), and with --detail-out also written to PATH.
+With torchrun (N > 1) every rank optimises its own replica of the problem (different Philox
+key): weak scaling, no collective on the data path.
 """
 from __future__ import annotations
 
@@ -28,10 +32,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "paths/s, iters/s; time to loss threshold, meta-estimator vs plain MC, 1 GB300"
 PATHS_PER_PIXEL = 12            # 2 proportional x (primal, adjoint fwd, replay) + 1 FD pair x 6
-# DRAM bytes (read + write) per traversal launch of spiral256, mean over one iteration's launches
-# of one ncu capture of the current kernels (cold caches; profiles/trace_spiral256.md)
-TRACE_DRAM_BYTES = {"trace_2_primal": 2.611e6, "trace_1_primal": 3.086e6}
-
+# DRAM bytes (read + write) per launch of the traversal kernels, from one ncu capture of the
+# spiral256 iteration with re-tracing replays; "source" names the commit the kernels were
+# captured at, and the bench reports the figure only while the traversal source is unchanged
+# since then (its sha1 is compared), else null.
+TRACE_DRAM = {"source": None, "trace_cu_sha1": None, "bytes": {}}
 
 def replica_scene(scene: dict, rank: int) -> dict:
     """Each rank optimises its own replica: the same problem under its own Philox key."""
@@ -72,6 +77,7 @@ def parse(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-volume", action="store_true", help="skip the 256^3 volume leg")
     ap.add_argument("--only-volume", action="store_true", help="run only the volume leg (for profiling)")
+    ap.add_argument("--detail-out", default=None, help="also write every side measurement to this JSON file")
     return ap.parse_args(argv)
 
 
@@ -160,98 +166,136 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------------------
-# CPU baseline: the FP64 oracle as it stands, single thread, on a bounded sample of paths
+# CPU baseline and reference arm: the FP64 oracle as it stands, on a bounded sample of paths
 # ----------------------------------------------------------------------------------------
-def cpu_baseline(w, budget_s=15.0):
-    import numpy as np
-    from oracle import orc
-    sc = orc.Scene(w.scene)
-    tex = w.init_tex.astype(np.float64)
-    npix = w.scene["width"] * w.scene["height"]
-    rng = np.random.default_rng(0)
-    done_paths, elapsed, n = 0, 0.0, 8
-    adj = np.full((1, 3), 1e-3)
-    while elapsed < budget_s:
-        pix = rng.integers(0, npix, n).astype(np.uint32)
-        smp = rng.integers(0, 4, n).astype(np.uint32)
-        t0 = time.perf_counter()
-        orc.render_samples(sc, tex, pix, smp, 1, orc.ST_PROP_PRIMAL)          # primal traversals
-        orc.adjoint_samples(sc, tex, pix, smp, 1, orc.ST_PROP_ADJ,            # forward + replay traversals
-                            np.repeat(adj, n, 0))
-        dt = time.perf_counter() - t0
-        done_paths += 3 * n
-        elapsed += dt
-        n = int(min(4 * n, max(8, n * (budget_s - elapsed) / max(dt, 1e-3))))
-        if elapsed >= 0.9 * budget_s:
-            break
-    return {"value": done_paths / elapsed, "unit": "paths/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done_paths} path traversals (primal + PRB forward + replay) of the spiral256 scene, "
-                      f"random pixels, FP64 brute-force intersection, single thread, {elapsed:.1f} s"}
+def workload_config(world: int = 1) -> dict:
+    """The workload both arms measure (the headline's `config`)."""
+    return {"workload": "spiral256", "image": [256, 256], "triangles": 8192, "texture": [256, 256, 5],
+            "max_depth": 5, "spp_prop": 2, "spp_fd": 1, "paths_per_iter": PATHS_PER_PIXEL * 256 * 256,
+            "adjoint": "path replay re-tracing every ray (no stored vertices)",
+            "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{world}"}
 
 
-def _cpu_worker(seed, budget_s):
-    """One process of the parallel CPU baseline: the oracle's loop of cpu_baseline on its own pixels;
-    returns (path traversals, seconds)."""
+_ORC = {}
+
+
+def _orc_init():
+    """Per-process oracle state: the spiral256 scene and its initial parameters (FP64)."""
     import numpy as np
     from oracle import orc
     from paper_2309_15676_gb300 import synth
     w = synth.workload_spiral()
-    sc = orc.Scene(w.scene)
-    tex = w.init_tex.astype(np.float64)
-    npix = w.scene["width"] * w.scene["height"]
-    rng = np.random.default_rng(1000 + seed)
-    done, elapsed, n = 0, 0.0, 8
-    adj = np.full((1, 3), 1e-3)
+    _ORC["orc"] = orc
+    _ORC["sc"] = orc.Scene(w.scene)
+    _ORC["tex"] = w.init_tex.astype(np.float64)
+    _ORC["npix"] = w.scene["width"] * w.scene["height"]
+
+
+def _orc_paths(n: int, seed: int):
+    """n random (pixel, sample) paths of spiral256 through the oracle: primal radiance, then the PRB
+    adjoint (radiance pass + replay); returns (path traversals, seconds)."""
+    import numpy as np
+    if not _ORC:
+        _orc_init()
+    orc, sc, tex, npix = _ORC["orc"], _ORC["sc"], _ORC["tex"], _ORC["npix"]
+    rng = np.random.default_rng(seed)
+    pix = rng.integers(0, npix, n).astype(np.uint32)
+    smp = rng.integers(0, 4, n).astype(np.uint32)
+    adj = np.full((n, 3), 1e-3)
+    t0 = time.perf_counter()
+    orc.render_samples(sc, tex, pix, smp, 1, orc.ST_PROP_PRIMAL)
+    orc.adjoint_samples(sc, tex, pix, smp, 1, orc.ST_PROP_ADJ, adj)
+    return 3 * n, time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s=15.0):
+    """Single thread: the oracle's paths in growing batches until about budget_s of work."""
+    done_paths, elapsed, n, k = 0, 0.0, 8, 0
     while elapsed < 0.9 * budget_s:
-        pix = rng.integers(0, npix, n).astype(np.uint32)
-        smp = rng.integers(0, 4, n).astype(np.uint32)
-        t0 = time.perf_counter()
-        orc.render_samples(sc, tex, pix, smp, 1, orc.ST_PROP_PRIMAL)
-        orc.adjoint_samples(sc, tex, pix, smp, 1, orc.ST_PROP_ADJ, np.repeat(adj, n, 0))
-        dt = time.perf_counter() - t0
-        done += 3 * n
+        p, dt = _orc_paths(n, k)
+        done_paths += p
         elapsed += dt
+        k += 1
         n = int(min(4 * n, max(8, n * (budget_s - elapsed) / max(dt, 1e-3))))
-    return done, elapsed
+    return {"value": done_paths / elapsed, "unit": "paths/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done_paths} path traversals (primal + PRB radiance pass + replay) of spiral256 at random "
+                      f"pixels, FP64, brute-force intersection, one thread, {elapsed:.1f} s"}
+
+
+class OraclePool:
+    """The oracle in one spawned process per host core (spawn: no CUDA state is inherited). A step
+    gives every process the same number of random paths; its time is the wall time of the step."""
+
+    def __init__(self, workers=None):
+        import multiprocessing as mp
+        self.workers = workers or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_orc_init)
+        self.k = 0
+
+    def step(self, n_per_worker: int):
+        t0 = time.perf_counter()
+        res = self.pool.starmap(_orc_paths, [(n_per_worker, 1000 * self.k + i) for i in range(self.workers)])
+        self.k += 1
+        return sum(r[0] for r in res), time.perf_counter() - t0
+
+    def calibrate(self, target_s: float) -> int:
+        """Paths per process so that a step takes about target_s (two untimed probes)."""
+        n = 16
+        for _ in range(2):
+            _, dt = self.step(n)
+            n = max(8, int(n * target_s / max(dt, 1e-3)))
+        return n
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def cpu_baseline_parallel(budget_s=10.0, workers=None):
-    """The same oracle loop in one process per host core (spawned, so that no CUDA state is inherited):
-    whole-host paths/s = the processes' traversals over the slowest one's time."""
-    import multiprocessing as mp
-    workers = workers or os.cpu_count() or 1
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(workers) as pool:
-        res = pool.starmap(_cpu_worker, [(k, budget_s) for k in range(workers)])
-    paths = sum(r[0] for r in res)
-    secs = max(r[1] for r in res)
-    return {"value": paths / secs, "unit": "paths/s", "cores": workers, "kind": "oracle",
-            "sample": f"{paths} path traversals in {workers} processes, {secs:.1f} s each"}
+    """The oracle's paths in one process per host core for about budget_s: whole-host paths/s."""
+    op = OraclePool(workers)
+    n = op.calibrate(budget_s / 4)
+    paths, secs = 0, 0.0
+    for _ in range(4):
+        p, dt = op.step(n)
+        paths += p
+        secs += dt
+    op.close()
+    return {"value": paths / secs, "unit": "paths/s", "cores": op.workers, "kind": "oracle",
+            "sample": f"{paths} path traversals in {op.workers} processes, 4 steps, {secs:.1f} s"}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle as it stands on this host's cores, same workload and metric."""
+    """Reference arm: the FP64 oracle as it stands on this host's cores (one spawned process per
+    core), same workload and metric. A step is a bounded sample of the workload: every process
+    runs the same number of random spiral256 paths (primal + PRB radiance pass + replay), sized so
+    that a step takes about two seconds; ms_per_step is the measured wall time of a step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle.build
     oracle.build.build()
-    w = workload()
-    steps = []
+    op = OraclePool()
+    n = op.calibrate(2.0)
     for _ in range(max(args.warmup, 0)):
-        cpu_baseline(w, budget_s=0.3)
-    for _ in range(max(args.steps, 1)):   # the whole arm takes about a minute of host time
-        steps.append(cpu_baseline(w, budget_s=max(0.3, 45.0 / max(args.steps, 1))))
-    v = sum(s["value"] for s in steps) / len(steps)
-    iters = v / (PATHS_PER_PIXEL * w.scene["width"] * w.scene["height"])
+        op.step(n)
+    paths, secs = 0, 0.0
+    for _ in range(max(args.steps, 1)):
+        p, dt = op.step(n)
+        paths += p
+        secs += dt
+    op.close()
+    steps = max(args.steps, 1)
+    v = paths / secs
+    iters = v / (PATHS_PER_PIXEL * 256 * 256)
+    sample = (f"each step: {op.workers} processes x {n} random spiral256 paths (x3 traversals: primal, PRB "
+              f"radiance pass, replay) = {paths // steps} traversals; FP64, brute-force intersection")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "paths/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / iters, "higher_is_better": True,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "spiral256", "image": [256, 256], "triangles": 8192, "texture": [256, 256, 5],
-                       "max_depth": 5, "spp_prop": 2, "spp_fd": 1},
-            "iters_per_s": iters,
-            "cpu_baseline": {"value": v, "unit": "paths/s", "cores": 1, "kind": "oracle",
-                             "sample": steps[0]["sample"]},
+            "config": workload_config(1), "iters_per_s": iters,
+            "step": "a bounded sample of the workload's paths (see cpu_baseline.sample), not a whole iteration",
+            "cpu_baseline": {"value": v, "unit": "paths/s", "cores": op.workers, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -581,8 +625,173 @@ def volume_leg(torch, iters=400, lr=0.1, warm=3, timed=20, frac=0.005):
     return out
 
 
+def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """Nominal FP32 rate: SMs x 128 FP32 lanes x 2 (an FMA is two operations) x SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def trace_traffic(kernel: str):
+    """DRAM bytes per launch of a traversal kernel class from the recorded ncu capture, or None
+    when no capture exists or the traversal source changed since it was taken."""
+    import hashlib
+    if not TRACE_DRAM["trace_cu_sha1"] or kernel not in TRACE_DRAM["bytes"]:
+        return None
+    with open(os.path.join(ROOT, "paper_2309_15676_gb300", "csrc", "trace.cu"), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != TRACE_DRAM["trace_cu_sha1"]:
+            return None
+    return TRACE_DRAM["bytes"][kernel]
+
+
+def timed_iterations(torch, ctx, steps, flush, local, dist=None):
+    """K graph-launched iterations, L2 flushed between them, each bracketed by CUDA events on the
+    launching stream; a region whose clock record rejects it (on any rank) is timed once more and
+    the second number kept. Returns (ms summed over the steps, clock summary, why re-measured)."""
+    remeasured = None
+    for attempt in range(2):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for k in range(steps):
+                l2_flush(torch, flush)
+                ev[k][0].record()
+                ctx.iterate(1, use_graph=True)
+                ev[k][1].record()
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+        ms = sum(x.elapsed_time(y) for x, y in ev)
+        why = clock_rejection(clk.summary())
+        if attempt == 1 or slowest_rank_ms(1.0 if why else 0.0, dist, "cuda") == 0.0:
+            break
+        remeasured = why or "another rank's clock record"
+    return ms, dict(clk.summary(), remeasured=remeasured)
+
+
+def kernel_table(torch, ctx, pid, flush, n_prof=3):
+    """Per-kernel event-timed launches of the same iteration (no graph), then a counting re-run of
+    the same iterations (BVH node and primitive tests per launch class); the state is rewound."""
+    blob = ctx.checkpoint_save()
+    ctx.profile(1)
+    for _ in range(n_prof):
+        l2_flush(torch, flush)
+        ctx.iterate(1, use_graph=False)
+    prof = ctx.profile_read()
+    ctx.checkpoint_load(blob)
+    ctx.profile(0)
+    ctx.profile(2)
+    for _ in range(n_prof):
+        ctx.iterate(1, use_graph=False)
+    counts = ctx.profile_read()
+    ctx.profile(0)
+    ctx.checkpoint_load(blob)
+    touched = touched_texels(ctx, pid)
+    ctx.checkpoint_load(blob)
+    tot = sum(v["ms"] for v in prof.values())
+    kernels = {k: {"launches_per_iter": v["launches"] / n_prof, "ms_per_iter": v["ms"] / n_prof,
+                   "share": v["ms"] / tot, "units_per_iter": v["units"] / n_prof} for k, v in prof.items()}
+    for k, v in kernels.items():
+        c = counts.get(k, {})
+        if c.get("node_tests"):
+            v["node_tests_per_iter"] = c["node_tests"] / n_prof
+            v["prim_tests_per_iter"] = c["prim_tests"] / n_prof
+            v["tflops"] = (NODE_FLOPS * c["node_tests"] + PRIM_FLOPS * c["prim_tests"]) / (
+                v["ms_per_iter"] * n_prof * 1e-3) / 1e12
+    return prof, counts, kernels, touched
+
+
+def dominant_roofline(prof, counts, kernels, rooflines, fp32_peak, sms, sm_max):
+    """Roofline of the kernel class with the largest share of the iteration's launch time. For a
+    traversal class: algorithmic work = four-box node tests x 97 FP32 operations + primitive tests
+    x 45 (counted by the counting run), over its event-timed launches, against the FP32 peak."""
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_iter"])
+    if dom in ("update", "scatter"):
+        rr = [r for r in rooflines if r["kernel"] == dom][0]
+        return dict(rr, traffic=None, share=kernels[dom]["share"])
+    dk = prof[dom]
+    ck = counts.get(dom, {})
+    flops = NODE_FLOPS * ck.get("node_tests", 0) + PRIM_FLOPS * ck.get("prim_tests", 0)
+    ach = flops / (dk["ms"] * 1e-3) / 1e12 if flops else None
+    return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": (ach / fp32_peak) if ach else None, "traffic": trace_traffic(dom),
+            "peak_basis": f"nominal FP32: {sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+            "ms_per_launch": dk["ms"] / dk["launches"], "share": kernels[dom]["share"],
+            "rays_per_s": dk["units"] / (dk["ms"] * 1e-3),
+            "flops_per_launch": flops / max(dk["launches"], 1)}
+
+
+def e2e_leg(torch, ctx, pid, tgt_host, steps, paths_per_iter, world):
+    """The same iterations end to end through the public API: every step uploads its input (the
+    target image, from pinned host memory) and reads its result (the loss) back into pinned host
+    memory; one step in flight, the host reads step k's loss after enqueueing step k + 1."""
+    loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        ctx.set_target_async(pid, tgt_host)
+        ctx.iterate(1, use_graph=True)
+        ctx.loss_async(pid, loss_host[k % 2:k % 2 + 1])
+        done[k % 2].record()
+        if k > 0:
+            done[(k - 1) % 2].synchronize()
+            losses.append(float(loss_host[(k - 1) % 2]))
+    done[(steps - 1) % 2].synchronize()
+    losses.append(float(loss_host[(steps - 1) % 2]))
+    e2e_s = time.perf_counter() - t0
+    assert len(losses) == steps and all(math.isfinite(x) and x > 0 for x in losses)
+    return {"value": world * paths_per_iter * steps / e2e_s, "unit": "paths/s",
+            "h2d_bytes_per_step": int(tgt_host.numel() * 4), "d2h_bytes_per_step": 8,
+            "iters_per_s": world * steps / e2e_s, "last_loss": losses[-1]}
+
+
+def hit_store_leg(torch, local, sc, target_img, init_tex, steps, flush, no_autotune):
+    """Variant: the replays take each vertex's closest hit and NEE visibility from a store their
+    PRB radiance pass wrote (17 B per vertex and branch) instead of tracing again. Same estimates;
+    paths/s here counts the 12 path evaluations per pixel although the 4 replays trace nothing."""
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    cr = Context(local, max_paths=1 << 20, replay_hit_store=True)
+    pr = cr.add_scene(sc, HyperParams(lr=0.01))
+    cr.set_target(pr, target_img)
+    cr.set_params(pr, init_tex)
+    shape = cr.autotune(3) if not no_autotune else "defaults"
+    cr.iterate(3, use_graph=True)
+    kr = min(steps, 50)
+    ms, _ = timed_iterations(torch, cr, kr, flush, local)
+    msr = ms / kr
+    paths = cr.stats(pr)["paths_per_iter"]
+    out = {"ms_per_step": msr, "paths_evaluated_per_s": paths / (msr * 1e-3),
+           "traced_paths_per_s": (paths * 8 / 12) / (msr * 1e-3), "steps": kr,
+           "launches_per_iter": cr.launch_count(), "launch_shape": shape}
+    cr.close()
+    return out
+
+
+def compact(x, nd=4):
+    """Rounds floats to nd significant digits (keeps the headline line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{nd}g}") if math.isfinite(x) else None
+    if isinstance(x, dict):
+        return {k: compact(v, nd) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [compact(v, nd) for v in x]
+    return x
+
+
+def headline(metric_value, steps, warmup, world, ms_per_step, iters_per_s, roof, cpu, e2e, clocks, launches,
+             variants, rooflines_hbm, peak_kind):
+    """The one JSON line the benchmark ends with (a few hundred bytes to ~2 KB)."""
+    line = {"metric": METRIC, "value": metric_value, "unit": "paths/s", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(world),
+            "iters_per_s": iters_per_s, "roofline": roof, "rooflines_hbm": rooflines_hbm, "peak_source": peak_kind,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches, "variants": variants}
+    return compact(line)
+
+
 def run_mine(args):
-    import numpy as np
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -597,16 +806,26 @@ def run_mine(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hbm_peak, peak_kind, sm_max = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = fp32_peak_tflops(sms, sm_max)
+    detail = {}
+
+    def emit(name, val):
+        detail[name] = val
+        if rank == 0:
+            print(json.dumps({"bench_leg": name, name: val}), flush=True)
+
     if args.only_scale:
-        print(json.dumps({"scale": scale_profile(torch, hbm_peak, args.scale_image)}), flush=True)
+        emit("scale", scale_profile(torch, hbm_peak, args.scale_image))
         return 0
     if args.only_volume:
-        print(json.dumps({"volume": volume_leg(torch)}), flush=True)
+        emit("volume", volume_leg(torch))
         return 0
 
     w = workload()
     sc = replica_scene(w.scene, rank)          # independent replica per rank
-    ctx = Context(local, max_paths=1 << 20)     # queue capacity: 16 spp chunks for the target render
+    # the headline iteration: PRB replays regenerate every path from its counters and trace again
+    ctx = Context(local, max_paths=1 << 20)   # queue capacity: 16 spp target chunks
     pid = ctx.add_scene(sc, HyperParams(lr=0.01))
     ctx.render_target(pid, torch.from_numpy(w.target_tex).cuda(), 256)
     ctx.set_params(pid, w.init_tex)
@@ -617,62 +836,16 @@ def run_mine(args):
 
     # launch shapes picked by the library's autotuner on this workload (state restored afterwards)
     tuned = ctx.autotune(3) if not args.no_autotune else "defaults"
-    # warm-up (captures the iteration graph)
-    ctx.iterate(max(args.warmup, 3), use_graph=True)
+    ctx.iterate(max(args.warmup, 3), use_graph=True)     # warm-up (captures the iteration graph)
     torch.cuda.synchronize()
 
-    # ---- timed region: K graph-launched iterations, L2 flushed between them; a region whose clock
-    # record rejects it (on any rank) is timed once more and the second number kept ----
-    remeasured = None
-    for attempt in range(2):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            for k in range(args.steps):
-                l2_flush(torch, flush)
-                ev[k][0].record()
-                ctx.iterate(1, use_graph=True)
-                ev[k][1].record()
-            torch.cuda.synchronize()
-            if dist:
-                dist.barrier()
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        why = clock_rejection(clk.summary())
-        if attempt == 1 or slowest_rank_ms(1.0 if why else 0.0, dist, "cuda") == 0.0:
-            break
-        remeasured = why or "another rank's clock record"
+    ms, clocks = timed_iterations(torch, ctx, args.steps, flush, local, dist)
     launches_per_iter = ctx.launch_count()
     ms_max = slowest_rank_ms(ms, dist, "cuda")
     value = whole_job_rate(world, paths_per_iter, args.steps, ms_max)
     iters_per_s = whole_job_rate(world, 1, args.steps, ms_max)
 
-    # ---- per-kernel breakdown: event-timed launches of the same iteration (no graph) ----
-    blob = ctx.checkpoint_save()
-    ctx.profile(1)
-    n_prof = 3
-    for _ in range(n_prof):
-        l2_flush(torch, flush)
-        ctx.iterate(1, use_graph=False)
-    prof = ctx.profile_read()
-    ctx.checkpoint_load(blob)
-    # counting run of the same iterations (rewound): node and primitive tests per launch class
-    ctx.profile(0)
-    ctx.profile(2)
-    for _ in range(n_prof):
-        ctx.iterate(1, use_graph=False)
-    counts = ctx.profile_read()
-    ctx.profile(0)
-    ctx.checkpoint_load(blob)
-    touched = touched_texels(ctx, pid)
-    ctx.checkpoint_load(blob)
-    tot = sum(v["ms"] for v in prof.values())
-    kernels = {k: {"launches_per_iter": v["launches"] / n_prof, "ms_per_iter": v["ms"] / n_prof,
-                   "share": v["ms"] / tot, "units_per_iter": v["units"] / n_prof} for k, v in prof.items()}
-    dom = max(kernels, key=lambda k: kernels[k]["ms_per_iter"])
-
-    # ---- rooflines ----
+    prof, counts, kernels, touched = kernel_table(torch, ctx, pid, flush)
     rooflines = []
     if "scatter" in prof:
         rooflines.append(scatter_roofline(prof["scatter"], touched, sc["tex_c"], hbm_peak))
@@ -684,134 +857,85 @@ def run_mine(args):
         rooflines.append({"kernel": "update", "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                           "frac": gbs / hbm_peak, "bytes_per_launch": byts, "ms": avg_ms,
                           "note": "327,680 params (21 MB) stay L2-resident at this size"})
-    upd67 = update_roofline(torch, hbm_peak) if rank == 0 else None
-    # dominant kernel: BVH traversal on the FP32 pipes; algorithmic work = four-box node tests x 97
-    # FP32 ops (24 FMA = 48, 48 min/max, 1 mul) + primitive tests x 45 (Moller-Trumbore), measured by the
-    # counting run; peak = 152 SMs x 128 FP32 lanes x 2 x max SM clock
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    dk = prof[dom]
-    ck = counts.get(dom, {})
-    flops = NODE_FLOPS * ck.get("node_tests", 0) + PRIM_FLOPS * ck.get("prim_tests", 0)
-    ach = flops / (dk["ms"] * 1e-3) / 1e12 if flops else None
-    roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": (ach / fp32_peak) if ach else None, "traffic": TRACE_DRAM_BYTES.get(dom),
-            "ms_per_launch": dk["ms"] / dk["launches"], "share": kernels[dom]["share"],
-            "rays_per_s": dk["units"] / (dk["ms"] * 1e-3),
-            "node_tests_per_launch": ck.get("node_tests", 0) / max(dk["launches"], 1),
-            "prim_tests_per_launch": ck.get("prim_tests", 0) / max(dk["launches"], 1),
-            "flops_per_launch": flops / max(dk["launches"], 1),
-            "note": ("traversal: a launch at this size is the dependent-latency tail of its last warps "
-                     "(ncu: about 3% of issue slots used, 9-16 active lanes per instruction), so the FP32 "
-                     "fraction is small by nature; see profiles/trace_spiral256.md")}
-    for k, v in kernels.items():
-        c = counts.get(k, {})
-        if c.get("node_tests"):
-            v["node_tests_per_iter"] = c["node_tests"] / n_prof
-            v["prim_tests_per_iter"] = c["prim_tests"] / n_prof
-            v["tflops"] = (NODE_FLOPS * c["node_tests"] + PRIM_FLOPS * c["prim_tests"]) / (
-                v["ms_per_iter"] * n_prof * 1e-3) / 1e12
-    if dom in ("update", "scatter"):
-        rr = [r for r in rooflines if r["kernel"] == dom][0]
-        roof = dict(rr, traffic=None, share=kernels[dom]["share"])
+    roof = dominant_roofline(prof, counts, kernels, rooflines, fp32_peak, sms, sm_max)
+    emit("kernels", {"per_class": kernels, "rooflines_spiral256": rooflines, "launch_shapes": tuned,
+                     "launches_per_iter": launches_per_iter})
 
-    # ---- e2e through the public API with host buffers ----
-    # the target image (same counters as the stored target) staged in pinned host memory
-    target_img = ctx.render(pid, torch.from_numpy(w.target_tex).cuda(), spp=256, stream=4, iteration=0)
+    # e2e through the public API with host buffers: the target image (same counters as the stored
+    # target) staged in pinned host memory
+    blob = ctx.checkpoint_save()
+    target_img = ctx.render(pid, torch.from_numpy(w.target_tex).cuda(), spp=256, stream=4, iteration=0).clone()
     tgt_host = target_img.cpu().pin_memory()
     ctx.checkpoint_load(blob)
-    torch.cuda.synchronize()
-    # every step: H2D of the step's input (the target, from pinned memory) and D2H of its result
-    # (the loss, into pinned memory); one step in flight, the host reads step k's loss after
-    # enqueueing step k + 1
-    loss_host = torch.zeros(2, dtype=torch.float64).pin_memory()
-    done = [torch.cuda.Event(), torch.cuda.Event()]
-    losses = []
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        ctx.set_target_async(pid, tgt_host)
-        ctx.iterate(1, use_graph=True)
-        ctx.loss_async(pid, loss_host[k % 2:k % 2 + 1])
-        done[k % 2].record()
-        if k > 0:
-            done[(k - 1) % 2].synchronize()
-            losses.append(float(loss_host[(k - 1) % 2]))
-    done[(args.steps - 1) % 2].synchronize()
-    losses.append(float(loss_host[(args.steps - 1) % 2]))
-    e2e_s = time.perf_counter() - t0
-    assert len(losses) == args.steps and all(math.isfinite(x) and x > 0 for x in losses)
-    e2e = {"value": world * paths_per_iter * args.steps / e2e_s, "unit": "paths/s",
-           "h2d_bytes_per_step": int(tgt_host.numel() * 4), "d2h_bytes_per_step": 8,
-           "iters_per_s": world * args.steps / e2e_s, "last_loss": losses[-1]}
+    e2e = e2e_leg(torch, ctx, pid, tgt_host, args.steps, paths_per_iter, world)
     ctx.close()
 
-    # ---- the same iterations with replays that re-trace every ray (no per-vertex hit store) ----
-    retrace = None
+    variants, rooflines_hbm, cpu = {}, {}, None
     if rank == 0:
-        cr = Context(local, max_paths=1 << 20, replay_retrace=True)
-        pr = cr.add_scene(sc, HyperParams(lr=0.01))
-        cr.set_target(pr, target_img)
-        cr.set_params(pr, w.init_tex)
-        shape_r = cr.autotune(3) if not args.no_autotune else "defaults"
-        cr.iterate(3, use_graph=True)
-        kr = min(args.steps, 50)
-        evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kr)]
-        torch.cuda.synchronize()
-        for k in range(kr):
-            l2_flush(torch, flush)
-            evr[k][0].record()
-            cr.iterate(1, use_graph=True)
-            evr[k][1].record()
-        torch.cuda.synchronize()
-        msr = sum(a.elapsed_time(b) for a, b in evr) / kr
-        retrace = {"ms_per_step": msr, "paths_per_s": paths_per_iter / (msr * 1e-3), "steps": kr,
-                   "launches_per_iter": cr.launch_count(), "launch_shape": shape_r}
-        cr.close()
-
-    cpu = None
-    ttt = None
-    if rank == 0 and not args.no_ttt:
-        ttt = {"spiral256 (learning rate tuned per method)":
-               time_to_threshold(torch, w, target_img, args.ttt_iters, lrs=(0.003, 0.01, 0.03, 0.1), precond=4.0)}
-        # config 1 as stated: 64x64 box, 32x32 RGB albedo, depth 3, 1 FD + 1 proportional spp, lr 0.01,
-        # 50 iterations (Adam on 2 fresh spp)
-        from paper_2309_15676_gb300 import synth as _s
-        wb = _s.workload_box()
-        cb = Context(local, max_paths=1 << 20)
-        pb = cb.add_scene(wb.scene, HyperParams())
-        tb = cb.render(pb, torch.from_numpy(wb.target_tex).cuda(), spp=256, stream=4, iteration=0).clone()
-        cb.close()
-        ttt["box64 (config 1: lr 0.01, 50 iterations)"] = time_to_threshold(torch, wb, tb, 50, lrs=(0.01,))
-        ttt["spiral512 spp sweep (config 3)"] = spp_sweep(torch)
-    validation = None
-    if rank == 0 and args.validate:
-        from paper_2309_15676_gb300.experiments import trajectory_study
-        validation = {kind: trajectory_study(runs=1000, iters=100, schedule=kind) for kind in ("linear", "exponential")}
-    batched = batched_compare(torch) if (rank == 0 and not args.no_batch) else None
-    scale = scale_profile(torch, hbm_peak, args.scale_image) if (rank == 0 and not args.no_scale) else None
-    volume = volume_leg(torch) if (rank == 0 and not args.no_volume) else None
-    if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(w)
-        cpu["multicore"] = cpu_baseline_parallel(10.0)
+        hs = hit_store_leg(torch, local, sc, target_img, w.init_tex, args.steps, flush, args.no_autotune)
+        emit("hit_store_variant", hs)
+        variants["hit_store"] = {"ms_per_step": hs["ms_per_step"], "paths_evaluated_per_s": hs["paths_evaluated_per_s"],
+                                 "traced_paths_per_s": hs["traced_paths_per_s"]}
+        upd67 = update_roofline(torch, hbm_peak)
+        emit("update_standalone", upd67)
+        rooflines_hbm["update_67M"] = {"frac": upd67["frac"], "achieved": upd67["achieved"], "unit": "GB/s"}
+        if not args.no_ttt:
+            emit("time_to_threshold", ttt_leg(torch, w, target_img, args.ttt_iters, local))
+        if args.validate:
+            from paper_2309_15676_gb300.experiments import trajectory_study
+            emit("validation", {k: trajectory_study(runs=1000, iters=100, schedule=k) for k in ("linear", "exponential")})
+        if not args.no_batch:
+            bt = batched_compare(torch)
+            emit("batched", bt)
+            variants["batched_64"] = {"ms_graph": bt["batched_graph"]["ms_per_iter"],
+                                      "ms_loop_plain": bt["per_problem_loop_plain"]["ms_per_iter"],
+                                      "speedup": bt["speedup_vs_plain_loop"]}
+        if not args.no_scale:
+            s = scale_profile(torch, hbm_peak, args.scale_image)
+            emit("scale", s)
+            variants["dsphere1024"] = {"ms_per_iter": s["ms_per_iter"], "paths_per_s": s["paths_per_s"]}
+            for r in s["rooflines"]:
+                rooflines_hbm[r["kernel"].split(" ")[0] + "_1024"] = {"frac": r["frac"], "achieved": r["achieved"],
+                                                                       "unit": "GB/s"}
+        if not args.no_volume:
+            v = volume_leg(torch)
+            emit("volume", v)
+            variants["volume256_meta"] = {"ms_per_iter": v["meta"]["ms_per_iter"]}
+        if not args.no_cpu:
+            cpu = cpu_baseline()
+            mc = cpu_baseline_parallel(10.0)
+            emit("cpu_baseline_multicore", mc)
+            cpu["multicore"] = {"value": mc["value"], "cores": mc["cores"]}
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "spiral256", "image": [256, 256], "triangles": 8192,
-                           "texture": [256, 256, 5], "max_depth": 5, "spp_prop": 2, "spp_fd": 1,
-                           "paths_per_iter": paths_per_iter, "l2": "flushed (256 MiB write) between timed steps",
-                           "parallelism": f"replicas x{world}"},
-                "iters_per_s": iters_per_s,
-                "replay_retrace": retrace,
-                "roofline": roof, "rooflines": rooflines + ([upd67] if upd67 else []),
-                "kernels": kernels, "peak_source": peak_kind,
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": dict(clk.summary(), remeasured=remeasured),
-                "gpu_launches": int(launches_per_iter * args.steps), "launch_shapes": tuned,
-                "time_to_threshold": ttt, "batched": batched, "scale": scale, "volume": volume,
-                "validation": validation}
-        print(json.dumps(line), flush=True)
+        if args.detail_out:
+            os.makedirs(os.path.dirname(os.path.abspath(args.detail_out)), exist_ok=True)
+            with open(args.detail_out, "w") as f:
+                json.dump(detail, f, indent=1)
+        line = headline(value, args.steps, args.warmup, world, ms_max / args.steps, iters_per_s, roof, cpu, e2e,
+                        clocks, int(launches_per_iter * args.steps), variants, rooflines_hbm, peak_kind)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def ttt_leg(torch, w, target_img, ttt_iters, local):
+    """Time to threshold: spiral256 (learning rate tuned per method, with and without gradient
+    preconditioning), the box of config 1 as stated, and config 3's spp sweep."""
+    from paper_2309_15676_gb300 import synth as _s
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    ttt = {"spiral256 (learning rate tuned per method)":
+           time_to_threshold(torch, w, target_img, ttt_iters, lrs=(0.003, 0.01, 0.03, 0.1), precond=4.0)}
+    # config 1 as stated: 64x64 box, 32x32 RGB albedo, depth 3, 1 FD + 1 proportional spp, lr 0.01,
+    # 50 iterations (Adam on 2 fresh spp)
+    wb = _s.workload_box()
+    cb = Context(local, max_paths=1 << 20)
+    pb = cb.add_scene(wb.scene, HyperParams())
+    tb = cb.render(pb, torch.from_numpy(wb.target_tex).cuda(), spp=256, stream=4, iteration=0).clone()
+    cb.close()
+    ttt["box64 (config 1: lr 0.01, 50 iterations)"] = time_to_threshold(torch, wb, tb, 50, lrs=(0.01,))
+    ttt["spiral512 spp sweep (config 3)"] = spp_sweep(torch)
+    return ttt
 
 
 def main():

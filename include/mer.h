@@ -170,12 +170,13 @@ typedef struct mer_config {
     int32_t blocks_per_sm;    /* persistent-grid occupancy target (0 = default) */
     int32_t smem_nodes;       /* BVH nodes staged in shared memory per block (0 = off) */
     int64_t max_paths;        /* capacity hint for path queues (0 = size from the scenes) */
-    /* 0 (default): the iteration's PRB radiance passes keep each path vertex's closest hit and
-     * NEE visibility (16 B + 1 B per vertex and branch) and the replays read them instead of
-     * tracing again (same hits, no traversal launches); 1: the replays re-trace every ray, so no
-     * per-vertex state is kept. The estimates are the same either way; mer_adjoint and
-     * mer_adjoint_pair always re-trace. */
-    int32_t replay_retrace;
+    /* 0 (default): the iteration's replays regenerate every path from its counters and trace its
+     * rays again, so no per-vertex state outlives a kernel (path replay as the checkpointing,
+     * Sec. 6 setup: PRB). 1: a variant in which the PRB radiance passes keep each path vertex's
+     * closest hit and NEE visibility (16 B + 1 B per vertex and branch) and the replays read them
+     * instead of tracing (same hits, no traversal launches in the replays). The estimates are the
+     * same either way; mer_adjoint and mer_adjoint_pair always re-trace. */
+    int32_t replay_hit_store;
 } mer_config;
 
 typedef struct mer_iter_stats {
@@ -339,7 +340,13 @@ mer_status mer_state_get(mer_ctx* ctx, int32_t pid, mer_state_view* out);
  * Variant flags without arrays of their own work here (PER_ELEMENT, with pi_next holding pi_{i-1}
  * on entry; NO_CLIP; GROWING_BETA); CENTRED, NAIVE_ADAM and UNCORRELATED are rejected
  * (MER_ERR_INVALID_ARG): use mer_meta_step_raw_ex.
- * Uses library-owned per-device scratch for the deterministic norm reduction. */
+ * Scratch: the per-block partial sums of the deterministic norm reduction go to one buffer per
+ * device that the library owns and shares between all calls of mer_meta_step_raw and
+ * mer_meta_step_raw_ex on that device (n/4096 doubles, grown on demand). Calls ordered on one
+ * stream are safe; calls that overlap on the GPU (different streams with no ordering between
+ * them) race on it and give wrong norms. Growing it (a call with a larger n than any before on
+ * this device) synchronises the device and frees the old buffer, so a caller that must not
+ * allocate or synchronise uses mer_meta_step_raw_noalloc. */
 mer_status mer_meta_step_raw(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
                              const float* pi, float* pi_next, float* F, float* dF, float* m2f, float* m2d,
                              float* mean, float* var, float* alpha_prev, int32_t iteration, int32_t count_f,
@@ -360,16 +367,16 @@ typedef struct mer_update_arrays {
 
 /* mer_meta_step_raw with every variant of hyper->flags: arrays as described above, scalars as
  * in mer_meta_step_raw (ADAM mode ignores the flags). Rejects (MER_ERR_INVALID_ARG) a flag whose
- * arrays are missing. */
+ * arrays are missing. Shares mer_meta_step_raw's per-device scratch (same race rule). */
 mer_status mer_meta_step_raw_ex(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
                                 const mer_update_arrays* arrays, int32_t iteration, int32_t count_f,
                                 int32_t count_d, double dpi_norm2, int32_t zero_grads, double* dpi_norm2_out,
                                 void* cuda_stream);
 
 /* The same update as mer_meta_step_raw, for callers that must not allocate device memory:
- * code running while a stream is being captured into a CUDA graph, applications that reserve
- * all device memory up front or hand it out through their own pool, and real-time loops where
- * an allocation (and the device synchronisation that freeing implies) is not allowed.
+ * applications that reserve all device memory up front or hand it out through their own pool
+ * (a library allocation would go around it or fail), and real-time loops where an allocation,
+ * and the device synchronisation that freeing a grown buffer implies, is not allowed.
  * The paper has no counterpart; this is an interface variant only.
  * Arguments, layout, results and tolerances are exactly those of mer_meta_step_raw.
  * Scratch: the per-block partial norms go to a fixed array compiled into the library (512 KiB
@@ -379,7 +386,9 @@ mer_status mer_meta_step_raw_ex(const mer_hyper* hyper, int64_t n, int32_t C, co
  * address once (cudaGetSymbolAddress, with that device current); make that first call before any
  * stream capture. All calls share the one array: calls that overlap on the GPU (different
  * streams, no ordering between them) race and give wrong norms; calls ordered on one stream are
- * safe. Nothing in the array needs to start at zero (every call writes all the entries it reads). */
+ * safe. Nothing in the array needs to start at zero (every call writes all the entries it reads).
+ * The looked-up address is kept for the life of the process: do not use this entry point on a
+ * device after cudaDeviceReset (or from another driver context on the same device). */
 mer_status mer_meta_step_raw_noalloc(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
                                      const float* pi, float* pi_next, float* F, float* dF, float* m2f, float* m2d,
                                      float* mean, float* var, float* alpha_prev, int32_t iteration, int32_t count_f,

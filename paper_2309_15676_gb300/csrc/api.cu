@@ -283,7 +283,7 @@ mer_status alloc_wave(mer_ctx* c, Wave& w, int64_t Q, int64_t R, int hs_depth) {
 mer_status ensure_wavefront(mer_ctx* c, int64_t need_paths, int maxD) {
     const int64_t want_q = std::max<int64_t>(need_paths, c->cfg.max_paths > 0 ? c->cfg.max_paths : 0);
     const int64_t want_r = 2 * want_q * std::max(1, maxD - 1);
-    if (want_q <= c->w[0].qcap && want_r <= c->w[0].rcap && (c->cfg.replay_retrace || maxD <= c->w[2].hs_depth))
+    if (want_q <= c->w[0].qcap && want_r <= c->w[0].rcap && (!c->cfg.replay_hit_store || maxD <= c->w[2].hs_depth))
         return MER_OK;
     cudaStreamSynchronize(c->st);
     for (cudaStream_t s : c->sx) cudaStreamSynchronize(s);
@@ -292,7 +292,7 @@ mer_status ensure_wavefront(mer_ctx* c, int64_t need_paths, int maxD) {
     const int64_t R = std::max<int64_t>(want_r, 1024);
     for (int i = 0; i < 4; ++i) {
         // sets 0 and 1 replay (records); sets 2 and 3 run the ADJ_FWD passes (hit store)
-        const int hs_depth = (i < 2 || c->cfg.replay_retrace) ? 0 : std::max(1, maxD);
+        const int hs_depth = (i < 2 || !c->cfg.replay_hit_store) ? 0 : std::max(1, maxD);
         mer_status s = alloc_wave(c, c->w[i], Q, i < 2 ? R : 1, hs_depth);
         if (s) return s;
     }
@@ -1442,40 +1442,9 @@ mer_status mer_meta_step_raw(const mer_hyper* hyper, int64_t n, int32_t C, const
 mer_status mer_meta_step_raw_ex(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
                                 const mer_update_arrays* arrays, int32_t iteration, int32_t count_f,
                                 int32_t count_d, double dpi_norm2, int32_t zero_grads, double* out, void* stream) {
-    if (!hyper || !arrays || n < 0 || C < 1 || C > 8 || !lo || !hi || !out)
-        return fail(nullptr, MER_ERR_INVALID_ARG, "bad arguments to mer_meta_step_raw");
-    if (const char* why = hyper_problem(*hyper)) return fail(nullptr, MER_ERR_INVALID_ARG, "%s", why);
-    const mer_update_arrays& A = *arrays;
-    const bool meta = hyper->mode == MER_MODE_META;
-    const int fl = meta ? hyper->flags : 0;
-    if (n > 0 && (!A.pi || !A.pi_next || !A.F || !A.m2f || !A.mean ||
-                  (meta && (!A.dF || !A.m2d || !A.var || !A.alpha_prev))))
-        return fail(nullptr, MER_ERR_INVALID_ARG, "missing arrays in mer_meta_step_raw");
-    if (n > 0 && (((fl & MER_META_CENTRED) && (!A.mu_f || !A.mu_d)) ||
-                  ((fl & MER_META_NAIVE_ADAM) && (!A.adam_m || !A.adam_v)) ||
-                  ((fl & MER_META_UNCORRELATED) && (!A.F_var || !A.dF_var))))
-        return fail(nullptr, MER_ERR_INVALID_ARG, "mer_meta_step_raw: the flags need variant arrays that are missing");
-    const void* ptrs[] = {A.pi, A.pi_next, A.F, A.dF, A.m2f, A.m2d, A.mean, A.var, A.alpha_prev,
-                          A.mu_f, A.mu_d, A.adam_m, A.adam_v, A.F_var, A.dF_var};
-    for (const void* q : ptrs)
-        if (q && ((uintptr_t)q & 15u)) return fail(nullptr, MER_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
-    if (A.pi == A.pi_next && n > 0) return fail(nullptr, MER_ERR_INVALID_ARG, "pi_next may not alias pi");
     UpdSeg S;
-    memset(&S, 0, sizeof S);
-    S.pA = const_cast<float*>(A.pi);
-    S.pB = A.pi_next;
-    S.F = A.F; S.dF = A.dF; S.m2f = A.m2f; S.m2d = A.m2d; S.mean = A.mean; S.var = A.var; S.ap = A.alpha_prev;
-    if (fl & MER_META_CENTRED) { S.mu_f = A.mu_f; S.mu_d = A.mu_d; }
-    if (fl & MER_META_NAIVE_ADAM) { S.am = A.adam_m; S.av = A.adam_v; }
-    if (fl & MER_META_UNCORRELATED) { S.Fv = A.F_var; S.dFv = A.dF_var; }
-    S.n = n;
-    S.C = C;
-    S.zero_grads = zero_grads;
-    for (int k = 0; k < C; ++k) {
-        S.lo[k] = lo[k];
-        S.hi[k] = hi[k];
-    }
-    S.hyper = *hyper;
+    if (const char* why = raw_update_seg(hyper, n, C, lo, hi, arrays, zero_grads, out, &S))
+        return fail(nullptr, MER_ERR_INVALID_ARG, "mer_meta_step_raw: %s", why);
     const int64_t nb = update_blocks_for(n);
     int dev = 0;
     cudaGetDevice(&dev);

@@ -386,6 +386,44 @@ cudaError_t launch_force_step(const float* pnew, const float* pold, int64_t n, P
     return cudaGetLastError();
 }
 
+const char* raw_update_seg(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
+                           const mer_update_arrays* arrays, int32_t zero_grads, const double* out, UpdSeg* S) {
+    if (!hyper || !arrays || n < 0 || C < 1 || C > 8 || !lo || !hi || !out)
+        return "bad arguments to the standalone update";
+    if (const char* why = hyper_problem(*hyper)) return why;
+    const mer_update_arrays& A = *arrays;
+    const bool meta = hyper->mode == MER_MODE_META;
+    const int fl = meta ? hyper->flags : 0;
+    if (n > 0 && (!A.pi || !A.pi_next || !A.F || !A.m2f || !A.mean ||
+                  (meta && (!A.dF || !A.m2d || !A.var || !A.alpha_prev))))
+        return "missing arrays in the standalone update";
+    if (n > 0 && (((fl & MER_META_CENTRED) && (!A.mu_f || !A.mu_d)) ||
+                  ((fl & MER_META_NAIVE_ADAM) && (!A.adam_m || !A.adam_v)) ||
+                  ((fl & MER_META_UNCORRELATED) && (!A.F_var || !A.dF_var))))
+        return "the update's flags need variant arrays that are missing (mer_meta_step_raw_ex takes them)";
+    const void* ptrs[] = {A.pi, A.pi_next, A.F, A.dF, A.m2f, A.m2d, A.mean, A.var, A.alpha_prev,
+                          A.mu_f, A.mu_d, A.adam_m, A.adam_v, A.F_var, A.dF_var};
+    for (const void* q : ptrs)
+        if (q && ((uintptr_t)q & 15u)) return "arrays must be 16-byte aligned";
+    if (A.pi == A.pi_next && n > 0) return "pi_next may not alias pi";
+    memset(S, 0, sizeof *S);
+    S->pA = const_cast<float*>(A.pi);
+    S->pB = A.pi_next;
+    S->F = A.F; S->dF = A.dF; S->m2f = A.m2f; S->m2d = A.m2d; S->mean = A.mean; S->var = A.var; S->ap = A.alpha_prev;
+    if (fl & MER_META_CENTRED) { S->mu_f = A.mu_f; S->mu_d = A.mu_d; }
+    if (fl & MER_META_NAIVE_ADAM) { S->am = A.adam_m; S->av = A.adam_v; }
+    if (fl & MER_META_UNCORRELATED) { S->Fv = A.F_var; S->dFv = A.dF_var; }
+    S->n = n;
+    S->C = C;
+    S->zero_grads = zero_grads;
+    for (int k = 0; k < C; ++k) {
+        S->lo[k] = lo[k];
+        S->hi[k] = hi[k];
+    }
+    S->hyper = *hyper;
+    return nullptr;
+}
+
 // ---------------------------------------------------------------------------------------
 // Allocation-free form of the standalone update. Its only scratch is the per-block partial
 // sums of ||pi' - pi||^2; here they live in a fixed file-scope device array instead of a
@@ -410,21 +448,13 @@ extern "C" mer_status mer_meta_step_raw_noalloc(const mer_hyper* hyper, int64_t 
                                                 int32_t count_d, double dpi_norm2, int32_t zero_grads,
                                                 double* dpi_norm2_out, void* cuda_stream) {
     using namespace mer;
-    if (!hyper || n < 0 || C < 1 || C > 8 || !lo || !hi || !dpi_norm2_out)
-        return mer_internal_fail(MER_ERR_INVALID_ARG, "bad arguments to mer_meta_step_raw_noalloc");
-    if (const char* why = hyper_problem(*hyper)) return mer_internal_fail(MER_ERR_INVALID_ARG, why);
-    const bool meta = hyper->mode == MER_MODE_META;
-    if (n > 0 && (!pi || !pi_next || !F || !m2f || !mean || (meta && (!dF || !m2d || !var || !alpha_prev))))
-        return mer_internal_fail(MER_ERR_INVALID_ARG, "missing arrays in mer_meta_step_raw_noalloc");
-    if (meta && (hyper->flags & (MER_META_CENTRED | MER_META_NAIVE_ADAM | MER_META_UNCORRELATED)))
-        return mer_internal_fail(MER_ERR_INVALID_ARG,
-                                 "mer_meta_step_raw_noalloc: these flags need variant arrays (use mer_meta_step_raw_ex)");
-    const void* ptrs[] = {pi, pi_next, F, dF, m2f, m2d, mean, var, alpha_prev};
-    for (const void* q : ptrs)
-        if (q && ((uintptr_t)q & 15u))
-            return mer_internal_fail(MER_ERR_INVALID_ARG, "mer_meta_step_raw_noalloc: arrays must be 16-byte aligned");
-    if (pi == pi_next && n > 0)
-        return mer_internal_fail(MER_ERR_INVALID_ARG, "mer_meta_step_raw_noalloc: pi_next may not alias pi");
+    mer_update_arrays A;
+    memset(&A, 0, sizeof A);
+    A.pi = pi; A.pi_next = pi_next; A.F = F; A.dF = dF; A.m2f = m2f; A.m2d = m2d; A.mean = mean; A.var = var;
+    A.alpha_prev = alpha_prev;
+    UpdSeg S;
+    if (const char* why = raw_update_seg(hyper, n, C, lo, hi, &A, zero_grads, dpi_norm2_out, &S))
+        return mer_internal_fail(MER_ERR_INVALID_ARG, why);
     const int64_t nb = update_blocks_for(n);
     if (nb > NOALLOC_MAX_BLOCKS)
         return mer_internal_fail(MER_ERR_INVALID_ARG,
@@ -445,19 +475,6 @@ extern "C" mer_status mer_meta_step_raw_noalloc(const mer_hyper* hyper, int64_t 
         }
         scratch = g_noalloc_addr[dev];
     }
-    UpdSeg S;
-    memset(&S, 0, sizeof S);
-    S.pA = const_cast<float*>(pi);
-    S.pB = pi_next;
-    S.F = F; S.dF = dF; S.m2f = m2f; S.m2d = m2d; S.mean = mean; S.var = var; S.ap = alpha_prev;
-    S.n = n;
-    S.C = C;
-    S.zero_grads = zero_grads;
-    for (int k = 0; k < C; ++k) {
-        S.lo[k] = lo[k];
-        S.hi[k] = hi[k];
-    }
-    S.hyper = *hyper;
     // every block writes its own partial before the finalize kernel reads it, so nothing in the
     // shared array has to start at zero
     const cudaError_t e = launch_update_raw(S, iteration, count_f, count_d, dpi_norm2, scratch, nb, dpi_norm2_out,

@@ -100,5 +100,10 @@ cudaError_t launch_force_step(const float* pnew, const float* pold, int64_t n, P
                               cudaStream_t st);
 cudaError_t launch_update_raw(const UpdSeg& S, int iteration, int count_f, int count_d, double n2, double* partials,
                               int64_t nblocks, double* out, cudaStream_t st);   // coefficients computed on the host
+// The argument checks of the standalone update (mer_meta_step_raw, _ex and _noalloc share them):
+// fills *S from the arrays and returns nullptr, or returns why the call cannot run (every such
+// case is MER_ERR_INVALID_ARG).
+const char* raw_update_seg(const mer_hyper* hyper, int64_t n, int32_t C, const float* lo, const float* hi,
+                           const mer_update_arrays* arrays, int32_t zero_grads, const double* out, UpdSeg* S);
 
 }  // namespace mer

@@ -1,6 +1,6 @@
 """Edge cases of the path tracer and the iteration against the oracle: the depth extremes (1:
 emitters only, so every texture gradient is exactly zero; 2: direct light only; 16: the largest
-depth the library accepts, deep queues and hit stores), a ragged image far from the 16x16 tiling
+depth the library accepts, deep queues, re-tracing replays and the hit-store variant), a ragged image far from the 16x16 tiling
 (7 x 5 pixels) with a 2 x 2 texture (bilinear clamp-to-edge on every fetch), and one-pixel images.
 Tolerances as elsewhere: >= 99.99% of per-sample radiances within 1e-4 relative (floor 1e-6),
 image-summed gradients within 1e-3 relative L2."""
@@ -38,14 +38,19 @@ def test_depth_extremes(depth):
         ref = orc.adjoint_image(orc.Scene(sc), w.init_tex, 2, 2, 1, dimg)
         e, f = _grad_check(got, ref)
         assert e < 1e-3 and f >= 0.999, (depth, e, f)
-    # whole iterations (hit store, FD pairs) run and stay finite at this depth
-    ctx.set_target(pid, np.full((16, 16, 3), 0.3, np.float32))
-    ctx.set_params(pid, w.init_tex)
-    ctx.iterate(3, use_graph=True)
-    st = ctx.stats(pid)
-    assert st["iteration"] == 3 and np.isfinite(st["loss"])
-    assert np.all(np.isfinite(ctx.get_params(pid).cpu().numpy()))
     ctx.close()
+    # whole iterations (re-tracing replays, and the hit-store variant; FD pairs) run and stay finite
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    for hit_store in (False, True):
+        ctx = Context(0, replay_hit_store=hit_store)
+        pid = ctx.add_scene(sc, HyperParams(lr=0.02))
+        ctx.set_target(pid, np.full((16, 16, 3), 0.3, np.float32))
+        ctx.set_params(pid, w.init_tex)
+        ctx.iterate(3, use_graph=True)
+        st = ctx.stats(pid)
+        assert st["iteration"] == 3 and np.isfinite(st["loss"])
+        assert np.all(np.isfinite(ctx.get_params(pid).cpu().numpy()))
+        ctx.close()
 
 
 @pytest.mark.parametrize("size", [(7, 5), (1, 1)])

@@ -12,9 +12,9 @@ from .gpu_common import need_gpu, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def _run(ws, flags, retrace, iters=3):
+def _run(ws, flags, hit_store, iters=3):
     from paper_2309_15676_gb300.api import Context, HyperParams
-    ctx = Context(0, replay_retrace=retrace)
+    ctx = Context(0, replay_hit_store=hit_store)
     rng = np.random.default_rng(3)
     ids = []
     for w in ws:
@@ -43,8 +43,8 @@ def test_stored_replay_equals_retrace(case):
     else:
         ws = [synth.workload_spiral(48, 40, 64, 16, 32, max_depth=5, spp_prop=2, spp_fd=1)]
     flags = META_FD_SHARED_PATH if case == "spiral_shared_fd" else 0
-    a, la = _run(ws, flags, retrace=False)
-    b, lb = _run(ws, flags, retrace=True)
+    a, la = _run(ws, flags, hit_store=True)
+    b, lb = _run(ws, flags, hit_store=False)
     assert la < lb          # the stored replays launch no traversal
     if case != "batch":     # depth 5: four passes of 2D+1 launches, replays of D (or 2D+1), 10 others
         assert (la, lb) == (4 * 11 + 2 * 5 + 10, 6 * 11 + 10), (la, lb)

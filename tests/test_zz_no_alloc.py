@@ -1,8 +1,9 @@
 """The allocation-free update entry point (mer_meta_step_raw_noalloc), called through the C ABI,
 gives the same results as mer_meta_step_raw on identical inputs, on two calls in a row.
 
-It exists for callers that may not allocate device memory (graph capture, preallocated pools,
-real-time loops); its scratch is a fixed array inside the library. This file is collected last so
+It exists for callers that may not allocate device memory (applications that hand out all device
+memory through their own pool, real-time loops that may not allocate or synchronise); its scratch
+is a fixed array inside the library. This file is collected last so
 that a run stopping at the first failure has already run every other test.
 """
 import ctypes as ct
