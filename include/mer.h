@@ -395,6 +395,15 @@ mer_status mer_meta_step_raw_noalloc(const mer_hyper* hyper, int64_t n, int32_t 
                                      int32_t count_d, double dpi_norm2, int32_t zero_grads, double* dpi_norm2_out,
                                      void* cuda_stream);
 
+/* Gradient preconditioning of Sec. 6 (texture gradients preconditioned after Nicolet et al. 2021)
+ * on its own: g <- (I + lambda L)^{-1} g in place, g a device HWC array of C x H x W floats
+ * (C in 1..5, 1 <= H, W <= 4094), L the Neumann graph Laplacian of the W x H texel grid per
+ * channel, lambda >= 0 finite (0 leaves g unchanged). The same kernels as the iteration's
+ * preconditioning (a DCT-II solve: FFT-based along a power-of-two side, a direct sum otherwise).
+ * Allocates its tables and scratch for the call and returns after the result is written
+ * (synchronous on cuda_stream). */
+mer_status mer_precondition(int32_t C, int32_t H, int32_t W, float lambda, float* g_dev, void* cuda_stream);
+
 /* Philox4x32-10 of n counters: ctr_dev [n][4] u32, out_dev [n][4] u32, key (k0, k1). */
 mer_status mer_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr_dev, int64_t n, uint32_t* out_dev,
                       void* cuda_stream);

@@ -129,6 +129,7 @@ SIGNATURES = {
                                              _vp, _vp, _vp, _vp, _vp, _vp, ct.c_int32, ct.c_int32, ct.c_int32,
                                              ct.c_double, ct.c_int32, _vp, _vp]),
     "mer_philox": (ct.c_int, [ct.c_uint32, ct.c_uint32, _vp, ct.c_int64, _vp, _vp]),
+    "mer_precondition": (ct.c_int, [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_float, _vp, _vp]),
     "mer_checkpoint_save": (ct.c_int, [_vp, _vp, ct.POINTER(ct.c_size_t)]),
     "mer_checkpoint_load": (ct.c_int, [_vp, _vp, ct.c_size_t]),
     "mer_autotune": (ct.c_int, [_vp, ct.c_int32, ct.c_char_p, ct.c_size_t]),

@@ -582,6 +582,18 @@ def meta_step_raw_ex(hyper: HyperParams, arrays: dict, C, lo, hi, iteration, cou
     return out
 
 
+def precondition(g: torch.Tensor, lam: float) -> torch.Tensor:
+    """(I + lam L)^{-1} applied in place to each channel of an (H, W, C) float32 CUDA gradient
+    (mer_precondition); returns g."""
+    if g.dim() != 3:
+        raise ValueError("precondition: an (H, W, C) tensor expected")
+    H, W, C = g.shape
+    _dev_buf(g, torch.float32, H * W * C, "precondition: g")
+    L = _lib.load()
+    check(L.mer_precondition(C, H, W, float(lam), _ptr(g), _cur_stream(g.device)))
+    return g
+
+
 def philox(k0: int, k1: int, ctr: torch.Tensor) -> torch.Tensor:
     """Philox4x32-10 of int32/uint32-bit counters [n, 4] (device) under key (k0, k1)."""
     L = _lib.load()

@@ -1,9 +1,8 @@
 """Build the CUDA library in-tree: paper_2309_15676_gb300/_build/libmer.so (sm_103a).
 
 Each translation unit is compiled by nvcc in parallel, then linked into one shared
-library with the CUDA runtime linked statically and cuBLAS (the texture preconditioner's plain
-matrix products) dynamically, found through an rpath to the toolkit. IEEE division / square root and
-denormals are kept (no fast-math): the update and the material model depend on them.
+library with the CUDA runtime linked statically; it links no other CUDA library. IEEE division /
+square root and denormals are kept (no fast-math): the update and the material model depend on them.
 """
 from __future__ import annotations
 
@@ -59,9 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(comp, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + [
-        "-L", cuda_lib, "-lcublas", "-Xlinker", "-rpath=" + cuda_lib]
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

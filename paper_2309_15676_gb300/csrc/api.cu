@@ -69,8 +69,6 @@ struct mer_ctx {
     ProblemDev* d_probs = nullptr;
     ProbState* d_pstate = nullptr;
     double* d_loss = nullptr;
-    cublasHandle_t blas = nullptr;   // matrix products of the gradient preconditioner
-    void* blas_ws = nullptr;         // its fixed workspace (no allocation during graph capture)
     bool any_uncorrelated = false;   // some problem uses MER_META_UNCORRELATED
     // pass tables
     int32_t *d_prop_prob = nullptr, *d_fd_prob = nullptr;
@@ -470,7 +468,7 @@ int enqueue_gradient(mer_ctx* c) {
         if (!p->precond) continue;
         if (g_timer) g_timer->before(KC_PRECOND, s[0]);
         for (float* gbuf : {p->F, p->meta ? p->dF : nullptr, p->Fv, p->dFv})
-            if (gbuf) n += precond_apply(c->blas, p->pc, gbuf, s[0]);
+            if (gbuf) n += precond_apply(p->pc, gbuf, s[0]);
         if (g_timer) {
             g_timer->after(KC_PRECOND, s[0]);
             g_timer->add_units(KC_PRECOND, p->n_par);
@@ -707,8 +705,6 @@ void mer_destroy(mer_ctx* c) {
         if (i < 2 && c->ev_loss[i]) cudaEventDestroy(c->ev_loss[i]);
         if (c->sx[i]) cudaStreamDestroy(c->sx[i]);
     }
-    if (c->blas) cublasDestroy(c->blas);
-    dfree(c->blas_ws);
     if (c->st) cudaStreamDestroy(c->st);
     delete c;
 }
@@ -816,6 +812,10 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
         const int root2 = build_bvh(d->positions, d->tris, d->n_tris, hn, order);
         std::vector<HostNode4> h4;
         collapse_bvh4(hn, root2, h4);
+        if (3 * bvh4_levels(h4) > TRAV_STACK)
+            return bail(fail(c, MER_ERR_INVALID_ARG,
+                             "mer_scene_add: the triangle BVH has %d levels; the traversal stack holds %d (at most %d "
+                             "levels)", bvh4_levels(h4), TRAV_STACK, TRAV_STACK / 3));
         std::vector<Node> nodes(h4.size());
         for (size_t i = 0; i < h4.size(); ++i) {
             const HostNode4& h = h4[i];
@@ -996,20 +996,12 @@ mer_status mer_scene_add(mer_ctx* c, const mer_scene_desc* d, int32_t* problem_i
     }
     if (p->hyper.precond_lambda > 0.0f) {
         const cudaError_t pe = precond_init(p->pc, p->C, p->H, p->W, p->hyper.precond_lambda);
-        for (float* a : {p->pc.DW, p->pc.DH, p->pc.S, p->pc.T1, p->pc.T2})
+        for (void* a : {(void*)p->pc.ax_w.fft_tw, (void*)p->pc.ax_w.dct_tw, (void*)p->pc.ax_w.cos4,
+                        (void*)p->pc.ax_h.fft_tw, (void*)p->pc.ax_h.dct_tw, (void*)p->pc.ax_h.cos4, (void*)p->pc.St,
+                        (void*)p->pc.T1, (void*)p->pc.T2})
             if (a) p->allocs.push_back(a);   // freed with the problem, also on the error path
         AK(pe);
         p->precond = true;
-        if (!c->blas) {
-            const size_t ws = (size_t)32 << 20;
-            if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) {
-                c->blas = nullptr;
-                return bail(fail(c, MER_ERR_CUDA, "cublasCreate failed"));
-            }
-            AK(cudaMalloc(&c->blas_ws, ws));
-            cublasSetWorkspace(c->blas, c->blas_ws, ws);
-            cublasSetMathMode(c->blas, CUBLAS_PEDANTIC_MATH);   // plain FP32, no reduced-precision modes
-        }
     }
     AK(alloc(&p->target, npx));
     AK(alloc(&p->img, npx));
@@ -1409,6 +1401,23 @@ mer_status mer_profile_read(mer_ctx* c, mer_kernel_time* out, int32_t max_entrie
 mer_status mer_launch_count(mer_ctx* c, int64_t* out) {
     if (!c || !out) return fail(c, MER_ERR_INVALID_ARG, "null argument");
     *out = c->launches;
+    return MER_OK;
+}
+
+mer_status mer_precondition(int32_t C, int32_t H, int32_t W, float lambda, float* g, void* stream) {
+    if (C < 1 || C > MER_MAX_CHANNELS || H < 1 || W < 1 || H > 4094 || W > 4094 || !g || !(lambda >= 0.0f) ||
+        !std::isfinite(lambda))
+        return fail(nullptr, MER_ERR_INVALID_ARG, "bad arguments to mer_precondition");
+    if (lambda == 0.0f) return MER_OK;
+    Precond pc;
+    cudaError_t e = precond_init(pc, C, H, W, lambda);
+    if (!e) {
+        precond_apply(pc, g, (cudaStream_t)stream);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaStreamSynchronize((cudaStream_t)stream);
+    precond_free(pc);
+    if (e) return fail(nullptr, MER_ERR_CUDA, "mer_precondition: %s", cudaGetErrorString(e));
     return MER_OK;
 }
 

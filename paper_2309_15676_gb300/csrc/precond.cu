@@ -1,12 +1,21 @@
 // Texture-gradient preconditioning (the experiments' setup of Sec. 6 preconditions texture
 // gradients after Nicolet et al. 2021): g <- (I + lambda L)^{-1} g per channel on the texel grid,
 // L the graph Laplacian of the W x H grid with Neumann boundary ((L x)_p = sum over the grid
-// neighbours q of x_p - x_q). L is diagonal in the orthonormal DCT-II basis
-//   d_k(x) = a_k cos(pi k (x + 1/2) / N),  a_0 = sqrt(1/N), a_k = sqrt(2/N),
-// with eigenvalues (2 - 2 cos(pi k / W)) + (2 - 2 cos(pi l / H)), so the solve is exact: the two
-// separable transforms, one scale per frequency and the two inverse transforms. The transforms
-// are plain matrix products (cuBLAS SGEMM in FP32); the layout changes and the scale are the
-// small kernels below.
+// neighbours q of x_p - x_q). L is diagonal in the DCT-II basis cos(pi k (2x + 1) / (2N)), with
+// eigenvalues (2 - 2 cos(pi k / W)) + (2 - 2 cos(pi l / H)), so the solve is exact: the two
+// separable forward transforms, one scale per frequency, the two inverse transforms. With the
+// unnormalised transform C = Cos x and its inverse, (I + lambda L)^{-1} = Cos^{-1} S Cos for both
+// axes (the orthonormal scale factors cancel), S = 1 / (1 + lambda mu).
+//
+// The 1-D transforms run in shared memory, one block per row:
+//  - N a power of two (every texture size of the workloads): Makhoul's reordering, an N-point
+//    radix-2 complex FFT and one twiddle, so a transform costs O(N log N) and every pass is one
+//    read and one write of the texture;
+//  - any other N: the direct sum over a 4N-entry cosine table, O(N^2) per row.
+// Five launches per gradient texture: row transforms (reading the HWC gradient), a transpose, the
+// column transforms with the scale and the inverse column transforms, a transpose back, and the
+// inverse row transforms (writing the HWC gradient). Twiddles and cosines are computed on the host
+// in double precision.
 #include "precond.cuh"
 
 #include <cmath>
@@ -14,36 +23,218 @@
 
 namespace mer {
 
-__global__ void k_hwc_to_chw(const float* __restrict__ g, float* __restrict__ t, int C, int64_t HW) {
-    const int64_t n = HW * C, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t p = i / C;
-        const int c = (int)(i - p * C);
-        t[(int64_t)c * HW + p] = g[i];
+namespace {
+
+constexpr int PC_THREADS = 256;
+constexpr int kMaxTexSide = 4094;   // mer_scene_add's limit on a texture side
+
+__host__ __device__ inline bool is_pow2(int n) { return n >= 4 && (n & (n - 1)) == 0; }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ unsigned bit_reverse(unsigned i, int bits) { return __brev(i) >> (32 - bits); }
+
+// In-place radix-2 decimation-in-time FFT of z[0..N) (input already in bit-reversed order), all
+// threads of the block; sign -1: forward (twiddles tw[j] = exp(-2 pi i j / N)), +1: inverse
+// (conjugate twiddles, no 1/N).
+__device__ void fft_smem(float2* z, int N, int log2n, const float2* __restrict__ tw, float sign) {
+    for (int s = 1; s <= log2n; ++s) {
+        const int half = 1 << (s - 1);
+        const int step = N >> s;   // twiddle index stride
+        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+            const int j = b & (half - 1);
+            const int i0 = ((b >> (s - 1)) << s) + j, i1 = i0 + half;
+            float2 w = __ldg(tw + j * step);
+            if (sign > 0.0f) w.y = -w.y;   // the inverse uses the conjugate twiddles
+            const float2 t = cmul(w, z[i1]);
+            const float2 u = z[i0];
+            z[i0] = make_float2(u.x + t.x, u.y + t.y);
+            z[i1] = make_float2(u.x - t.x, u.y - t.y);
+        }
+        __syncthreads();
     }
 }
 
-__global__ void k_chw_to_hwc(const float* __restrict__ t, float* __restrict__ g, int C, int64_t HW) {
-    const int64_t n = HW * C, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t p = i / C;
-        const int c = (int)(i - p * C);
-        g[i] = t[(int64_t)c * HW + p];
+// Forward unnormalised DCT-II of x[0..N) (shared, stride sx) into out[0..N) (shared or global,
+// stride so): out[k] = sum_n x[n] cos(pi k (2n + 1) / (2N)). z: N float2 of shared scratch.
+__device__ void dct2_row(const float* x, int sx, float* out, int so, const PcAxis& ax, float2* z) {
+    const int N = ax.N;
+    if (ax.log2n > 0) {
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            // v[n] = x[2n] (n < N/2), v[N-1-n'] = x[2n'+1]
+            const float val = n < N / 2 ? x[(2 * n) * sx] : x[(2 * (N - 1 - n) + 1) * sx];
+            z[bit_reverse((unsigned)n, ax.log2n)] = make_float2(val, 0.0f);
+        }
+        __syncthreads();
+        fft_smem(z, N, ax.log2n, ax.fft_tw, -1.0f);
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            const float2 e = __ldg(ax.dct_tw + k);   // exp(-i pi k / (2N))
+            out[k * so] = e.x * z[k].x - e.y * z[k].y;
+        }
+        __syncthreads();
+    } else {
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            float acc = 0.0f;
+            int m = k;                       // k (2n + 1) mod 4N, stepping by 2k
+            const int step = (2 * k) % (4 * N);
+            for (int n = 0; n < N; ++n) {
+                acc = fmaf(x[n * sx], __ldg(ax.cos4 + m), acc);
+                m += step;
+                if (m >= 4 * N) m -= 4 * N;
+            }
+            out[k * so] = acc;
+        }
+        __syncthreads();
     }
 }
 
-__global__ void k_scale_planes(float* __restrict__ t, const float* __restrict__ S, int C, int64_t HW) {
-    const int64_t n = HW * C, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) t[i] *= S[i % HW];
+// Inverse of dct2_row: out[n] = x such that dct2_row(x) = C; C[0..N) in shared memory (stride sc).
+__device__ void dct2_inv_row(const float* C, int sc, float* out, int so, const PcAxis& ax, float2* z) {
+    const int N = ax.N;
+    if (ax.log2n > 0) {
+        // V[k] = exp(+i pi k / (2N)) (C[k] - i C[N-k]), C[N] = 0; v = IFFT(V) / N
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            const float a = C[k * sc], b = k == 0 ? 0.0f : C[(N - k) * sc];
+            const float2 e = __ldg(ax.dct_tw + k);
+            const float2 w = make_float2(e.x, -e.y);   // exp(+i pi k / (2N))
+            z[bit_reverse((unsigned)k, ax.log2n)] = cmul(w, make_float2(a, -b));
+        }
+        __syncthreads();
+        fft_smem(z, N, ax.log2n, ax.fft_tw, 1.0f);
+        const float inv = 1.0f / (float)N;
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            // x[2m] = Re v[m] (m < N/2), x[2m+1] = Re v[N-1-m]
+            const int src = (n & 1) ? (N - 1 - (n >> 1)) : (n >> 1);
+            out[n * so] = z[src].x * inv;
+        }
+        __syncthreads();
+    } else {
+        // x[n] = sum_k w_k C[k] cos(pi k (2n + 1) / (2N)), w_0 = 1/N, w_k = 2/N
+        const float w0 = 1.0f / (float)N, w1 = 2.0f / (float)N;
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            float acc = 0.0f;
+            int m = 0;                       // k (2n + 1) mod 4N, stepping by 2n + 1
+            const int step = (2 * n + 1) % (4 * N);
+            for (int k = 0; k < N; ++k) {
+                acc = fmaf((k == 0 ? w0 : w1) * C[k * sc], __ldg(ax.cos4 + m), acc);
+                m += step;
+                if (m >= 4 * N) m -= 4 * N;
+            }
+            out[n * so] = acc;
+        }
+        __syncthreads();
+    }
 }
 
-static void dct_matrix(int N, std::vector<float>& D) {
-    D.resize((size_t)N * N);
+// rows of the HWC gradient: T[c][y][k] = forward transform along x of g[y][.][c]
+__global__ void __launch_bounds__(PC_THREADS) k_pc_rows_fwd(const float* __restrict__ g, float* __restrict__ T, int C,
+                                                            int H, PcAxis ax) {
+    extern __shared__ float4 pc_smem[];
+    const int W = ax.N, y = blockIdx.x;
+    float* row = reinterpret_cast<float*>(pc_smem);                     // W x C
+    float2* z = reinterpret_cast<float2*>(row + ((W * C + 3) & ~3));    // N complex
+    const float* src = g + (size_t)y * W * C;
+    for (int i = threadIdx.x; i < W * C; i += blockDim.x) row[i] = src[i];
+    __syncthreads();
+    for (int c = 0; c < C; ++c) dct2_row(row + c, C, T + ((size_t)c * H + y) * W, 1, ax, z);
+}
+
+// inverse rows back into the HWC gradient: g[y][.][c] = inverse transform of T[c][y][.]
+__global__ void __launch_bounds__(PC_THREADS) k_pc_rows_inv(const float* __restrict__ T, float* __restrict__ g, int C,
+                                                            int H, PcAxis ax) {
+    extern __shared__ float4 pc_smem[];
+    const int W = ax.N, y = blockIdx.x;
+    float* row = reinterpret_cast<float*>(pc_smem);                     // C x W in, then W x C out
+    float* res = row + ((size_t)C * W + 3) / 4 * 4;
+    float2* z = reinterpret_cast<float2*>(res + ((W * C + 3) & ~3));
+    for (int c = 0; c < C; ++c)
+        for (int i = threadIdx.x; i < W; i += blockDim.x) row[c * W + i] = T[((size_t)c * H + y) * W + i];
+    __syncthreads();
+    for (int c = 0; c < C; ++c) dct2_inv_row(row + c * W, 1, res + c, C, ax, z);
+    float* dst = g + (size_t)y * W * C;
+    for (int i = threadIdx.x; i < W * C; i += blockDim.x) dst[i] = res[i];
+}
+
+// columns (as rows after the transpose): U[c][k][.] <- inverse_y( S^T[k][.] * forward_y(U[c][k][.]) )
+__global__ void __launch_bounds__(PC_THREADS) k_pc_cols(float* __restrict__ U, const float* __restrict__ St, int W,
+                                                        PcAxis ax) {
+    extern __shared__ float4 pc_smem[];
+    const int H = ax.N;
+    const int c = blockIdx.x / W, k = blockIdx.x - c * W;
+    float* col = reinterpret_cast<float*>(pc_smem);          // H
+    float* frq = col + ((H + 3) & ~3);                       // H
+    float2* z = reinterpret_cast<float2*>(frq + ((H + 3) & ~3));
+    float* line = U + ((size_t)c * W + k) * H;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) col[i] = line[i];
+    __syncthreads();
+    dct2_row(col, 1, frq, 1, ax, z);
+    const float* s = St + (size_t)k * H;
+    for (int l = threadIdx.x; l < H; l += blockDim.x) frq[l] *= __ldg(s + l);
+    __syncthreads();
+    dct2_inv_row(frq, 1, line, 1, ax, z);
+}
+
+// out[c][j][i] = in[c][i][j] for C planes of R x Q (32 x 32 tiles)
+__global__ void k_pc_transpose(const float* __restrict__ in, float* __restrict__ out, int R, int Q) {
+    __shared__ float tile[32][33];
+    const int c = blockIdx.z;
+    const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const float* src = in + (size_t)c * R * Q;
+    float* dst = out + (size_t)c * R * Q;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int r = r0 + dy, q = q0 + threadIdx.x;
+        if (r < R && q < Q) tile[dy][threadIdx.x] = src[(size_t)r * Q + q];
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int q = q0 + dy, r = r0 + threadIdx.x;
+        if (q < Q && r < R) dst[(size_t)q * R + r] = tile[threadIdx.x][dy];
+    }
+}
+
+size_t rows_fwd_smem(int W, int C) { return sizeof(float) * (((size_t)W * C + 3) & ~(size_t)3) + sizeof(float2) * W; }
+size_t rows_inv_smem(int W, int C) {
+    return 2 * sizeof(float) * (((size_t)W * C + 3) & ~(size_t)3) + sizeof(float2) * W;
+}
+size_t cols_smem(int H) { return 2 * sizeof(float) * (((size_t)H + 3) & ~(size_t)3) + sizeof(float2) * H; }
+
+cudaError_t axis_init(PcAxis& ax, int N) {
+    ax.N = N;
+    ax.log2n = 0;
+    if (is_pow2(N))
+        while ((1 << ax.log2n) < N) ++ax.log2n;
     const double pi = 3.14159265358979323846;
-    for (int k = 0; k < N; ++k) {
-        const double a = k == 0 ? std::sqrt(1.0 / N) : std::sqrt(2.0 / N);
-        for (int x = 0; x < N; ++x) D[(size_t)k * N + x] = (float)(a * std::cos(pi * k * (x + 0.5) / N));
+    cudaError_t e = cudaSuccess;
+    if (ax.log2n > 0) {
+        std::vector<float2> ft(N / 2), dt(N);
+        for (int j = 0; j < N / 2; ++j) ft[j] = make_float2((float)std::cos(2 * pi * j / N), (float)-std::sin(2 * pi * j / N));
+        for (int k = 0; k < N; ++k) dt[k] = make_float2((float)std::cos(pi * k / (2.0 * N)), (float)-std::sin(pi * k / (2.0 * N)));
+        e = cudaMalloc(&ax.fft_tw, sizeof(float2) * ft.size());
+        if (!e) e = cudaMalloc(&ax.dct_tw, sizeof(float2) * dt.size());
+        if (!e) e = cudaMemcpy(ax.fft_tw, ft.data(), sizeof(float2) * ft.size(), cudaMemcpyHostToDevice);
+        if (!e) e = cudaMemcpy(ax.dct_tw, dt.data(), sizeof(float2) * dt.size(), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> ct(4 * (size_t)N);
+        for (int m = 0; m < 4 * N; ++m) ct[m] = (float)std::cos(pi * m / (2.0 * N));
+        e = cudaMalloc(&ax.cos4, sizeof(float) * ct.size());
+        if (!e) e = cudaMemcpy(ax.cos4, ct.data(), sizeof(float) * ct.size(), cudaMemcpyHostToDevice);
     }
+    return e;
+}
+
+void axis_free(PcAxis& ax) {
+    for (void* p : {(void*)ax.fft_tw, (void*)ax.dct_tw, (void*)ax.cos4})
+        if (p) cudaFree(p);
+    ax.fft_tw = ax.dct_tw = nullptr;
+    ax.cos4 = nullptr;
+}
+
+}  // namespace
+
+size_t precond_max_smem(int C, int H, int W) {
+    return std::max(std::max(rows_fwd_smem(W, C), rows_inv_smem(W, C)), cols_smem(H));
 }
 
 cudaError_t precond_init(Precond& pc, int C, int H, int W, float lambda) {
@@ -51,55 +242,52 @@ cudaError_t precond_init(Precond& pc, int C, int H, int W, float lambda) {
     pc.H = H;
     pc.W = W;
     pc.lambda = lambda;
-    std::vector<float> DW, DH, S((size_t)H * W);
-    dct_matrix(W, DW);
-    dct_matrix(H, DH);
+    std::vector<float> St((size_t)H * W);
     const double pi = 3.14159265358979323846;
-    for (int l = 0; l < H; ++l)
-        for (int k = 0; k < W; ++k) {
+    for (int k = 0; k < W; ++k)
+        for (int l = 0; l < H; ++l) {
             const double mu = (2.0 - 2.0 * std::cos(pi * k / W)) + (2.0 - 2.0 * std::cos(pi * l / H));
-            S[(size_t)l * W + k] = (float)(1.0 / (1.0 + (double)lambda * mu));
+            St[(size_t)k * H + l] = (float)(1.0 / (1.0 + (double)lambda * mu));
         }
     const size_t plane = (size_t)C * H * W;
-    cudaError_t e = cudaMalloc(&pc.DW, sizeof(float) * DW.size());
-    if (!e) e = cudaMalloc(&pc.DH, sizeof(float) * DH.size());
-    if (!e) e = cudaMalloc(&pc.S, sizeof(float) * S.size());
+    cudaError_t e = axis_init(pc.ax_w, W);
+    if (!e) e = axis_init(pc.ax_h, H);
+    if (!e) e = cudaMalloc(&pc.St, sizeof(float) * St.size());
     if (!e) e = cudaMalloc(&pc.T1, sizeof(float) * plane);
     if (!e) e = cudaMalloc(&pc.T2, sizeof(float) * plane);
-    if (!e) e = cudaMemcpy(pc.DW, DW.data(), sizeof(float) * DW.size(), cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(pc.DH, DH.data(), sizeof(float) * DH.size(), cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(pc.S, S.data(), sizeof(float) * S.size(), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(pc.St, St.data(), sizeof(float) * St.size(), cudaMemcpyHostToDevice);
+    // the opt-in shared-memory limit of the three row kernels, set for the largest texture the
+    // library accepts (so that one problem's setting never lowers another's)
+    const int smem = (int)precond_max_smem(MER_MAX_CHANNELS, kMaxTexSide, kMaxTexSide);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (!e) e = cudaFuncSetAttribute(k_pc_rows_fwd, at, smem);
+    if (!e) e = cudaFuncSetAttribute(k_pc_rows_inv, at, smem);
+    if (!e) e = cudaFuncSetAttribute(k_pc_cols, at, smem);
     return e;
 }
 
 void precond_free(Precond& pc) {
-    for (float* p : {pc.DW, pc.DH, pc.S, pc.T1, pc.T2})
+    axis_free(pc.ax_w);
+    axis_free(pc.ax_h);
+    for (float* p : {pc.St, pc.T1, pc.T2})
         if (p) cudaFree(p);
-    pc.DW = pc.DH = pc.S = pc.T1 = pc.T2 = nullptr;
+    pc.St = pc.T1 = pc.T2 = nullptr;
 }
 
-// Row-major products through the column-major library: C(m x n) = op_a(A) op_b(B) is the
-// column-major C^T = op_b(B)^T op_a(A)^T, i.e. the call with the operands swapped.
-int precond_apply(cublasHandle_t h, const Precond& pc, float* g, cudaStream_t st) {
+int precond_apply(const Precond& pc, float* g, cudaStream_t st) {
     const int C = pc.C, H = pc.H, W = pc.W;
-    const int64_t HW = (int64_t)H * W, n = HW * C;
-    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
-    const float one = 1.0f, zero = 0.0f;
-    cublasSetStream(h, st);
-    k_hwc_to_chw<<<blocks, 256, 0, st>>>(g, pc.T1, C, HW);
-    // rows (along W): T2 = T1 . DW^T      (C*H rows)
-    cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, W, C * H, W, &one, pc.DW, W, pc.T1, W, &zero, pc.T2, W);
-    // columns (along H), per channel: T1_c = DH . T2_c
-    cublasSgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, W, H, H, &one, pc.T2, W, HW, pc.DH, H, 0, &zero, pc.T1, W,
-                              HW, C);
-    k_scale_planes<<<blocks, 256, 0, st>>>(pc.T1, pc.S, C, HW);
-    // inverse columns: T2_c = DH^T . T1_c
-    cublasSgemmStridedBatched(h, CUBLAS_OP_N, CUBLAS_OP_T, W, H, H, &one, pc.T1, W, HW, pc.DH, H, 0, &zero, pc.T2, W,
-                              HW, C);
-    // inverse rows: T1 = T2 . DW
-    cublasSgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, W, C * H, W, &one, pc.DW, W, pc.T2, W, &zero, pc.T1, W);
-    k_chw_to_hwc<<<blocks, 256, 0, st>>>(pc.T1, g, C, HW);
-    return 3;   // own kernels (the four products are library launches)
+    const dim3 tb(32, 8);
+    // T1[c][y][k] <- row transforms of g
+    k_pc_rows_fwd<<<H, PC_THREADS, rows_fwd_smem(W, C), st>>>(g, pc.T1, C, H, pc.ax_w);
+    // T2[c][k][y] <- T1[c][y][k]
+    k_pc_transpose<<<dim3((W + 31) / 32, (H + 31) / 32, C), tb, 0, st>>>(pc.T1, pc.T2, H, W);
+    // columns: forward, scale, inverse (in place on T2)
+    k_pc_cols<<<C * W, PC_THREADS, cols_smem(H), st>>>(pc.T2, pc.St, W, pc.ax_h);
+    // T1[c][y][k] <- T2[c][k][y]
+    k_pc_transpose<<<dim3((H + 31) / 32, (W + 31) / 32, C), tb, 0, st>>>(pc.T2, pc.T1, W, H);
+    // g <- inverse row transforms of T1
+    k_pc_rows_inv<<<H, PC_THREADS, rows_inv_smem(W, C), st>>>(pc.T1, g, C, H, pc.ax_w);
+    return 5;
 }
 
 }  // namespace mer

@@ -49,6 +49,10 @@ def test_context_free_errors_without_gpu(lib):
     st = lib.mer_philox(0, 0, None, 5, None, None)
     assert st == 1
     assert b"bad arguments" in lib.mer_last_error(None)
+    for args in ((0, 4, 4, 1.0), (6, 4, 4, 1.0), (3, 0, 4, 1.0), (3, 4, 4095, 1.0), (3, 4, 4, -1.0),
+                 (3, 4, 4, float("nan")), (3, 4, 4, float("inf"))):
+        assert lib.mer_precondition(*args, ct.c_void_p(16), None) == 1, args
+        assert b"bad arguments to mer_precondition" in lib.mer_last_error(None)
 
 
 def test_struct_sizes_match_header():

@@ -1,6 +1,8 @@
 """Gradient preconditioning on the GPU (precond_lambda > 0): after a gradient step, F and dF of a
 preconditioned problem equal the oracle's (I + lambda L)^{-1} applied to the unpreconditioned
-gradients of the same problem on the same counters (relative L2 below 1e-4)."""
+gradients of the same problem on the same counters (relative L2 below 1e-4); and the solve on its
+own (mer_precondition) equals the oracle's on random gradients of power-of-two sides (the FFT route,
+up to 2048), other sides (the direct route) and mixed shapes, for weak and strong smoothing."""
 import numpy as np
 import pytest
 
@@ -45,8 +47,8 @@ def test_preconditioned_gradients_match_oracle():
 
 
 def test_preconditioned_iterations_in_a_graph():
-    """The preconditioner's library products are captured in the iteration graph: graph-launched
-    iterations equal plain ones."""
+    """The preconditioner's kernels are captured in the iteration graph: graph-launched iterations
+    equal plain ones."""
     torch = need_gpu()
     from paper_2309_15676_gb300.api import Context, HyperParams
     w = synth.workload_box(32, 32, 16, max_depth=3)
@@ -61,3 +63,18 @@ def test_preconditioned_iterations_in_a_graph():
         out.append(c.get_params(p).cpu().numpy())
         c.close()
     assert np.allclose(out[0], out[1], rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("C,H,W", [(5, 64, 64), (3, 1024, 1024), (5, 2048, 64), (5, 64, 2048), (3, 5, 7),
+                                   (5, 100, 36), (3, 1, 33), (5, 33, 1), (3, 1, 1), (5, 48, 2), (4, 4, 4),
+                                   (3, 256, 100)])
+@pytest.mark.parametrize("lam", [0.5, 4.0, 100.0])
+def test_precondition_standalone_matches_oracle(C, H, W, lam):
+    """FP32 transforms of a texture of unit-variance noise: relative L2 error below 1e-5 (a few
+    FP32 ulp times the log of the side for the FFT route, the sum length for the direct route)."""
+    torch = need_gpu()
+    from paper_2309_15676_gb300.api import precondition
+    g = np.random.default_rng(C * 7919 + H * 31 + W).normal(size=(H, W, C)).astype(np.float32)
+    got = precondition(torch.from_numpy(g).cuda(), lam).cpu().numpy()
+    ref = precond.precondition(g.astype(np.float64), lam)
+    assert rel_l2(got, ref) < 1e-5, rel_l2(got, ref)
