@@ -217,6 +217,23 @@ int emit4(const std::vector<HostNode>& bin, int n2, std::vector<HostNode4>& out)
 
 }  // namespace
 
+int bvh4_levels(const std::vector<HostNode4>& nodes) {
+    if (nodes.empty()) return 0;
+    // inner levels along the deepest root-to-leaf path (iterative: node, level)
+    std::vector<std::pair<int, int>> todo{{0, 1}};
+    int best = 0;
+    while (!todo.empty()) {
+        const auto [n, lv] = todo.back();
+        todo.pop_back();
+        best = std::max(best, lv);
+        for (int k = 0; k < 4; ++k) {
+            const int c = nodes[n].child[k];
+            if (c >= 0 && c != kEmptyChild) todo.push_back({c, lv + 1});
+        }
+    }
+    return best;
+}
+
 void collapse_bvh4(const std::vector<HostNode>& bin, int root, std::vector<HostNode4>& out) {
     out.clear();
     if (root < 0) return;

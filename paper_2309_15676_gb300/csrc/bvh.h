@@ -28,6 +28,11 @@ struct HostNode4 {
 // surface area by its own two children until it holds four (or only leaves are left).
 void collapse_bvh4(const std::vector<HostNode>& bin, int root, std::vector<HostNode4>& out);
 
+// Inner-node levels on the deepest root-to-leaf path of a four-wide tree (root = level 1; 0 for an
+// empty tree). A nearest-first traversal keeps at most three deferred children per level on its
+// stack, so it needs 3 x levels stack entries.
+int bvh4_levels(const std::vector<HostNode4>& nodes);
+
 // Builds a binned-SAH BVH over n_tris triangles (vertex positions pos[nv][3], indices
 // tris[n][3]). Returns the root's local index (-1 if no triangles); order[k] is the
 // original triangle id of leaf-ordered triangle k.

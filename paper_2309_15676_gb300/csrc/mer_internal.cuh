@@ -73,6 +73,9 @@ __device__ __forceinline__ v3 normalize(v3 a) { return a * (1.0f / sqrtf(dot(a, 
 // child >= 0: inner node index; child < 0: leaf ~((first << 3) | (count - 1)) over the
 // leaf-ordered triangles [first, first + count); NODE_EMPTY: unused slot.
 constexpr int NODE_EMPTY = 0x7fffffff;
+// Traversal stack entries per thread: a nearest-first walk defers at most three children per inner
+// level, so trees of up to TRAV_STACK / 3 inner levels are accepted (mer_scene_add refuses deeper).
+constexpr int TRAV_STACK = 64;
 struct __align__(16) Node {
     float4 lx, hx, ly, hy, lz, hz;
     int4 child;
@@ -230,14 +233,18 @@ __device__ __forceinline__ float pow5(float x) {
     return x2 * x2 * x;
 }
 
-// value f (RGB). n faces wo.
-__device__ __forceinline__ v3 bsdf_f(const MatEval& m, v3 n, v3 wo, v3 wi) {
+// Half vector of (wo, wi). A direction the GGX lobe sampled comes with its half vector, which
+// the evaluation uses as is: recomputing it from wo + wi loses about eps / (wo . h) of relative
+// precision (wo + wi = 2 (wo . h) h), which the steep GGX peak of a low roughness amplifies.
+__device__ __forceinline__ v3 half_vec(v3 wo, v3 wi) { return normalize(wo + wi); }
+
+// value f (RGB). n faces wo; h = the half vector of (wo, wi).
+__device__ __forceinline__ v3 bsdf_f(const MatEval& m, v3 n, v3 wo, v3 wi, v3 h) {
     const float co = dot(n, wo), ci = dot(n, wi);
     if (co <= 0.0f || ci <= 0.0f) return mk(0, 0, 0);
     if (m.type == 0) return mk(m.th[0] * INV_PI_F, m.th[1] * INV_PI_F, m.th[2] * INV_PI_F);
     const float metal = m.th[3], r = m.th[4];
     const float a = r * r, a2 = a * a;
-    const v3 h = normalize(wo + wi);
     const float ch = dot(n, h), vh = dot(wi, h);
     const float S = ggx_d(a2, ch, sin2(n, h)) * smith_g1(a2, co) * smith_g1(a2, ci) / (4.0f * co * ci);
     const float fw = pow5(1.0f - vh);
@@ -252,7 +259,7 @@ __device__ __forceinline__ v3 bsdf_f(const MatEval& m, v3 n, v3 wo, v3 wi) {
 }
 
 // value and derivatives df[j][c] = d f_c / d theta_j
-__device__ __forceinline__ v3 bsdf_f_grad(const MatEval& m, v3 n, v3 wo, v3 wi, float df[MAXC][3]) {
+__device__ __forceinline__ v3 bsdf_f_grad(const MatEval& m, v3 n, v3 wo, v3 wi, v3 h, float df[MAXC][3]) {
 #pragma unroll
     for (int j = 0; j < MAXC; ++j) df[j][0] = df[j][1] = df[j][2] = 0.0f;
     const float co = dot(n, wo), ci = dot(n, wi);
@@ -263,7 +270,6 @@ __device__ __forceinline__ v3 bsdf_f_grad(const MatEval& m, v3 n, v3 wo, v3 wi, 
     }
     const float metal = m.th[3], r = m.th[4];
     const float a = r * r, a2 = a * a;
-    const v3 h = normalize(wo + wi);
     const float ch = dot(n, h), vh = dot(wi, h);
     const float k = ggx_k(a2, ch, sin2(n, h));
     const float D = a2 / (PI_F * k * k);
@@ -292,20 +298,21 @@ __device__ __forceinline__ v3 bsdf_f_grad(const MatEval& m, v3 n, v3 wo, v3 wi, 
     return mk(f[0], f[1], f[2]);
 }
 
-__device__ __forceinline__ float bsdf_pdf(const MatEval& m, v3 n, v3 wo, v3 wi) {
+__device__ __forceinline__ float bsdf_pdf(const MatEval& m, v3 n, v3 wo, v3 wi, v3 h) {
     const float co = dot(n, wo), ci = dot(n, wi);
     if (co <= 0.0f || ci <= 0.0f) return 0.0f;
     if (m.type == 0) return ci * INV_PI_F;
     const float a = m.th[4] * m.th[4], a2 = a * a;
     const float ps = 0.5f * (1.0f + m.th[3]);
-    const v3 h = normalize(wo + wi);
     const float ch = dot(n, h), oh = dot(wo, h);
     const float pspec = oh > 0.0f ? ggx_d(a2, ch, sin2(n, h)) * ch / (4.0f * oh) : 0.0f;
     return ps * pspec + (1.0f - ps) * ci * INV_PI_F;
 }
 
-// returns false if the sampled direction is not above the surface
-__device__ __forceinline__ bool bsdf_sample(const MatEval& m, v3 n, v3 wo, float ul, float u1, float u2, v3& wi) {
+// returns false if the sampled direction is not above the surface; h: the half vector of
+// (wo, wi) (the sampled one for the GGX lobe)
+__device__ __forceinline__ bool bsdf_sample(const MatEval& m, v3 n, v3 wo, float ul, float u1, float u2, v3& wi,
+                                            v3& hv) {
     if (m.type == 1 && ul < 0.5f * (1.0f + m.th[3])) {
         const float a = m.th[4] * m.th[4], a2 = a * a;
         const float t2 = a2 * u1 / (1.0f - u1);       // tan^2 of the half-vector angle
@@ -317,8 +324,10 @@ __device__ __forceinline__ bool bsdf_sample(const MatEval& m, v3 n, v3 wo, float
         const float oh = dot(wo, h);
         if (oh <= 0.0f) return false;
         wi = h * (2.0f * oh) - wo;
+        hv = h;
     } else {
         wi = cosine_dir(n, u1, u2);
+        hv = half_vec(wo, wi);
     }
     return dot(n, wi) > 0.0f;
 }

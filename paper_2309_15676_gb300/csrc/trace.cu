@@ -118,107 +118,149 @@ struct Hit {
     int prim;   // local: triangles [0, n_tris), spheres n_tris + i; -1 = miss
 };
 
-// closest hit (ANY = false) or any hit before tmax (ANY = true). Ties in t go to the
-// smaller primitive id, independent of traversal order.
 // algorithmic work of a traversal (counted only in the counting instantiation)
 struct TravCount {
     unsigned nodes = 0;   // four-box node tests
     unsigned prims = 0;   // triangle and sphere tests
 };
 
-template <bool ANY, bool STATS = false>
-__device__ __forceinline__ bool traverse(const ProblemDev& P, const Node* s_nodes, int smem_n, v3 o, v3 d,
-                                         float tmax, Hit& h, TravCount& tc) {
-    h.t = tmax;
-    h.prim = -1;
-    h.b1 = h.b2 = 0.0f;
-    int best = 0x7fffffff;
-    if (P.nodes) {
-        const float dx = fabsf(d.x) < 1e-20f ? copysignf(1e-20f, d.x) : d.x;
-        const float dy = fabsf(d.y) < 1e-20f ? copysignf(1e-20f, d.y) : d.y;
-        const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
-        const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
-        const float ox = o.x * ix, oy = o.y * iy, oz = o.z * iz;
-        const int sx = ix < 0.0f ? 1 : 0, sy = iy < 0.0f ? 1 : 0, sz = iz < 0.0f ? 1 : 0;
-        int stack[64];
-        int sp = 0;
-        int node = 0;
-        const float grow = 1.0f + 4.8e-7f;   // conservative box exit (a few ulp)
-        while (true) {
-            while (node >= 0) {
-                const NodeRay n = load_node(P.nodes, s_nodes, smem_n, node, sx, sy, sz);
-                if (STATS) tc.nodes++;
-                const float tfar = h.t * grow;
-                // slab test of the four children; a miss (or an unused slot) sorts last
-                float tn[4];
-                int rf[4];
-                const float nxs[4] = {n.nx.x, n.nx.y, n.nx.z, n.nx.w}, fxs[4] = {n.fx.x, n.fx.y, n.fx.z, n.fx.w};
-                const float nys[4] = {n.ny.x, n.ny.y, n.ny.z, n.ny.w}, fys[4] = {n.fy.x, n.fy.y, n.fy.z, n.fy.w};
-                const float nzs[4] = {n.nz.x, n.nz.y, n.nz.z, n.nz.w}, fzs[4] = {n.fz.x, n.fz.y, n.fz.z, n.fz.w};
-                const int cs[4] = {n.child.x, n.child.y, n.child.z, n.child.w};
-                int nh = 0;
+// One lane's traversal state: closest hit (any = false) or any hit before tmax (any = true) of
+// the ray (o, d) against the problem's four-wide BVH and then its spheres. Ties in t go to the
+// smaller primitive id, independent of traversal order. Deferred children go on the lane's stack;
+// the scene upload refuses trees whose depth could need more than TRAV_STACK entries (three
+// deferred children per inner level), and should a push still find the stack full, `complete`
+// becomes false and the caller reports MER_ERR_BOUNDS through the error word.
+struct TravRay {
+    v3 o, d;
+    float ix, iy, iz, ox, oy, oz;   // reciprocal direction and origin scaled by it
+    int sx, sy, sz;                 // direction signs: which slab plane is near
+    float t, b1, b2;                // closest hit so far (t = tmax initially)
+    int best;                       // its triangle id (0x7fffffff: none)
+    int node, sp;                   // next node (NODE_EMPTY: finished), stack depth
+    bool any, hit_any, complete;
+};
+
+__device__ __forceinline__ void trav_begin(TravRay& R, v3 o, v3 d, float tmax, bool any, bool has_bvh) {
+    R.o = o;
+    R.d = d;
+    const float dx = fabsf(d.x) < 1e-20f ? copysignf(1e-20f, d.x) : d.x;
+    const float dy = fabsf(d.y) < 1e-20f ? copysignf(1e-20f, d.y) : d.y;
+    const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
+    R.ix = 1.0f / dx;
+    R.iy = 1.0f / dy;
+    R.iz = 1.0f / dz;
+    R.ox = o.x * R.ix;
+    R.oy = o.y * R.iy;
+    R.oz = o.z * R.iz;
+    R.sx = R.ix < 0.0f ? 1 : 0;
+    R.sy = R.iy < 0.0f ? 1 : 0;
+    R.sz = R.iz < 0.0f ? 1 : 0;
+    R.t = tmax;
+    R.b1 = R.b2 = 0.0f;
+    R.best = 0x7fffffff;
+    R.node = has_bvh ? 0 : NODE_EMPTY;
+    R.sp = 0;
+    R.any = any;
+    R.hit_any = false;
+    R.complete = true;
+}
+
+// One step of the BVH walk: descend through inner nodes (nearest child first, the others
+// deferred) until a leaf, test its triangles, take the next deferred subtree. Returns true when
+// the walk has finished (stack empty, or any-hit found).
+template <bool STATS>
+__device__ __forceinline__ bool trav_step(const ProblemDev& P, const Node* s_nodes, int smem_n, TravRay& R,
+                                          int* stack, TravCount& tc) {
+    const float grow = 1.0f + 4.8e-7f;   // conservative box exit (a few ulp)
+    int node = R.node;
+    while (node >= 0 && node != NODE_EMPTY) {
+        const NodeRay n = load_node(P.nodes, s_nodes, smem_n, node, R.sx, R.sy, R.sz);
+        if (STATS) tc.nodes++;
+        const float tfar = R.t * grow;
+        // slab test of the four children; a miss (or an unused slot) sorts last
+        float tn[4];
+        int rf[4];
+        const float nxs[4] = {n.nx.x, n.nx.y, n.nx.z, n.nx.w}, fxs[4] = {n.fx.x, n.fx.y, n.fx.z, n.fx.w};
+        const float nys[4] = {n.ny.x, n.ny.y, n.ny.z, n.ny.w}, fys[4] = {n.fy.x, n.fy.y, n.fy.z, n.fy.w};
+        const float nzs[4] = {n.nz.x, n.nz.y, n.nz.z, n.nz.w}, fzs[4] = {n.fz.x, n.fz.y, n.fz.z, n.fz.w};
+        const int cs[4] = {n.child.x, n.child.y, n.child.z, n.child.w};
+        int nh = 0;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float t0 = fmax3(fmaf(nxs[k], ix, -ox), fmaf(nys[k], iy, -oy), fmaxf(fmaf(nzs[k], iz, -oz), 0.0f));
-                    const float t1 = fmin3(fmaf(fxs[k], ix, -ox), fmaf(fys[k], iy, -oy), fminf(fmaf(fzs[k], iz, -oz), tfar));
-                    const bool hit = t0 <= t1 && cs[k] != NODE_EMPTY;
-                    tn[k] = hit ? t0 : INFINITY;
-                    rf[k] = cs[k];
-                    nh += hit ? 1 : 0;
-                }
-                if (nh == 0) {
-                    if (sp == 0) { node = NODE_EMPTY; break; }
-                    node = stack[--sp];
-                    continue;
-                }
-                // nearest first: five compare-exchanges sort the four (t, child) pairs
+        for (int k = 0; k < 4; ++k) {
+            const float t0 = fmax3(fmaf(nxs[k], R.ix, -R.ox), fmaf(nys[k], R.iy, -R.oy), fmaxf(fmaf(nzs[k], R.iz, -R.oz), 0.0f));
+            const float t1 = fmin3(fmaf(fxs[k], R.ix, -R.ox), fmaf(fys[k], R.iy, -R.oy), fminf(fmaf(fzs[k], R.iz, -R.oz), tfar));
+            const bool hit = t0 <= t1 && cs[k] != NODE_EMPTY;
+            tn[k] = hit ? t0 : INFINITY;
+            rf[k] = cs[k];
+            nh += hit ? 1 : 0;
+        }
+        if (nh == 0) {
+            node = R.sp == 0 ? NODE_EMPTY : stack[--R.sp];
+            continue;
+        }
+        // nearest first: five compare-exchanges sort the four (t, child) pairs
 #define MER_CX(i, j)                                   \
     if (tn[j] < tn[i]) {                               \
         const float tt = tn[i]; tn[i] = tn[j]; tn[j] = tt; \
         const int rr = rf[i]; rf[i] = rf[j]; rf[j] = rr;   \
     }
-                MER_CX(0, 1) MER_CX(2, 3) MER_CX(0, 2) MER_CX(1, 3) MER_CX(1, 2)
+        MER_CX(0, 1) MER_CX(2, 3) MER_CX(0, 2) MER_CX(1, 3) MER_CX(1, 2)
 #undef MER_CX
-                if (nh > 3 && sp < 64) stack[sp++] = rf[3];
-                if (nh > 2 && sp < 64) stack[sp++] = rf[2];
-                if (nh > 1 && sp < 64) stack[sp++] = rf[1];
-                node = rf[0];
-            }
-            if (node == NODE_EMPTY) break;
-            // leaf
-            const int x = ~node;
-            const int first = x >> 3, count = (x & 7) + 1;
-            if (STATS) tc.prims += count;
-            for (int k = 0; k < count; ++k) {
-                const TriGeo T = load_tri(P.tris, first + k);
-                float t, u, v;
-                if (tri_test(T, o, d, t, u, v)) {
-                    const int pid = __float_as_int(T.v0.w);
-                    if (ANY) {
-                        if (t < tmax) { h.prim = pid; h.t = t; return true; }
-                    } else if (t < h.t || (t == h.t && pid < best)) {
-                        h.t = t; h.b1 = u; h.b2 = v; best = pid;
-                    }
+        if (nh > 3) { if (R.sp < TRAV_STACK) stack[R.sp++] = rf[3]; else R.complete = false; }
+        if (nh > 2) { if (R.sp < TRAV_STACK) stack[R.sp++] = rf[2]; else R.complete = false; }
+        if (nh > 1) { if (R.sp < TRAV_STACK) stack[R.sp++] = rf[1]; else R.complete = false; }
+        node = rf[0];
+    }
+    if (node == NODE_EMPTY) {
+        R.node = NODE_EMPTY;
+        return true;
+    }
+    // leaf
+    const int x = ~node;
+    const int first = x >> 3, count = (x & 7) + 1;
+    if (STATS) tc.prims += count;
+    for (int k = 0; k < count; ++k) {
+        const TriGeo T = load_tri(P.tris, first + k);
+        float t, u, v;
+        if (tri_test(T, R.o, R.d, t, u, v)) {
+            const int pid = __float_as_int(T.v0.w);
+            if (R.any) {
+                if (t < R.t) {
+                    R.hit_any = true;
+                    R.node = NODE_EMPTY;
+                    return true;
                 }
+            } else if (t < R.t || (t == R.t && pid < R.best)) {
+                R.t = t; R.b1 = u; R.b2 = v; R.best = pid;
             }
-            if (sp == 0) break;
-            node = stack[--sp];
         }
     }
-    if (!ANY) h.prim = (best == 0x7fffffff) ? -1 : best;
+    R.node = R.sp == 0 ? NODE_EMPTY : stack[--R.sp];
+    return R.node == NODE_EMPTY;
+}
+
+// the walk has finished: the spheres, then the hit (closest: prim -1 if none; any: prim >= 0
+// if occluded)
+template <bool STATS>
+__device__ __forceinline__ Hit trav_end(const ProblemDev& P, TravRay& R, TravCount& tc) {
+    Hit h;
+    h.t = R.t;
+    h.b1 = R.b1;
+    h.b2 = R.b2;
+    h.prim = R.any ? (R.hit_any ? 0 : -1) : (R.best == 0x7fffffff ? -1 : R.best);
     if (STATS) tc.prims += P.n_sph;
-    for (int i = 0; i < P.n_sph; ++i) {
+    for (int i = 0; i < P.n_sph && !(R.any && h.prim >= 0); ++i) {
         const Sphere S = P.sph[i];
         float t;
-        if (sphere_test(S, o, d, t)) {
-            if (ANY) {
-                if (t < tmax) { h.prim = P.n_tris + i; return true; }
+        if (sphere_test(S, R.o, R.d, t)) {
+            if (R.any) {
+                if (t < R.t) h.prim = P.n_tris + i;
             } else if (t < h.t) {
                 h.t = t; h.prim = P.n_tris + i; h.b1 = h.b2 = 0.0f;
             }
         }
     }
-    return h.prim >= 0;
+    return h;
 }
 
 // ---------------------------------------------------------------------------------
@@ -417,63 +459,12 @@ __device__ __forceinline__ int stage_nodes(const PassArgs& A, const Node*& s_nod
     return cnt;
 }
 
-// ---------------------------------------------------------------------------------
-// extend: closest hit of every queued ray (shared once per coincident pair)
-// ---------------------------------------------------------------------------------
 // adds a warp's traversal counts to stats[2*cls], stats[2*cls+1]; all lanes must call
 __device__ __forceinline__ void flush_counts(const PassArgs& A, int cls, const TravCount& tc) {
     const unsigned nsum = __reduce_add_sync(FULL, tc.nodes), psum = __reduce_add_sync(FULL, tc.prims);
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(A.stats + 2 * cls, (unsigned long long)nsum);
         atomicAdd(A.stats + 2 * cls + 1, (unsigned long long)psum);
-    }
-}
-
-// closest hit of path-queue entry j of depth `depth` (once per coincident pair)
-template <int NB, bool STATS>
-// Continuation item j: branch bsel only (an FD pair's two branches in two lanes), or every
-// branch in turn (bsel = -1).
-__device__ __forceinline__ void extend_item(const PassArgs& A, const Node* s_nodes, int n_staged, int depth, int64_t j,
-                                            int bsel, TravCount& tc) {
-    const bool first = depth == 1;
-    const int qi = depth & 1;
-    uint32_t flags;
-    int q;
-    v3 o[NB], d[NB];
-    if (first) {
-        if (NB == 2 && bsel == 1) return;   // both branches start on the same camera ray
-        const PathId id = decode_path(A, j);
-        q = id.q;
-        const ProblemDev& P = A.probs[q];
-        flags = (NB == 2) ? (FLAG_A | FLAG_B | FLAG_COINC) : FLAG_A;
-        if (A.fd_kind && A.iter_override < 0 && A.pstate[q].iteration == 0) flags = 0;
-        const uint4 r = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, 0, 0);
-        camera_ray(P, id.pixel, u01(r.x), u01(r.y), o[0], d[0]);
-        if (NB == 2) { o[NB - 1] = o[0]; d[NB - 1] = d[0]; }
-    } else {
-        flags = A.qu[qi][QU_FLAGS * A.qcap + j];
-        q = (flags >> 8) & 0xff;
-        if (bsel >= 0 && (!(flags & (1u << bsel)) || (bsel == 1 && (flags & FLAG_COINC)))) return;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            if (bsel >= 0 && b != bsel) continue;
-            const float* f = A.qf[qi] + (size_t)(b * QF_PER_BRANCH) * A.qcap + j;
-            o[b] = mk(f[(QF_O + 0) * A.qcap], f[(QF_O + 1) * A.qcap], f[(QF_O + 2) * A.qcap]);
-            d[b] = mk(f[(QF_D + 0) * A.qcap], f[(QF_D + 1) * A.qcap], f[(QF_D + 2) * A.qcap]);
-        }
-    }
-    const ProblemDev& P = A.probs[q];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        if (bsel >= 0 && b != bsel) continue;
-        if (!(flags & (1u << b))) continue;
-        if (b == 1 && (flags & FLAG_COINC)) continue;
-        Hit h;
-        traverse<false, STATS>(P, s_nodes, q == A.smem_prob ? n_staged : 0, o[b], d[b], INFINITY, h, tc);
-        A.hitf[(size_t)(b * HF_PER_BRANCH + HF_T) * A.qcap + j] = h.t;
-        A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B1) * A.qcap + j] = h.b1;
-        A.hitf[(size_t)(b * HF_PER_BRANCH + HF_B2) * A.qcap + j] = h.b2;
-        A.hitp[(size_t)b * A.qcap + j] = h.prim;
     }
 }
 
@@ -628,7 +619,7 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
         // and densities, and evaluates only its own integrand along them
         const bool shared = NB == 2 && P.fd_shared != 0;
         float pbN0 = 0.0f, pbC0 = 0.0f;
-        v3 wiC0 = mk(0, 0, 0);
+        v3 wiC0 = mk(0, 0, 0), hC0 = mk(0, 0, 1);
         bool okC0 = false;
         if (any_alive) {
             const uint4 r0 = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, (uint32_t)depth, 0);
@@ -665,8 +656,9 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
                 contrib[b] = mk(0, 0, 0);
                 if (ls[b].ok) {
                     float df[MAXC][3];
-                    const v3 f = wg ? bsdf_f_grad(m, nf, wo, ls[b].wi, df) : bsdf_f(m, nf, wo, ls[b].wi);
-                    const float pb = (shared && b == 1) ? pbN0 : bsdf_pdf(m, nf, wo, ls[b].wi);
+                    const v3 hl = half_vec(wo, ls[b].wi);
+                    const v3 f = wg ? bsdf_f_grad(m, nf, wo, ls[b].wi, hl, df) : bsdf_f(m, nf, wo, ls[b].wi, hl);
+                    const float pb = (shared && b == 1) ? pbN0 : bsdf_pdf(m, nf, wo, ls[b].wi, hl);
                     if (b == 0) pbN0 = pb;
                     const float qn = dot(ls[b].wi, nf) * mis2(ls[b].pdf, pb) / ls[b].pdf;
                     contrib[b] = mk(beta[b].x * f.x * ls[b].le.x, beta[b].y * f.y * ls[b].le.y,
@@ -691,17 +683,19 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
                     wi = wiC0;
                     ok = okC0;
                     pb = pbC0;
-                    if (ok) f = wg ? bsdf_f_grad(m, nf, wo, wi, df) : bsdf_f(m, nf, wo, wi);
+                    if (ok) f = wg ? bsdf_f_grad(m, nf, wo, wi, hC0, df) : bsdf_f(m, nf, wo, wi, hC0);
                 } else {
-                    ok = bsdf_sample(m, nf, wo, u01(r1.x), u01(r1.y), u01(r1.z), wi);
+                    v3 hs;
+                    ok = bsdf_sample(m, nf, wo, u01(r1.x), u01(r1.y), u01(r1.z), wi, hs);
                     if (ok) {
-                        f = wg ? bsdf_f_grad(m, nf, wo, wi, df) : bsdf_f(m, nf, wo, wi);
-                        pb = bsdf_pdf(m, nf, wo, wi);
+                        f = wg ? bsdf_f_grad(m, nf, wo, wi, hs, df) : bsdf_f(m, nf, wo, wi, hs);
+                        pb = bsdf_pdf(m, nf, wo, wi, hs);
                         ok = pb > 0.0f;
                     }
                     if (b == 0) {
                         okC0 = ok;
                         wiC0 = wi;
+                        hC0 = hs;
                         pbC0 = pb;
                     }
                 }
@@ -886,22 +880,89 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
     }
 }
 
-// any-hit of shadow entry j; if the light is visible, add the NEE radiance to the path's
-// accumulator and (replay) the NEE part of the gradient to its record
+// ---------------------------------------------------------------------------------
+// trace: one launch consumes two independent queues that shade(depth_ext - 1) produced —
+// the continuation rays of depth depth_ext (closest hit) and the NEE shadow rays of depth
+// depth_sh = depth_ext - 1 (any hit). The first launch of a pass has no shadow rays; the
+// last one has no continuation rays.
+//
+// A work unit is one ray: units [0, n_eu) are continuation rays (NB = 2: entry u >> 1, branch
+// u & 1, so an FD pair's two rays take two lanes), units [n_eu, n_eu + n_sh) the shadow rays.
+// Units are fetched dynamically (persistent threads with dynamic ray fetching, after Aila and
+// Laine 2009): every lane keeps its own walk, and whenever TRACE_REFILL or more lanes of a warp
+// are idle, those lanes take the next units from the launch's fetch counter (one atomic per warp),
+// so a warp does not wait for its slowest ray while units remain.
+// ---------------------------------------------------------------------------------
+constexpr int TRACE_REFILL = 8;
+
+struct Unit {
+    int64_t j;   // queue entry
+    int b;       // branch of a continuation ray; -1: shadow ray
+    int q;       // problem
+};
+
+// starts unit u's walk; false if the unit traces nothing (a branch that ended, a problem without
+// FD samples at iteration 0, or the second branch of a coincident pair, whose hit the first
+// branch's unit writes)
+template <int NB>
+__device__ __forceinline__ bool unit_setup(const PassArgs& A, int depth_ext, int64_t u, int64_t n_eu, Unit& U,
+                                           TravRay& R) {
+    v3 o, d;
+    if (u < n_eu) {
+        U.j = NB == 2 ? (u >> 1) : u;
+        U.b = NB == 2 ? (int)(u & 1) : 0;
+        if (depth_ext == 1) {
+            if (U.b == 1) return false;   // both branches start on the same camera ray
+            const PathId id = decode_path(A, U.j);
+            U.q = id.q;
+            if (A.fd_kind && A.iter_override < 0 && A.pstate[U.q].iteration == 0) return false;
+            const ProblemDev& P = A.probs[U.q];
+            const uint4 r = draw(P.seed, P.key_id, id.pixel, id.sample, id.iter, A.stream, 0, 0);
+            camera_ray(P, id.pixel, u01(r.x), u01(r.y), o, d);
+        } else {
+            const int qi = depth_ext & 1;
+            const uint32_t flags = A.qu[qi][QU_FLAGS * A.qcap + U.j];
+            if (!(flags & (1u << U.b)) || (U.b == 1 && (flags & FLAG_COINC))) return false;
+            U.q = (flags >> 8) & 0xff;
+            const float* f = A.qf[qi] + (size_t)(U.b * QF_PER_BRANCH) * A.qcap + U.j;
+            o = mk(f[(QF_O + 0) * A.qcap], f[(QF_O + 1) * A.qcap], f[(QF_O + 2) * A.qcap]);
+            d = mk(f[(QF_D + 0) * A.qcap], f[(QF_D + 1) * A.qcap], f[(QF_D + 2) * A.qcap]);
+        }
+        trav_begin(R, o, d, INFINITY, false, A.probs[U.q].nodes != nullptr);
+    } else {
+        U.j = u - n_eu;
+        U.b = -1;
+        const size_t C = (size_t)A.shcap;
+        const float* F = A.shf;
+        o = mk(F[(SF_O + 0) * C + U.j], F[(SF_O + 1) * C + U.j], F[(SF_O + 2) * C + U.j]);
+        d = mk(F[(SF_D + 0) * C + U.j], F[(SF_D + 1) * C + U.j], F[(SF_D + 2) * C + U.j]);
+        U.q = A.shu[SU_META * C + U.j] & 0xff;
+        trav_begin(R, o, d, F[SF_TMAX * C + U.j], true, A.probs[U.q].nodes != nullptr);
+    }
+    return true;
+}
+
+// the walk of unit U has finished: a continuation ray writes its closest hit; a shadow ray whose
+// light is visible adds the NEE radiance to its path's accumulator and (replay) the NEE part of the
+// gradient to its record; a radiance pass with a hit store also keeps the visibility for its replay
 template <int NB, int MODE, bool STATS>
-__device__ __forceinline__ void shadow_item(const PassArgs& A, const Node* s_nodes, int n_staged, int64_t j, int depth_sh,
+__device__ __forceinline__ void unit_finish(const PassArgs& A, int depth_sh, const Unit& U, TravRay& R,
                                             TravCount& tc) {
+    const Hit h = trav_end<STATS>(A.probs[U.q], R, tc);
+    if (!R.complete) set_err(A, MER_ERR_BOUNDS);
+    if (U.b >= 0) {
+        A.hitf[(size_t)(U.b * HF_PER_BRANCH + HF_T) * A.qcap + U.j] = h.t;
+        A.hitf[(size_t)(U.b * HF_PER_BRANCH + HF_B1) * A.qcap + U.j] = h.b1;
+        A.hitf[(size_t)(U.b * HF_PER_BRANCH + HF_B2) * A.qcap + U.j] = h.b2;
+        A.hitp[(size_t)U.b * A.qcap + U.j] = h.prim;
+        return;
+    }
     const size_t C = (size_t)A.shcap;
     const float* F = A.shf;
-    const v3 o = mk(F[(SF_O + 0) * C + j], F[(SF_O + 1) * C + j], F[(SF_O + 2) * C + j]);
-    const v3 d = mk(F[(SF_D + 0) * C + j], F[(SF_D + 1) * C + j], F[(SF_D + 2) * C + j]);
-    const float tmax = F[SF_TMAX * C + j];
+    const int64_t j = U.j;
     const uint32_t g = A.shu[SU_PATH * C + j];
-    const uint32_t meta = A.shu[SU_META * C + j];
-    const int q = meta & 0xff;
-    const uint32_t mask = (meta >> 8) & 3u;
-    Hit h;
-    const bool occluded = traverse<true, STATS>(A.probs[q], s_nodes, q == A.smem_prob ? n_staged : 0, o, d, tmax, h, tc);
+    const uint32_t mask = (A.shu[SU_META * C + j] >> 8) & 3u;
+    const bool occluded = h.prim >= 0;
     if (MODE != MODE_REPLAY && A.hs) {   // ADJ_FWD: keep the visibility for the replay, by path
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -924,40 +985,46 @@ __device__ __forceinline__ void shadow_item(const PassArgs& A, const Node* s_nod
     }
 }
 
-// ---------------------------------------------------------------------------------
-// trace: one launch consumes two independent queues that shade(depth_ext - 1) produced —
-// the continuation rays of depth depth_ext (closest hit) and the NEE shadow rays of depth
-// depth_sh = depth_ext - 1 (any hit). The first launch of a pass has no shadow rays; the
-// last one has no continuation rays.
-// ---------------------------------------------------------------------------------
 template <int NB, int MODE, bool STATS>
-__global__ void __launch_bounds__(256) k_trace(PassArgs A, int depth_ext, int depth_sh) {
+__global__ void __launch_bounds__(256, NB == 1 ? 4 : 3) k_trace(PassArgs A, int depth_ext, int depth_sh) {
     const Node* s_nodes;
     const int n_staged = stage_nodes(A, s_nodes);
     const int64_t n_ext = depth_ext == 1 ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth_ext], A.qcap);
     const int64_t n_sh = depth_sh > 0 ? min((int64_t)A.cnt[CNT_S + depth_sh], A.shcap) : 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // a launch whose lanes all fit in one pass of the resident grid is bound by the latency of
-    // its slowest item: an FD pair's two continuation rays then take two lanes; with more work
-    // than lanes, one lane traces both (fewer idle lanes, one read of the pair's state)
-    const bool split = NB == 2 && 2 * n_ext + n_sh <= stride;
-    const int64_t n_ext_lanes = split ? 2 * n_ext : n_ext;
-    const int64_t n = n_ext_lanes + n_sh;
-    TravCount tc_e, tc_s;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        if (j < n_ext_lanes) {
-            if (split) extend_item<NB, STATS>(A, s_nodes, n_staged, depth_ext, j >> 1, (int)(j & 1), tc_e);
-            else extend_item<NB, STATS>(A, s_nodes, n_staged, depth_ext, j, NB == 2 ? -1 : 0, tc_e);
-        } else {
-            shadow_item<NB, MODE, STATS>(A, s_nodes, n_staged, j - n_ext_lanes, depth_sh, tc_s);
+    const int64_t n_eu = NB == 2 ? 2 * n_ext : n_ext;
+    const int64_t n = n_eu + n_sh;
+    uint32_t* fetch = A.cnt + CNT_FETCH + depth_ext;   // zeroed with the pass counters
+    const unsigned lane = threadIdx.x & 31u;
+    int stack[TRAV_STACK];
+    TravRay R;
+    Unit U{0, 0, 0};
+    TravCount tc;
+    bool busy = false, more = n > 0;
+    while (true) {
+        const unsigned idle = __ballot_sync(FULL, !busy);
+        if (more && __popc(idle) >= TRACE_REFILL) {
+            const unsigned cnt = (unsigned)__popc(idle);
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(fetch, cnt);
+            base = __shfl_sync(FULL, base, 0);
+            if ((int64_t)base + cnt >= n) more = false;
+            if (!busy) {
+                const int64_t u = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
+                if (u < n) busy = unit_setup<NB>(A, depth_ext, u, n_eu, U, R);
+            }
+        }
+        if (!__any_sync(FULL, busy)) {
+            if (!more) break;
+            continue;
+        }
+        if (busy && trav_step<STATS>(A.probs[U.q], s_nodes, U.q == A.smem_prob ? n_staged : 0, R, stack, tc)) {
+            unit_finish<NB, MODE, STATS>(A, depth_sh, U, R, tc);
+            busy = false;
         }
     }
     if (STATS) {
         const int cls = (NB == 1 ? KC_TRACE1_PRIMAL : KC_TRACE2_PRIMAL) + (MODE == MODE_REPLAY ? 1 : 0);
-        TravCount t;
-        t.nodes = tc_e.nodes + tc_s.nodes;
-        t.prims = tc_e.prims + tc_s.prims;
-        flush_counts(A, cls, t);
+        flush_counts(A, cls, tc);
     }
 }
 

@@ -7,12 +7,13 @@ namespace mer {
 
 enum PassMode : int { MODE_PRIMAL = 0, MODE_ADJ_FWD = 1, MODE_REPLAY = 2 };
 
-// counter block layout (u32), zeroed at the start of every pass
+// counter block layout (u32); words [0, CNT_ERR) are zeroed at the start of every pass
 constexpr int CNT_Q = 0;       // [k]: entries of the path queue consumed at depth k
 constexpr int CNT_S = 32;      // [k]: shadow entries produced at depth k
 constexpr int CNT_R = 64;      // records produced by the pass
-constexpr int CNT_ERR = 65;    // first error code seen by a kernel (bounds)
-constexpr int CNT_WORDS = 72;
+constexpr int CNT_FETCH = 65;  // [k]: work units taken by the trace launch of depth k (k <= 17)
+constexpr int CNT_ERR = 95;    // first error code seen by a kernel (bounds, waits), kept across passes
+constexpr int CNT_WORDS = 96;
 
 // path-queue fields (float), per branch b: base index b * QF_PER_BRANCH
 constexpr int QF_O = 0, QF_D = 3, QF_BETA = 6, QF_PDFB = 9, QF_PDFENV = 10, QF_PER_BRANCH = 11;

@@ -1,7 +1,9 @@
 """The host BVH builder (binned SAH, collapsed to four-wide nodes) checked on the CPU with a small
 C++ program linked against it: the leaf order is a permutation of the triangles, every child box
 of the binary and of the four-wide tree contains its subtree's triangles, the four-wide leaves
-cover every triangle exactly once (a one-triangle scene's root holds it twice), and a stack traversal of the four-wide tree finds the same
+cover every triangle exactly once (a one-triangle scene's root holds it twice), the reported number of
+inner levels (which bounds the traversal stack) equals the depth found by recursion, and a stack
+traversal of the four-wide tree finds the same
 closest hit as brute force for random rays. Inputs: a small spiral and a small displaced sphere
 (the synthetic scenes), and degenerate sets (one triangle, many identical triangles, a flat grid
 whose boxes have zero thickness, long thin triangles). On the synthetic meshes the tree's SAH cost
@@ -121,6 +123,13 @@ int main() {
         }
     };
     if (!w.empty()) check4(0);
+    // inner levels of the deepest path (the traversal stack bound) by recursion
+    std::function<int(int)> levels = [&](int i) -> int {
+        int m = 0;
+        for (int c = 0; c < 4; ++c) if (w[i].child[c] >= 0 && w[i].child[c] != kEmptyChild) m = std::max(m, levels(w[i].child[c]));
+        return 1 + m;
+    };
+    if (bvh4_levels(w) != (w.empty() ? 0 : levels(0))) { printf("FAIL levels\n"); return 1; }
     // exactly once (a one-triangle scene's root references its triangle from both children)
     for (int k = 0; k < nt; ++k) if (nt == 1 ? cover[k] < 1 : cover[k] != 1) ++bad;
     if (bad) { printf("FAIL four-wide %d\n", bad); return 1; }
