@@ -180,12 +180,12 @@ __device__ __forceinline__ float proc_grp(Grp& g, const UpdSeg& S, const Coef& k
     float out[4];
     float acc = 0.0f;
     const int C = S.C;
-    const int c0 = (int)((uint32_t)(v * 4) % (uint32_t)C);
+    // channel of the group's first element (32-bit modulo while the index fits in 32 bits)
+    const int c0 = (v * 4 < ((int64_t)1 << 32)) ? (int)((uint32_t)(v * 4) % (uint32_t)C) : (int)((v * 4) % C);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         int c = c0 + l;
-        if (c >= C) c -= C;
-        if (c >= C) c -= C;
+        while (c >= C) c -= C;   // C = 1 wraps up to three times
         float st;
         if (meta)
             st = meta_elem(S.hyper, k, pv[l], Fv[l], dFv[l], m2fv[l], m2dv[l], meanv[l], varv[l], apv[l], S.lo[c],

@@ -71,7 +71,8 @@ def _rand_state(rng, n, iteration):
 
 @pytest.mark.parametrize("n,C,iteration,n2,mode", [
     (4099, 3, 0, 0.0, "meta"), (4099, 3, 5, 2.5e-5, "meta"), (50001, 5, 7, 0.0, "meta"),
-    (50001, 5, 3, 1e-3, "meta"), (17, 5, 1, 4e-6, "meta"), (4099, 3, 0, 0.0, "adam"), (50001, 5, 9, 0.0, "adam")])
+    (50001, 5, 3, 1e-3, "meta"), (17, 5, 1, 4e-6, "meta"), (4099, 3, 0, 0.0, "adam"), (50001, 5, 9, 0.0, "adam"),
+    (2048, 1, 3, 1e-3, "meta"), (2048, 1, 0, 0.0, "adam"), (4099, 2, 5, 2.5e-5, "meta"), (4098, 4, 2, 0.0, "adam")])
 def test_update_matches_oracle(torch_mod, n, C, iteration, n2, mode):
     torch = torch_mod
     from paper_2309_15676_gb300.api import HyperParams, MODE_ADAM, MODE_META, meta_step_raw
@@ -157,6 +158,39 @@ def _sample_parity(ctx, pid, scene, tex, spp, stream, iteration, max_ref=None, s
     return ok.mean(), len(idx)
 
 
+def _sample_parity_pooled(ctx, pid, scene, tex, spp, stream, iteration, n_ref, seed=0):
+    """_sample_parity on n_ref randomly chosen paths, the oracle's side run in one process per host
+    core (full-size scenes). Returns the fraction of paths within tolerance, the fraction once the
+    paths that FP32 arithmetic cannot resolve are set aside, the count, and the worst paths
+    (index, GPU value, oracle value) for the assertion message.
+
+    A path outside the tolerance is set aside when the oracle's own algorithm, evaluated in single
+    precision (orc.render_samples_f32), is outside the tolerance of its FP64 evaluation on that path
+    too: its radiance depends on FP32 rounding beyond 1e-4 (grazing glossy bounces, whose direction
+    amplifies the last-bit differences of the ray and texture coordinates). Every path, set aside or
+    not, must stay within 1e-2."""
+    from .oracle_pool import OraclePool
+    got = ctx.render_samples(pid, tex, spp=spp, stream=stream, iteration=iteration).cpu().numpy()
+    npix = scene["width"] * scene["height"]
+    got = got.reshape(spp * npix, 3)
+    n_ref = min(n_ref, spp * npix)
+    idx = np.sort(np.random.default_rng(seed).choice(spp * npix, n_ref, replace=False))
+    pixels, samples = idx % npix, idx // npix
+    with OraclePool(scene, tex) as op:
+        ref = op.render_samples(pixels, samples, iteration, stream)
+    tol = lambda r: 1e-4 * np.abs(r) + 1e-6
+    err = np.abs(got[idx] - ref) - tol(ref)
+    ok = np.all(err <= 0, axis=1)
+    assert np.all(np.abs(got[idx] - ref) <= 1e-2 * np.abs(ref) + 1e-6), "a path differs by more than 1e-2"
+    bad = np.where(~ok)[0]
+    explained = np.zeros(len(bad), bool)
+    if len(bad):
+        r32 = orc.render_samples_f32(orc.Scene(scene), tex, pixels[bad], samples[bad], iteration, stream)
+        explained = np.any(np.abs(r32 - ref[bad]) > tol(ref[bad]), axis=1)
+    worst = [(int(idx[k]), got[idx[k]].tolist(), ref[k].tolist(), bool(e)) for k, e in zip(bad[:6], explained[:6])]
+    return ok.mean(), 1.0 - float((~explained).sum()) / len(idx), len(idx), worst
+
+
 def test_radiance_box(torch_mod):
     w = synth.workload_box(64, 64, 32, max_depth=3)
     ctx, pid = _ctx(torch_mod, w.scene)
@@ -174,11 +208,12 @@ def test_radiance_spiral_small(torch_mod):
 
 
 def test_radiance_spiral_full_size_sampled(torch_mod):
-    """256x256, 8192 triangles, 5-channel 256^2 textures, depth 5: 3000 sampled paths."""
+    """256x256, 8192 triangles, 5-channel 256^2 textures, depth 5, 2 spp: 30,000 sampled paths (so
+    that the 99.99% bar allows at most 3 paths outside the tolerance)."""
     w = synth.workload_spiral()
     ctx, pid = _ctx(torch_mod, w.scene)
-    frac, n = _sample_parity(ctx, pid, w.scene, w.init_tex, 2, 0, 11, max_ref=3000)
-    assert frac >= 0.999, (frac, n)
+    frac, frac_resolved, n, worst = _sample_parity_pooled(ctx, pid, w.scene, w.init_tex, 2, 0, 11, 30000)
+    assert frac >= 0.9999, (frac, frac_resolved, n, worst)
     ctx.close()
 
 
@@ -286,14 +321,24 @@ def test_iteration_matches_oracle(torch_mod):
         # update on identical inputs (the GPU's F, dF and state)
         ost = meta.MetaState(pre["m2f"], pre["m2d"], pre["mean"], pre["var"], pre["alpha_prev"],
                              stats_pre["count_f"], stats_pre["count_d"], it)
-        ref_pi, ref_n2, _ = meta.meta_update(pre["pi_cur"], F, dF, ost, H, stats_pre["dpi_norm2"],
-                                             lo[None, None, :], hi[None, None, :])
+        n2 = stats_pre["dpi_norm2"]
+        ref_pi, ref_n2, _ = meta.meta_update(pre["pi_cur"], F, dF, ost, H, n2, lo[None, None, :], hi[None, None, :])
         ctx.update_step()
-        got_pi = ctx.get_params(pid).cpu().numpy().astype(np.float64)
-        step_ref = ref_pi - pre["pi_cur"]
-        err = np.abs((got_pi - pre["pi_cur"]) - step_ref)
-        assert np.all(err <= 1e-4 * np.abs(step_ref) + 1e-4 * H.lr), (it, err.max())
-        assert abs(ctx.stats(pid)["dpi_norm2"] - ref_n2) <= 1e-4 * ref_n2
+        post = {k: v.cpu().numpy().astype(np.float64) for k, v in ctx.state(pid).items()}
+        # the update on identical inputs within 1e-5 of the magnitude of its terms, as for the
+        # standalone entry point: Moment2 and variance outputs relative, the meta-estimate against
+        # |mean_prev + dF| + |F|, the step against lr times that over (sqrt(var) + eps)
+        assert np.allclose(post["m2f"], ost.m2f, rtol=1e-5, atol=0), it
+        assert np.allclose(post["m2d"], ost.m2d, rtol=1e-5, atol=0), it
+        assert np.allclose(post["var"], ost.var, rtol=1e-5, atol=0), it
+        dfu = dF if (it >= 1 and n2 > 0) else 0.0
+        scale_mean = np.abs(pre["mean"] + dfu) + np.abs(F)
+        assert np.all(np.abs(post["mean"] - ost.mean) <= 1e-5 * scale_mean + 1e-30), it
+        assert np.all(np.abs(post["alpha_prev"] - ost.alpha_prev) <= 1e-5 * np.abs(ost.alpha_prev) + 1e-7), it
+        step_scale = H.lr * scale_mean / (np.sqrt(ost.var) + H.eps)
+        err = np.abs(post["pi_cur"] - ref_pi)
+        assert np.all(err <= 1e-5 * step_scale + 2 ** -23 * np.abs(pre["pi_cur"]) + 1e-12), (it, err.max())
+        assert abs(ctx.stats(pid)["dpi_norm2"] - ref_n2) <= 1e-5 * ref_n2 + 1e-12 * F.size, it
     ctx.close()
 
 
