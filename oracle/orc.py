@@ -77,6 +77,22 @@ def lib():
     return _lib
 
 
+_lib32 = None
+
+
+def lib32():
+    """The oracle's source built in single precision (oracle_f32.c): only the per-sample radiance,
+    for telling paths that FP32 arithmetic cannot resolve to the parity tolerance."""
+    global _lib32
+    if _lib32 is None:
+        L = ct.CDLL(_build.build_f32())
+        f32p = ct.POINTER(ct.c_float)
+        L.orc_render_samples.argtypes = [ct.POINTER(OrcScene), f32p, ct.c_int64, _u32p, _u32p, ct.c_uint32,
+                                         ct.c_uint32, f32p]
+        _lib32 = L
+    return _lib32
+
+
 def _p(a, t):
     return a.ctypes.data_as(t)
 
@@ -166,6 +182,18 @@ def render_samples(sc: Scene, tex, pixels, samples, iteration, stream):
     lib().orc_render_samples(sc.ref(), _p(t, _f64p), len(pixels), _p(pixels, _u32p), _p(samples, _u32p),
                              iteration, stream, _p(out, _f64p))
     return out
+
+
+def render_samples_f32(sc: Scene, tex, pixels, samples, iteration, stream):
+    """render_samples evaluated by the single-precision build (never a reference value)."""
+    pixels = np.ascontiguousarray(pixels, np.uint32)
+    samples = np.ascontiguousarray(samples, np.uint32)
+    out = np.zeros((len(pixels), 3), np.float32)
+    t = np.ascontiguousarray(np.asarray(tex, np.float32))
+    f32p = ct.POINTER(ct.c_float)
+    lib32().orc_render_samples(sc.ref(), t.ctypes.data_as(f32p), len(pixels), _p(pixels, _u32p), _p(samples, _u32p),
+                               iteration, stream, out.ctypes.data_as(f32p))
+    return out.astype(np.float64)
 
 
 def render_image(sc: Scene, tex, spp, iteration, stream):

@@ -4,11 +4,15 @@ configuration the benchmark uses, on outputs the oracle computes one by one:
   of the 1024^2 / 204,800-triangle displaced sphere (depth 8, 2048^2 x 5 textures);
 - full-size adjoints whose loss adjoint is non-zero only at a few hundred randomly chosen pixels,
   against the oracle's per-path replay of exactly those samples (image-summed gradient tolerance);
-- the 64-problem batch (images, meshes, textures and depths of uneven sizes, images shrunk 4x):
-  sampled radiance of several problems inside the batched context, and their gradient step in the
-  batch against each problem alone.
-Tolerances as elsewhere: >= 99.9% of sampled radiances within 1e-4 relative (floor 1e-6), relative
-L2 of image-summed gradients below 1e-3."""
+- the 64-problem batch at its full size (images up to 512^2, meshes up to 50k triangles, textures
+  up to 512^2 x 5, depths 3-8): sampled radiance of several problems inside the batched context, and
+  their gradient step in the batch against each problem alone.
+Tolerances as elsewhere: >= 99.99% of sampled radiances within 1e-4 relative (floor 1e-6), on
+30,000 sampled paths per workload so that the bar allows at most 3 paths outside it (the oracle's
+side runs in one process per host core); relative L2 of image-summed gradients below 1e-3. On the
+depth-8 glossy workloads a few paths in 10^4 cannot be resolved to 1e-4 in FP32 at all (the
+oracle's own algorithm evaluated in FP32 misses them as well): there the 99.99% bar applies to the
+paths FP32 resolves, at least 99.9% of all paths must be within 1e-4, and every path within 1e-2."""
 import numpy as np
 import pytest
 
@@ -16,7 +20,7 @@ from oracle import orc
 from paper_2309_15676_gb300 import synth
 
 from .gpu_common import need_gpu, rel_l2
-from .test_gpu_parity import _grad_check, _sample_parity
+from .test_gpu_parity import _grad_check, _sample_parity_pooled
 
 pytestmark = pytest.mark.gpu
 
@@ -32,10 +36,11 @@ def test_full_size_radiance_sampled(which):
     need_gpu()
     w = synth.workload_spiral(512, 512, 512, 32, 1024, max_depth=8) if which == "spiral512" else synth.workload_sphere()
     ctx, pid = _ctx(w.scene)
-    frac, n = _sample_parity(ctx, pid, w.scene, w.init_tex, 1, 0, 11, max_ref=1500 if which == "dsphere1024" else 2000,
-                             seed=5)
+    frac, frac_resolved, n, worst = _sample_parity_pooled(ctx, pid, w.scene, w.init_tex, 1, 0, 11, 30000, seed=5)
     ctx.close()
-    assert frac >= 0.999, (which, frac, n)
+    # spiral512 (depth 8, glossy): about 2 in 10^4 paths depend on FP32 rounding beyond 1e-4 (the
+    # oracle's own FP32 evaluation misses them too); the bar holds for the paths FP32 resolves
+    assert frac >= 0.999 and frac_resolved >= 0.9999, (which, frac, frac_resolved, n, worst)
 
 
 @pytest.mark.parametrize("which,npix,spp", [("spiral256", 300, 2), ("dsphere1024", 100, 1)])
@@ -61,9 +66,12 @@ def test_full_size_adjoint_sparse_loss(which, npix, spp):
 
 
 def test_batch_of_64_problems():
+    """The fourth configuration at its full size: 64 problems in one context, sampled radiance of
+    four problems of different kinds (7,500 paths each) inside the batched context, and the batched
+    gradient step of three problems against each problem alone."""
     need_gpu()
     from paper_2309_15676_gb300.api import Context, HyperParams
-    ws = synth.workload_batch(64, seed=4, scale=0.25)
+    ws = synth.workload_batch(64, seed=4)
     ctx = Context(0, max_paths=1 << 20)
     ids = []
     rng = np.random.default_rng(23)
@@ -75,10 +83,16 @@ def test_batch_of_64_problems():
         ctx.set_params(p, w.init_tex)
         ids.append(p)
         targets.append(t)
-    # sampled radiance of a few problems of different kinds inside the batched context
+    ok, ok_resolved, n = 0.0, 0.0, 0
     for q in (0, 17, 40, 63):
-        frac, n = _sample_parity(ctx, ids[q], ws[q].scene, ws[q].init_tex, 1, 0, 5, max_ref=300, seed=q)
-        assert frac >= 0.999, (q, frac, n)
+        npix = ws[q].scene["width"] * ws[q].scene["height"]
+        spp = -(-7500 // npix)                     # small images: several samples per pixel
+        f, fr, m, worst = _sample_parity_pooled(ctx, ids[q], ws[q].scene, ws[q].init_tex, spp, 0, 5, 7500, seed=q)
+        assert f >= 0.999, (q, f, fr, m, worst)   # no single problem far off
+        ok += f * m
+        ok_resolved += fr * m
+        n += m
+    assert ok / n >= 0.999 and ok_resolved / n >= 0.9999, (ok / n, ok_resolved / n, n)
     # the batched gradient step equals each problem alone
     ctx.iterate(1, use_graph=True)
     ctx.gradient_step()

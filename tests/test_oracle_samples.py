@@ -102,3 +102,21 @@ def test_volume_sample_of_an_empty_volume_is_the_background(oracle_lib):
     L = orc.vol_render_samples(vol, p, pix, pix * 7, 9, 2)
     bg = np.float32([0.2, 0.3, 0.4]).astype(np.float64)
     assert np.array_equal(L, np.tile(bg, (40, 1)))
+
+
+def test_single_precision_build_is_the_same_algorithm_in_fp32():
+    """The oracle's source built in single precision (used only to tell which paths FP32 arithmetic
+    cannot resolve to the parity tolerance) computes the same radiance as the FP64 build up to FP32
+    rounding: nearly every path within 1e-4 relative, all within 1e-2, and not bit-identical (so the
+    narrowing took effect)."""
+    w = synth.workload_spiral(24, 20, 32, 8, 16, max_depth=4)
+    sc = orc.Scene(w.scene)
+    n = 24 * 20 * 2
+    pix = np.arange(n, dtype=np.uint32) % (24 * 20)
+    smp = (np.arange(n) // (24 * 20)).astype(np.uint32)
+    r64 = orc.render_samples(sc, w.init_tex, pix, smp, 3, 0)
+    r32 = orc.render_samples_f32(sc, w.init_tex, pix, smp, 3, 0)
+    close = np.all(np.abs(r32 - r64) <= 1e-4 * np.abs(r64) + 1e-6, axis=1)
+    assert close.mean() >= 0.99
+    assert np.all(np.abs(r32 - r64) <= 1e-2 * np.abs(r64) + 1e-6)
+    assert np.any(r32 != r64)
