@@ -78,6 +78,8 @@ def parse(argv=None):
     ap.add_argument("--no-volume", action="store_true", help="skip the 256^3 volume leg")
     ap.add_argument("--only-volume", action="store_true", help="run only the volume leg (for profiling)")
     ap.add_argument("--detail-out", default=None, help="also write every side measurement to this JSON file")
+    ap.add_argument("--diagnose", action="store_true",
+                    help="add the meta-estimator vs Adam study (free and pinned metal/roughness, beta_D sweep)")
     return ap.parse_args(argv)
 
 
@@ -308,52 +310,12 @@ def l2_flush(torch, buf):
     buf.zero_()            # 256 MiB > the 129 MB L2
 
 
-def eval_loss(torch, ctx, pid, target, spp=64):
-    img = ctx.render(pid, None, spp=spp, stream=5, iteration=0)
-    return float(((img - target) ** 2).mean())
-
-
 def optimise_run(torch, w, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags=0, precond_lambda=0.0):
-    """One optimisation run: iterations and GPU time (iterations only, evaluation excluded) until
-    the 64-spp eval loss drops below `frac` of its initial value (and below 10% of it); evaluated
-    every 2 iterations for the first 50, then every 10."""
-    from paper_2309_15676_gb300.api import Context, HyperParams
-    sc = dict(w.scene)
-    sc["spp_prop"], sc["spp_fd"] = spp_prop, spp_fd
-    ctx = Context(0)
-    pid = ctx.add_scene(sc, HyperParams(mode=mode, lr=lr, flags=flags, precond_lambda=precond_lambda))
-    ctx.set_target(pid, target_img)
-    ctx.set_params(pid, w.init_tex)
-    # capture the iteration graph (and initialise any library it calls) outside the timed region:
-    # one iteration, then rewind the state
-    blob = ctx.checkpoint_save()
-    ctx.iterate(1, use_graph=True)
-    ctx.checkpoint_load(blob)
-    torch.cuda.synchronize()
-    l0 = eval_loss(torch, ctx, pid, target_img)
-    thr = frac * l0
-    gpu_ms, it, reached, reached_ms, last, lmin = 0.0, 0, None, None, l0, l0
-    r10, r10_ms = None, None
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    while it < max_iters:
-        k = 2 if it < 50 else 10
-        e0.record()
-        ctx.iterate(k, use_graph=True)
-        e1.record()
-        e1.synchronize()
-        gpu_ms += e0.elapsed_time(e1)
-        it += k
-        last = eval_loss(torch, ctx, pid, target_img)
-        lmin = min(lmin, last)
-        if reached is None and last <= thr:
-            reached, reached_ms = it, gpu_ms
-        if r10 is None and last <= 0.1 * l0:
-            r10, r10_ms = it, gpu_ms
-    ctx.close()
-    return {"lr": lr, "iters": reached, "gpu_s": reached_ms / 1e3 if reached else None, "loss0": l0,
-            "iters_10pct": r10, "gpu_s_10pct": r10_ms / 1e3 if r10 else None,
-            "final_loss_ratio": last / l0, "min_loss_ratio": lmin / l0, "iters_run": it,
-            "gpu_s_total": gpu_ms / 1e3}
+    """One optimisation run (experiments.optimise_run): iterations and GPU time to `frac` and to 10%
+    of the iteration-0 64-spp eval loss."""
+    from paper_2309_15676_gb300.experiments import optimise_run as run
+    return run(w.scene, w.init_tex, target_img, mode, spp_prop, spp_fd, lr, max_iters, frac, flags=flags,
+               precond_lambda=precond_lambda)
 
 
 def time_to_threshold(torch, w, target_img, max_iters, lrs=(0.001, 0.003, 0.01, 0.03), frac=0.05, precond=None):
@@ -533,6 +495,8 @@ def scale_profile(torch, hbm_peak, image=1024):
                                  "bytes": byts, "ms": p["ms"], "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                  "frac": gbs / hbm_peak})
     out["kernel_ms"] = {k: v["ms"] for k, v in prof.items()}
+    out["kernel_units"] = {k: v["units"] for k, v in prof.items()}
+    out["kernel_launches"] = {k: v["launches"] for k, v in prof.items()}
     return out
 
 
@@ -881,6 +845,9 @@ def run_mine(args):
         rooflines_hbm["update_67M"] = {"frac": upd67["frac"], "achieved": upd67["achieved"], "unit": "GB/s"}
         if not args.no_ttt:
             emit("time_to_threshold", ttt_leg(torch, w, target_img, args.ttt_iters, local))
+        if args.diagnose:
+            from paper_2309_15676_gb300.experiments import meta_vs_adam_study
+            emit("meta_vs_adam", meta_vs_adam_study())
         if args.validate:
             from paper_2309_15676_gb300.experiments import trajectory_study
             emit("validation", {k: trajectory_study(runs=1000, iters=100, schedule=k) for k in ("linear", "exponential")})

@@ -54,3 +54,16 @@ def test_summary_statistics_of_simulated_runs():
     c = out["texel_curves"]["noisiest"]
     assert c["texel"] == int(np.argmax(s))
     assert np.allclose(c["true_gradient"], g[::10, c["texel"]], atol=5 * 2.0 * se + 1e-12)
+
+
+def test_pinned_spiral_holds_metal_and_roughness():
+    """The pinned form of the spiral: metalness and roughness equal the same constants in the
+    initial and target textures and their clamp ranges are that single value (the update cannot
+    move them), base colour stays free and differs between the two textures."""
+    import numpy as np
+    from paper_2309_15676_gb300.experiments import pinned_spiral
+    sc, init, tgt = pinned_spiral(0.5, 0.35, width=16, height=16, segments=16, sides=8, tex=8)
+    for t in (init, tgt):
+        assert np.all(t[..., 3] == np.float32(0.5)) and np.all(t[..., 4] == np.float32(0.35))
+    assert sc["clamp_lo"][3] == sc["clamp_hi"][3] == 0.5 and sc["clamp_lo"][4] == sc["clamp_hi"][4] == 0.35
+    assert sc["clamp_lo"][:3] == [0.0, 0.0, 0.0] and np.any(init[..., :3] != tgt[..., :3])
