@@ -532,6 +532,36 @@ def update_roofline(torch, hbm_peak, n=67_108_864, reps=10):
             "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
 
 
+def precond_leg(torch, hbm_peak):
+    """The gradient preconditioner's kernels inside an iteration (event-timed launches of one
+    non-graph iteration) on the 256^2 x 5 and 1024^2 x 5 spiral textures: time per gradient texture
+    and bytes moved (five passes, each one read and one write of the texture: 10 x 4 B per
+    parameter)."""
+    import numpy as np
+    from paper_2309_15676_gb300 import synth
+    from paper_2309_15676_gb300.api import Context, HyperParams
+    out = {}
+    for name, w in (("spiral256 (256^2 x 5)", synth.workload_spiral()),
+                    ("spiral512 (1024^2 x 5)", synth.workload_spiral(512, 512, 512, 32, 1024, max_depth=8))):
+        ctx = Context(0)
+        pid = ctx.add_scene(w.scene, HyperParams(lr=0.01, precond_lambda=4.0))
+        ctx.set_target(pid, np.zeros((w.scene["height"], w.scene["width"], 3), np.float32))
+        ctx.set_params(pid, w.init_tex)
+        ctx.iterate(2, use_graph=True)
+        ctx.profile(1)
+        ctx.iterate(1, use_graph=False)
+        p = ctx.profile_read()["precond"]
+        ctx.profile(0)
+        ctx.close()
+        n_par = w.init_tex.size
+        textures = 2                      # F and dF of the meta-estimator
+        ms = p["ms"] / textures
+        byts = 10 * 4 * n_par
+        out[name] = {"ms_per_texture": ms, "bytes_per_texture": byts, "achieved": byts / (ms * 1e-3) / 1e9,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": byts / (ms * 1e-3) / 1e9 / hbm_peak}
+    return out
+
+
 def volume_leg(torch, iters=400, lr=0.1, warm=3, timed=20, frac=0.005):
     """The 256^3 emissive-absorptive volume (67.1M parameters, four 256^2 views, 1 + 1 spp): kernel
     times, graph-launched iteration times of the meta-estimator and of Adam, and their loss curves at
@@ -842,6 +872,9 @@ def run_mine(args):
                                  "traced_paths_per_s": hs["traced_paths_per_s"]}
         upd67 = update_roofline(torch, hbm_peak)
         emit("update_standalone", upd67)
+        pc = precond_leg(torch, hbm_peak)
+        emit("precond", pc)
+        variants["precond_1024x1024x5_ms"] = pc["spiral512 (1024^2 x 5)"]["ms_per_texture"]
         rooflines_hbm["update_67M"] = {"frac": upd67["frac"], "achieved": upd67["achieved"], "unit": "GB/s"}
         if not args.no_ttt:
             emit("time_to_threshold", ttt_leg(torch, w, target_img, args.ttt_iters, local))

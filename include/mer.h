@@ -177,6 +177,9 @@ typedef struct mer_config {
      * instead of tracing (same hits, no traversal launches in the replays). The estimates are the
      * same either way; mer_adjoint and mer_adjoint_pair always re-trace. */
     int32_t replay_hit_store;
+    /* traversal launches: a warp's idle lanes take new rays once at least this many of its 32
+     * lanes are idle (1..32; 0 = default 8; mer_autotune picks it) */
+    int32_t trace_refill;
 } mer_config;
 
 typedef struct mer_iter_stats {

@@ -50,7 +50,7 @@ class SceneDesc(ct.Structure):
 
 class Config(ct.Structure):
     _fields_ = [("device", ct.c_int32), ("block_size", ct.c_int32), ("blocks_per_sm", ct.c_int32),
-                ("smem_nodes", ct.c_int32), ("max_paths", ct.c_int64), ("replay_hit_store", ct.c_int32)]
+                ("smem_nodes", ct.c_int32), ("max_paths", ct.c_int64), ("replay_hit_store", ct.c_int32), ("trace_refill", ct.c_int32)]
 
 
 class IterStats(ct.Structure):

@@ -173,10 +173,11 @@ class Context:
     """A set of inverse-rendering problems on one GPU (mer_ctx)."""
 
     def __init__(self, device: int = 0, block_size: int = 0, blocks_per_sm: int = 0, smem_nodes: int = 0,
-                 max_paths: int = 0, replay_hit_store: bool = False):
+                 max_paths: int = 0, replay_hit_store: bool = False, trace_refill: int = 0):
         self.L = _lib.load()
         self.device = torch.device("cuda", device)
-        cfg = _lib.Config(device, block_size, blocks_per_sm, smem_nodes, max_paths, int(replay_hit_store))
+        cfg = _lib.Config(device, block_size, blocks_per_sm, smem_nodes, max_paths, int(replay_hit_store),
+                          int(trace_refill))
         h = ct.c_void_p()
         check(self.L.mer_create(ct.byref(cfg), _cur_stream(self.device), ct.byref(h)))
         self.h = h

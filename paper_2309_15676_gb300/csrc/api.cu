@@ -91,7 +91,7 @@ struct mer_ctx {
     // graph of one iteration
     cudaGraphExec_t gexec = nullptr;
     bool graph_dirty = true;
-    LaunchShape shape{128, 0, 0, 1};
+    LaunchShape shape{128, 0, 0, 1, 8};
     int64_t launches = 0;
     void* timer = nullptr;      // EventTimer while profiling
     bool counting = false;      // profiling mode 2: traversal kernels count their tests
@@ -660,6 +660,7 @@ mer_status mer_create(const mer_config* cfg, void* cuda_stream, mer_ctx** out) {
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     c->shape.block = C.block_size > 0 ? C.block_size : 128;
     c->shape.smem_nodes = C.smem_nodes;
+    c->shape.refill = C.trace_refill > 0 ? std::min(C.trace_refill, 32) : 8;
     cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
     if (!e) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
     if (!e) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
@@ -1590,14 +1591,36 @@ mer_status mer_autotune(mer_ctx* c, int32_t trial_iters, char* desc, size_t desc
                 }
                 mer_checkpoint_load(c, saved.data(), saved.size());
             }
+    // then the traversal's refill threshold at the best shape
+    c->shape = best_shape;
+    c->cfg.blocks_per_sm = best_per_sm;
+    for (int rf : {4, 8, 16, 24}) {
+        c->shape.refill = rf;
+        c->graph_dirty = true;
+        if (mer_iterate(c, 1, 1)) {
+            mer_checkpoint_load(c, saved.data(), saved.size());
+            continue;
+        }
+        cudaEventRecord(e0, c->st);
+        const mer_status ts = mer_iterate(c, trial_iters, 1);
+        cudaEventRecord(e1, c->st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ts == MER_OK && cudaGetLastError() == cudaSuccess && ms < best) {
+            best = ms;
+            best_shape.refill = rf;
+        }
+        mer_checkpoint_load(c, saved.data(), saved.size());
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->shape = best_shape;
     c->cfg.blocks_per_sm = best_per_sm;
     c->graph_dirty = true;
     if (desc && desc_len)
-        snprintf(desc, desc_len, "block=%d blocks_per_sm=%d smem_nodes=%d ms_per_iter=%.4f", best_shape.block,
-                 best_per_sm, best_shape.smem_nodes, best / trial_iters);
+        snprintf(desc, desc_len, "block=%d blocks_per_sm=%d smem_nodes=%d refill=%d ms_per_iter=%.4f",
+                 best_shape.block, best_per_sm, best_shape.smem_nodes, best_shape.refill, best / trial_iters);
     return mer_checkpoint_load(c, saved.data(), saved.size());
 }
 

@@ -31,6 +31,19 @@ __device__ __forceinline__ void red_add(float* p, float a) {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(a) : "memory");
 }
 
+// L2 policy that keeps lines resident ahead of streamed data: the gradient textures are cleared
+// with it right before their scatter, and the scatter's reductions carry it, so that the
+// read-modify-writes find their lines in L2 while the records stream through (evict-first)
+__device__ __forceinline__ uint64_t evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void red_add_keep(float* p, float a, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(a), "l"(pol) : "memory");
+}
+
 // per-problem fields the scatter needs, cached in shared memory: the layout and the gradient
 // texture this launch adds to (NULL: the problem has none and its records are skipped)
 struct SProb {
@@ -219,12 +232,12 @@ __device__ __forceinline__ int stage_record(bool valid, float4 a, float4 b, cons
 // Phase 2, ten lanes per row and three rows per step over the compacted rows: each reduction
 // instruction adds up to three contiguous runs of 2C floats, which the load/store unit packs into
 // one request per 32-byte sector (about two per row) instead of one per vector reduction and lane.
-__device__ __forceinline__ void reduce_rows(const WarpArea& WA, int lane, int nrows) {
+__device__ __forceinline__ void reduce_rows(const WarpArea& WA, int lane, int nrows, uint64_t pol) {
     const int slot = lane / 10, e = lane - 10 * slot;
     for (int q = slot; q - slot < nrows; q += 3) {
         if (slot < 3 && q < nrows) {
             const RowEnt R = WA.rows[q];
-            if (e < R.len) red_add(R.addr + e, WA.vals[R.vidx + e]);
+            if (e < R.len) red_add_keep(R.addr + e, WA.vals[R.vidx + e], pol);
         }
     }
 }
@@ -245,6 +258,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scatter(uint32_t* __restrict__ c
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     WarpArea& WA = areas[wib];
     uint64_t* bar = bars + wib * SC_STAGES;
+    const uint64_t keep = evict_last_policy();
     for (int t = threadIdx.x; t < n_probs; t += blockDim.x) {
         const ProblemDev& P = probs[t];
         sp[t] = SProb{P.tex_c, P.tex_w, P.tex_h, 0, grad_target(P, which), nullptr};
@@ -292,22 +306,27 @@ __global__ void __launch_bounds__(SC_THREADS) k_scatter(uint32_t* __restrict__ c
         }
         const int nrows = stage_record(valid, a, b, sp, grad_over, which, WA, lane);
         __syncwarp();
-        reduce_rows(WA, lane, nrows);
+        reduce_rows(WA, lane, nrows, keep);
         __syncwarp();   // the rows are read before the next chunk overwrites them
     }
 }
 
 // float4 stores over each problem's gradient texture `which` (16-byte aligned allocations;
-// scalar tail; problems without one are skipped)
+// scalar tail; problems without one are skipped), marked evict-last in L2 for the scatter that
+// follows
 __global__ void k_zero_grads(const ProblemDev* __restrict__ probs, int n_probs, int which) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t keep = evict_last_policy();
     for (int q = 0; q < n_probs; ++q) {
         float* g = grad_target(probs[q], which);
         if (!g) continue;
         const int64_t n = probs[q].n_par, n4 = n >> 2;
         float4* g4 = reinterpret_cast<float4*>(g);
-        for (int64_t i = t0; i < n4; i += stride) g4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int64_t i = t0; i < n4; i += stride)
+            asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %1, %1, %1}, %2;" ::"l"(g4 + i), "f"(0.0f),
+                         "l"(keep)
+                         : "memory");
         for (int64_t i = 4 * n4 + t0; i < n; i += stride) g[i] = 0.0f;
     }
 }

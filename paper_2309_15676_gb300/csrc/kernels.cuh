@@ -35,6 +35,7 @@ struct LaunchShape {
     int per_sm;       // cap on resident blocks per SM of the persistent grids (0 = occupancy)
     int smem_nodes;   // BVH nodes staged in shared memory
     int sms;          // multiprocessors of the device
+    int refill;       // traversal: idle lanes of a warp that trigger fetching new rays (1..32)
 };
 
 int run_pass(const PassArgs& A, int nb, int mode, int max_depth, const LaunchShape& L, cudaStream_t st);

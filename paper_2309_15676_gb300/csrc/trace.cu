@@ -889,12 +889,10 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
 // A work unit is one ray: units [0, n_eu) are continuation rays (NB = 2: entry u >> 1, branch
 // u & 1, so an FD pair's two rays take two lanes), units [n_eu, n_eu + n_sh) the shadow rays.
 // Units are fetched dynamically (persistent threads with dynamic ray fetching, after Aila and
-// Laine 2009): every lane keeps its own walk, and whenever TRACE_REFILL or more lanes of a warp
-// are idle, those lanes take the next units from the launch's fetch counter (one atomic per warp),
+// Laine 2009): every lane keeps its own walk, and whenever A.refill or more lanes of a warp are
+// idle, those lanes take the next units from the launch's fetch counter (one atomic per warp),
 // so a warp does not wait for its slowest ray while units remain.
 // ---------------------------------------------------------------------------------
-constexpr int TRACE_REFILL = 8;
-
 struct Unit {
     int64_t j;   // queue entry
     int b;       // branch of a continuation ray; -1: shadow ray
@@ -1000,9 +998,10 @@ __global__ void __launch_bounds__(256, NB == 1 ? 4 : 3) k_trace(PassArgs A, int 
     Unit U{0, 0, 0};
     TravCount tc;
     bool busy = false, more = n > 0;
+    const int refill = min(max(A.refill, 1), 32);
     while (true) {
         const unsigned idle = __ballot_sync(FULL, !busy);
-        if (more && __popc(idle) >= TRACE_REFILL) {
+        if (more && __popc(idle) >= refill) {
             const unsigned cnt = (unsigned)__popc(idle);
             uint32_t base = 0;
             if (lane == 0) base = atomicAdd(fetch, cnt);
@@ -1118,6 +1117,7 @@ struct PassLauncher {
         const size_t smem = (size_t)L.smem_nodes * sizeof(Node);
         PassArgs B = A;
         B.smem_nodes = L.smem_nodes;
+        B.refill = L.refill;
         grids(L, smem);
         if (MODE == MODE_REPLAY && B.hs) {
             for (int depth = 1; depth <= max_depth; ++depth) shade(B, depth, L, st);

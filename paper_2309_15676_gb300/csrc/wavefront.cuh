@@ -78,6 +78,7 @@ struct PassArgs {
     int64_t hs_cap;
     int32_t smem_nodes;       // top BVH nodes of problem smem_prob staged in shared memory
     int32_t smem_prob;
+    int32_t refill;           // traversal: idle lanes of a warp that trigger fetching new rays
     unsigned long long* stats; // counting run: [2*class] node tests, [2*class+1] primitive tests
 };
 

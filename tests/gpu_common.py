@@ -22,3 +22,13 @@ def frac_within(a, ref, rtol, atol):
     a = np.asarray(a, np.float64)
     ref = np.asarray(ref, np.float64)
     return float(np.mean(np.abs(a - ref) <= rtol * np.abs(ref) + atol))
+
+
+def params_match(a, b, frac=0.999, atol=1e-5, cap=0.1):
+    """Parameters of two runs that differ only in the order of float reductions (gradients
+    accumulate with float atomics, and the dynamic ray fetching reorders records): at least `frac`
+    of them within `atol`, none further apart than `cap`. A texel whose samples cancel to within a
+    rounding of zero can take a full normalised step in one run and none in the other, so a bound
+    on every element would test the rounding, not the method."""
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))
+    return float(np.mean(d <= atol)) >= frac and float(d.max()) <= cap

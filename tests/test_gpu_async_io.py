@@ -5,7 +5,7 @@ import pytest
 
 from paper_2309_15676_gb300 import synth
 
-from .gpu_common import need_gpu
+from .gpu_common import need_gpu, params_match
 
 pytestmark = pytest.mark.gpu
 
@@ -35,4 +35,4 @@ def test_async_target_and_loss_match_synchronous_calls():
         ctx.close()
     (la, pa), (lb, pb) = out
     assert abs(la - lb) <= 1e-9 * lb
-    assert np.allclose(pa, pb, rtol=0, atol=1e-5)
+    assert params_match(pa, pb)

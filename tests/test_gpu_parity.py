@@ -14,7 +14,7 @@ import pytest
 from oracle import meta, orc
 from paper_2309_15676_gb300 import synth
 
-from .gpu_common import frac_within, need_gpu, rel_l2
+from .gpu_common import frac_within, need_gpu, params_match, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -369,14 +369,14 @@ def test_graph_checkpoint_batch_consistency(torch_mod):
     c, (c1,) = make([(ws, ts)])
     c.iterate(3, use_graph=True)
     pa, pb, pc = a.get_params(a1).cpu().numpy(), b.get_params(b1).cpu().numpy(), c.get_params(c1).cpu().numpy()
-    assert np.allclose(pa, pb, rtol=0, atol=1e-5) and np.allclose(pb, pc, rtol=0, atol=1e-5)
-    assert np.allclose(a.get_params(a0).cpu().numpy(), b.get_params(b0).cpu().numpy(), rtol=0, atol=1e-5)
+    assert params_match(pa, pb) and params_match(pb, pc)
+    assert params_match(a.get_params(a0).cpu().numpy(), b.get_params(b0).cpu().numpy())
     blob = b.checkpoint_save()
     b.iterate(2, use_graph=True)
     after = b.get_params(b1).cpu().numpy()
     b.checkpoint_load(blob)
     b.iterate(2, use_graph=True)
-    assert np.allclose(b.get_params(b1).cpu().numpy(), after, rtol=0, atol=1e-5)
+    assert params_match(b.get_params(b1).cpu().numpy(), after)
     assert b.stats(b1)["iteration"] == 5
     for x in (a, b, c):
         x.close()

@@ -9,7 +9,7 @@ import pytest
 from oracle import precond
 from paper_2309_15676_gb300 import synth
 
-from .gpu_common import need_gpu, rel_l2
+from .gpu_common import need_gpu, params_match, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +62,7 @@ def test_preconditioned_iterations_in_a_graph():
         c.iterate(3, use_graph=graph)
         out.append(c.get_params(p).cpu().numpy())
         c.close()
-    assert np.allclose(out[0], out[1], rtol=0, atol=1e-5)
+    assert params_match(out[0], out[1])
 
 
 @pytest.mark.parametrize("C,H,W", [(5, 64, 64), (3, 1024, 1024), (5, 2048, 64), (5, 64, 2048), (3, 5, 7),

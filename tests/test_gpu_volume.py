@@ -8,7 +8,7 @@ import pytest
 from oracle import orc
 from paper_2309_15676_gb300 import synth
 
-from .gpu_common import frac_within, need_gpu
+from .gpu_common import frac_within, need_gpu, params_match
 from .test_gpu_parity import _grad_check
 
 pytestmark = pytest.mark.gpu
@@ -209,7 +209,7 @@ def test_volume_optimiser_graph_equals_launches_and_rejects_bad_input():
     a.iterate(4, use_graph=False)
     b.iterate(4, use_graph=True)
     pa, pb = a.params().cpu().numpy(), b.params().cpu().numpy()
-    assert np.allclose(pa, pb, rtol=0, atol=1e-5)
+    assert params_match(pa, pb)
     assert a.stats()["iteration"] == b.stats()["iteration"] == 4
     # reset: back to iteration 0 and the same first step
     init = np.full(a.shape, 0.3, np.float32)
