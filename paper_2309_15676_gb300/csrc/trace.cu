@@ -440,6 +440,39 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* ctr, uint32_t cnt) {
 
 __device__ __forceinline__ void set_err(const PassArgs& A, int code) { atomicCAS(&A.cnt[CNT_ERR], 0u, (uint32_t)code); }
 
+// Passes with at least this many paths append their continuation rays grouped by direction
+// octant within each block (block_append_grouped); smaller passes append per warp.
+constexpr int64_t GROUP_MIN_PATHS = (int64_t)1 << 20;
+
+// Block-aggregated append grouped by key (0..7): the block's entries of each key get contiguous
+// slots, keys in ascending order, with one atomic per block. Every thread of the block must call
+// it (it synchronises the block); returns this thread's slot if `want`.
+__device__ __forceinline__ uint32_t block_append_grouped(uint32_t* ctr, bool want, int key) {
+    __shared__ uint32_t s_cnt[8];
+    if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint32_t rank = want ? atomicAdd(&s_cnt[key], 1u) : 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t c[8], tot = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            c[k] = s_cnt[k];
+            tot += c[k];
+        }
+        uint32_t off = tot ? atomicAdd(ctr, tot) : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            s_cnt[k] = off;
+            off += c[k];
+        }
+    }
+    __syncthreads();
+    const uint32_t slot = s_cnt[key] + rank;
+    __syncthreads();   // every thread has read its base before the next call resets them
+    return slot;
+}
+
 extern __shared__ float4 s_dyn[];
 
 // stages the first nodes of problem smem_prob's BVH (its top levels) in shared memory;
@@ -487,10 +520,13 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
     const bool stored = MODE == MODE_REPLAY && A.hs != nullptr;
     const bool first = depth == 1;
     const int64_t n = first ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth], A.qcap);
-    const int64_t nw = (n + 31) & ~(int64_t)31;
+    // whole blocks iterate together (the grouped append synchronises the block)
+    const int64_t nb = (n + blockDim.x - 1) / blockDim.x * blockDim.x;
+    const bool grouped = A.n_paths >= GROUP_MIN_PATHS;
     const int qi = depth & 1, qo = qi ^ 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nw; j += stride) {
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < nb; j0 += stride) {
+        const int64_t j = j0 + threadIdx.x;
         const bool valid = j < n;
         uint32_t flags = 0;
         int64_t g = 0;
@@ -845,7 +881,16 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
             bool any_cont = false;
 #pragma unroll
             for (int b = 0; b < NB; ++b) any_cont |= cont[b];
-            const uint32_t slot = warp_append(&A.cnt[CNT_Q + depth + 1], any_cont ? 1u : 0u);
+            // a large pass groups the block's continuation rays by direction octant, so that
+            // the next traversal's warps take runs of rays heading the same way
+            uint32_t slot;
+            if (grouped) {
+                const v3 dc = cont[0] ? wi_b[0] : wi_b[NB - 1];
+                const int oct = any_cont ? ((dc.x < 0.0f) | ((dc.y < 0.0f) << 1) | ((dc.z < 0.0f) << 2)) : 0;
+                slot = block_append_grouped(&A.cnt[CNT_Q + depth + 1], any_cont, oct);
+            } else {
+                slot = warp_append(&A.cnt[CNT_Q + depth + 1], any_cont ? 1u : 0u);
+            }
             if (any_cont) {
                 if (slot >= A.qcap) {
                     set_err(A, MER_ERR_BOUNDS);
