@@ -318,7 +318,11 @@ mer_status mer_update_step(mer_ctx* ctx);
 /* n_iters full iterations (gradient + update) of all problems; use_graph = 1 replays one
  * captured CUDA graph per iteration (captured on first use). */
 mer_status mer_iterate(mer_ctx* ctx, int32_t n_iters, int32_t use_graph);
-/* Statistics of a problem (synchronous). */
+/* Statistics of a problem (synchronous). Also reads the kernels' error word: a capacity overrun
+ * returns MER_ERR_BOUNDS and a bounded wait that ran out MER_ERR_TIMEOUT. After MER_ERR_TIMEOUT
+ * the context's results can no longer be trusted (a scatter block may have left with copies in
+ * flight), and mer_gradient_step, mer_update_step and mer_iterate refuse it (MER_ERR_STATE):
+ * destroy the context. */
 mer_status mer_stats(mer_ctx* ctx, int32_t pid, mer_iter_stats* out);
 
 /* Optimiser state of a problem (parameter-shaped device arrays owned by the context) for

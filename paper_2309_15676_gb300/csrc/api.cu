@@ -96,6 +96,7 @@ struct mer_ctx {
     void* timer = nullptr;      // EventTimer while profiling
     bool counting = false;      // profiling mode 2: traversal kernels count their tests
     unsigned long long* d_stats = nullptr;
+    bool failed = false;        // a kernel's bounded wait ran out: the context refuses further work
 };
 
 namespace {
@@ -491,6 +492,9 @@ mer_status check_err_word(mer_ctx* c) {
         CK(c, cudaMemcpy(&e, w.cnt + CNT_ERR, sizeof e, cudaMemcpyDeviceToHost));
         if (e) {
             cudaMemset(w.cnt + CNT_ERR, 0, sizeof(uint32_t));
+            // a bounded wait that ran out may have left copies in flight: nothing the context
+            // computes from now on can be trusted
+            if (e == MER_ERR_TIMEOUT) c->failed = true;
             return fail(c, (int)e, "a kernel reported %s (code %u)",
                         e == MER_ERR_TIMEOUT ? "a bounded wait that ran out" : "an out-of-capacity write", e);
         }
@@ -1258,6 +1262,7 @@ mer_status mer_adjoint_pair(mer_ctx* c, int32_t pid, const float* texA, const fl
 
 mer_status mer_gradient_step(mer_ctx* c) {
     if (!c || c->probs.empty()) return fail(c, MER_ERR_STATE, "no problems");
+    if (c->failed) return fail(c, MER_ERR_STATE, "a kernel ran out of a bounded wait earlier; destroy this context");
     Guard g(c);
     c->launches = enqueue_gradient(c);
     CK(c, cudaGetLastError());
@@ -1266,6 +1271,7 @@ mer_status mer_gradient_step(mer_ctx* c) {
 
 mer_status mer_update_step(mer_ctx* c) {
     if (!c || c->probs.empty()) return fail(c, MER_ERR_STATE, "no problems");
+    if (c->failed) return fail(c, MER_ERR_STATE, "a kernel ran out of a bounded wait earlier; destroy this context");
     Guard g(c);
     c->launches = enqueue_update(c);
     CK(c, cudaGetLastError());
@@ -1274,6 +1280,7 @@ mer_status mer_update_step(mer_ctx* c) {
 
 mer_status mer_iterate(mer_ctx* c, int32_t n_iters, int32_t use_graph) {
     if (!c || c->probs.empty()) return fail(c, MER_ERR_STATE, "no problems");
+    if (c->failed) return fail(c, MER_ERR_STATE, "a kernel ran out of a bounded wait earlier; destroy this context");
     if (n_iters < 0) return fail(c, MER_ERR_INVALID_ARG, "negative iteration count");
     Guard g(c);
     if (!use_graph) {

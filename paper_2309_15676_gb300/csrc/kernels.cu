@@ -285,8 +285,10 @@ __global__ void __launch_bounds__(SC_THREADS) k_scatter(uint32_t* __restrict__ c
         if (!__all_sync(FULLM, ok)) {
             if (lane == 0) {
                 atomicCAS(&cnt[CNT_ERR], 0u, (uint32_t)MER_ERR_TIMEOUT);
+                // drain the copies still in flight into this warp's ring before the block can
+                // leave (ten times the normal limit); the host refuses the context from now on
                 for (int64_t q = k; q < min(my, k + SC_STAGES); ++q)
-                    mbar_wait(&bar[q % SC_STAGES], (uint32_t)(q / SC_STAGES) & 1u);
+                    mbar_wait(&bar[q % SC_STAGES], (uint32_t)(q / SC_STAGES) & 1u, 10 * SC_WAIT_NS);
             }
             __syncwarp();
             return;
