@@ -8,23 +8,6 @@ KernelTimer* g_timer = nullptr;
 
 constexpr unsigned FULLM = 0xffffffffu;
 
-// sum of v over the lanes of `peers` (lanes listed in vmask all call this); every lane gets
-// the sum over its own peer group, in a fixed lane order
-__device__ __forceinline__ float peer_sum(unsigned vmask, unsigned peers, float v, int maxg) {
-    const unsigned lane = threadIdx.x & 31u;
-    unsigned others = peers & ~(1u << lane);
-    float acc = v;
-    for (int i = 1; i < maxg; ++i) {
-        const int src = others ? (__ffs(others) - 1) : (int)lane;
-        const float x = __shfl_sync(vmask, v, src);
-        if (others) {
-            acc += x;
-            others &= others - 1;
-        }
-    }
-    return acc;
-}
-
 // Fire-and-forget reduction: no value comes back, so the issuing warp never waits on the L2
 // (the vector atomicAdd overloads return the old value and compile to waiting atomics)
 __device__ __forceinline__ void red_add(float* p, float a) {
@@ -40,9 +23,12 @@ __device__ __forceinline__ uint64_t evict_last_policy() {
     return pol;
 }
 
+// No "memory" clobber: nothing in the scatter reads the gradient texture, and without it the
+// compiler may hoist the shared-memory loads of the next rows above the reduction
 __device__ __forceinline__ void red_add_keep(float* p, float a, uint64_t pol) {
-    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(a), "l"(pol) : "memory");
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(a), "l"(pol));
 }
+
 
 // per-problem fields the scatter needs, cached in shared memory: the layout and the gradient
 // texture this launch adds to (NULL: the problem has none and its records are skipped)
@@ -70,24 +56,22 @@ __device__ __forceinline__ void fill_row(float (&v)[10], const float (&g)[MAXC],
 
 constexpr int SC_THREADS = 256;
 constexpr int SC_WARPS = SC_THREADS / 32;
-constexpr int SC_STAGES = 3;                        // chunks in flight per warp
+constexpr int SC_STAGES = 2;                        // chunks in flight per warp
 constexpr int SC_CHUNK = 32;                        // records per chunk (one per lane in phase 1)
 constexpr int SC_ROWS = 2 * SC_CHUNK;               // bilinear rows of a chunk
 constexpr uint32_t SC_WAIT_POLLS = 1u << 20;        // bound on the polls of one stage barrier
 constexpr uint64_t SC_WAIT_NS = 200000000ull;       // and on its wall time (0.2 s)
 constexpr uint32_t SC_SUSPEND_NS = 1000;            // suspend hint of one poll
 
-// one non-empty bilinear row of a chunk: where its run starts, how long it is, where its values are
-struct __align__(16) RowEnt {
-    float* addr;
-    int len;                            // C or 2C floats
-    int vidx;                           // index of its first value in WarpArea::vals
-};
-
+// Per-warp staging. The chunk's non-empty bilinear rows are compacted: row q keeps its ten values
+// (zero beyond its length) at vals[10 q ...] and the address of its first float at addr[q], so that
+// a reduction step of three rows reads thirty contiguous values (one shared-memory wavefront) and
+// three row addresses. When footprints merge, vals first holds each lane's two raw rows at
+// vals[20 lane ...].
 struct __align__(16) WarpArea {
     Record ring[SC_STAGES][SC_CHUNK];   // records, filled by bulk copies
-    float vals[SC_CHUNK * 20];          // weighted row values of each record: row 0 then row 1
-    RowEnt rows[SC_ROWS];               // the chunk's non-empty rows, compacted
+    float vals[SC_ROWS * 10];           // row values, compacted
+    float* addr[SC_ROWS];               // row start addresses, compacted
 };
 constexpr size_t SC_HEAD = 256;         // stage barriers, then the warp areas, then the problem table
 
@@ -163,22 +147,39 @@ int run_wait_selftest(uint64_t limit_ns, int32_t* status, uint64_t* waited_ns, c
     return 1;
 }
 
+// Records of a chunk that share a footprint origin are merged only when some origin is held by at
+// least this many lanes: at 1024^2 over a 2048^2 texture a chunk's groups are pairs at most in 99%
+// of chunks, and merging pairs costs more instructions than the 3% of reductions it saves; an image
+// much finer than its texture (many lanes per texel) merges.
+constexpr int SC_MERGE_MIN = 3;
+
+// Writes compacted row q (values v[0..10), zero beyond the row's length, to be added at p)
+__device__ __forceinline__ void put_row(WarpArea& WA, int q, float* p, const float (&v)[10]) {
+    float2* d = reinterpret_cast<float2*>(WA.vals + 10 * q);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) d[j] = make_float2(v[2 * j], v[2 * j + 1]);
+    WA.addr[q] = p;
+}
+
 // Phase 1, one record per lane: the bilinear footprint (clamp-to-edge) of the record's texel
 // window becomes two rows of up to 2C contiguous floats (taps xa, xb of texel rows ya, yb;
-// taps that clamp onto the same texel are merged first) holding w_k g[c]. Lanes holding the same
-// footprint origin are merged with __match_any_sync and a segmented shuffle sum over both rows,
-// run by every participating lane; the group's first lane keeps the rows. Lanes whose record is
-// absent or all-zero sit out. The values go to the warp's area and the non-empty rows to a
-// compacted list (ballot + prefix count); returns the number of rows, the same on every lane.
+// taps that clamp onto the same texel are merged first) holding w_k g[c]; the values beyond a
+// row's length are zero (a single-texel row's second tap has weight zero). Lanes whose record is
+// absent or all-zero sit out. When some footprint origin is held by SC_MERGE_MIN lanes or more,
+// each group's first lane adds its peers' rows (in lane order) and alone keeps them. The non-empty
+// rows are compacted (ballot + prefix count: every lane's first row, then every lane's second row)
+// into the warp's area; returns their number, the same on every lane.
 __device__ __forceinline__ int stage_record(bool valid, float4 a, float4 b, const SProb* sp, float* grad_over,
-                                            int which, WarpArea& WA, int lane) {
+                                            WarpArea& WA, int lane) {
     const uint32_t pos = __float_as_uint(a.x);
     const float g[MAXC] = {a.w, b.x, b.y, b.z, b.w};
     valid = valid && (g[0] != 0.0f || g[1] != 0.0f || g[2] != 0.0f || g[3] != 0.0f || g[4] != 0.0f);
     const unsigned vmask = __ballot_sync(FULLM, valid);
     bool r0 = false, r1 = false;
-    int off0 = 0, off1 = 0, len = 0;
+    int off0 = 0, off1 = 0;
     float* base = nullptr;
+    unsigned peers = 0;
+    int maxg = 0;
     float v0[10], v1[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) v0[k] = v1[k] = 0.0f;
@@ -194,51 +195,63 @@ __device__ __forceinline__ int stage_record(bool valid, float4 a, float4 b, cons
         if (one_y) { w00 += w01; w10 += w11; w01 = 0.0f; w11 = 0.0f; }
         if (C == 5) { fill_row<5>(v0, g, w00, w10); fill_row<5>(v1, g, w01, w11); }
         else { fill_row<3>(v0, g, w00, w10); fill_row<3>(v1, g, w01, w11); }
-        len = (one_x ? 1 : 2) * C;
         // texture extents are below 4096 per side and C <= 5: offsets fit in 32 bits
         off0 = (ya * W + xa) * C;
         off1 = (yb * W + xa) * C;
         base = grad_over ? grad_over : P.tgt;
         r0 = base != nullptr;
         r1 = r0 && !one_y;
-        // same pos => same problem and layout; every lane of vmask runs every shuffle
-        const unsigned peers = __match_any_sync(vmask, pos);
-        const int maxg = (int)__reduce_max_sync(vmask, (unsigned)__popc(peers));
-        if (maxg > 1) {
-#pragma unroll
-            for (int k = 0; k < 10; ++k) {
-                v0[k] = peer_sum(vmask, peers, v0[k], maxg);
-                v1[k] = peer_sum(vmask, peers, v1[k], maxg);
-            }
-            if (lane != __ffs(peers) - 1) r0 = r1 = false;
+        // same pos => same problem and layout
+        peers = __match_any_sync(vmask, pos);
+        maxg = (int)__reduce_max_sync(vmask, (unsigned)__popc(peers));
+    }
+    maxg = __shfl_sync(FULLM, maxg, vmask ? __ffs(vmask) - 1 : 0);
+    if (maxg >= SC_MERGE_MIN) {   // warp-uniform
+        float4* d = reinterpret_cast<float4*>(WA.vals + 20 * lane);
+        if (valid) {
+            d[0] = make_float4(v0[0], v0[1], v0[2], v0[3]);
+            d[1] = make_float4(v0[4], v0[5], v0[6], v0[7]);
+            d[2] = make_float4(v0[8], v0[9], v1[0], v1[1]);
+            d[3] = make_float4(v1[2], v1[3], v1[4], v1[5]);
+            d[4] = make_float4(v1[6], v1[7], v1[8], v1[9]);
         }
+        __syncwarp();
+        const bool lead = valid && lane == __ffs(peers) - 1;
+        unsigned others = lead ? (peers & ~(1u << lane)) : 0u;
+        for (int i = 1; i < maxg; ++i) {
+            if (others) {
+                const float4* o = reinterpret_cast<const float4*>(WA.vals + 20 * (__ffs(others) - 1));
+                const float4 x0 = o[0], x1 = o[1], x2 = o[2], x3 = o[3], x4 = o[4];
+                v0[0] += x0.x; v0[1] += x0.y; v0[2] += x0.z; v0[3] += x0.w;
+                v0[4] += x1.x; v0[5] += x1.y; v0[6] += x1.z; v0[7] += x1.w;
+                v0[8] += x2.x; v0[9] += x2.y; v1[0] += x2.z; v1[1] += x2.w;
+                v1[2] += x3.x; v1[3] += x3.y; v1[4] += x3.z; v1[5] += x3.w;
+                v1[6] += x4.x; v1[7] += x4.y; v1[8] += x4.z; v1[9] += x4.w;
+                others &= others - 1;
+            }
+        }
+        __syncwarp();   // every raw row is read before the compacted rows overwrite the area
+        if (valid && !lead) r0 = r1 = false;
     }
     const unsigned m0 = __ballot_sync(FULLM, r0), m1 = __ballot_sync(FULLM, r1);
     const unsigned below = (1u << lane) - 1u;
     const int n0 = __popc(m0);
-    if (r0) WA.rows[__popc(m0 & below)] = RowEnt{base + off0, len, 20 * lane};
-    if (r1) WA.rows[n0 + __popc(m1 & below)] = RowEnt{base + off1, len, 20 * lane + 10};
-    if (r0) {
-        float4* d = reinterpret_cast<float4*>(WA.vals + 20 * lane);
-        d[0] = make_float4(v0[0], v0[1], v0[2], v0[3]);
-        d[1] = make_float4(v0[4], v0[5], v0[6], v0[7]);
-        d[2] = make_float4(v0[8], v0[9], v1[0], v1[1]);
-        d[3] = make_float4(v1[2], v1[3], v1[4], v1[5]);
-        d[4] = make_float4(v1[6], v1[7], v1[8], v1[9]);
-    }
+    if (r0) put_row(WA, __popc(m0 & below), base + off0, v0);
+    if (r1) put_row(WA, n0 + __popc(m1 & below), base + off1, v1);
     return n0 + __popc(m1);
 }
 
-// Phase 2, ten lanes per row and three rows per step over the compacted rows: each reduction
-// instruction adds up to three contiguous runs of 2C floats, which the load/store unit packs into
-// one request per 32-byte sector (about two per row) instead of one per vector reduction and lane.
+// Phase 2, ten lanes per row and three rows per step over the compacted rows: step t reads the
+// contiguous values vals[30 t + lane] and the three row addresses, and each reduction instruction
+// adds up to three runs of 2C floats, which the load/store unit packs into one request per 32-byte
+// sector. Zero values (a row's padding, or an exactly zero product) add nothing and are skipped.
 __device__ __forceinline__ void reduce_rows(const WarpArea& WA, int lane, int nrows, uint64_t pol) {
     const int slot = lane / 10, e = lane - 10 * slot;
-    for (int q = slot; q - slot < nrows; q += 3) {
-        if (slot < 3 && q < nrows) {
-            const RowEnt R = WA.rows[q];
-            if (e < R.len) red_add_keep(R.addr + e, WA.vals[R.vidx + e], pol);
-        }
+    if (slot >= 3) return;
+    for (int q = slot, f = lane; q < nrows; q += 3, f += 30) {
+        const float v = WA.vals[f];
+        float* p = WA.addr[q];
+        if (v != 0.0f) red_add_keep(p + e, v, pol);
     }
 }
 
@@ -296,9 +309,13 @@ __global__ void __launch_bounds__(SC_THREADS) k_scatter(uint32_t* __restrict__ c
         const bool valid = (gw + k * tw) * SC_CHUNK + lane < n;
         float4 a = make_float4(0, 0, 0, 0), b = a;
         if (valid) {
+            // lanes 4-7 of each group of eight read the two halves in the other order, so that the
+            // eight 16-byte reads of one shared-memory wavefront fall on distinct banks
             const float4* r = reinterpret_cast<const float4*>(&WA.ring[s][lane]);
-            a = r[0];
-            b = r[1];
+            const int h = (lane >> 2) & 1;
+            const float4 x = r[h], y = r[h ^ 1];
+            a = h ? y : x;
+            b = h ? x : y;
         }
         __syncwarp();
         if (lane == 0 && k + SC_STAGES < my) {
@@ -306,7 +323,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_scatter(uint32_t* __restrict__ c
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(k + SC_STAGES);
         }
-        const int nrows = stage_record(valid, a, b, sp, grad_over, which, WA, lane);
+        const int nrows = stage_record(valid, a, b, sp, grad_over, WA, lane);
         __syncwarp();
         reduce_rows(WA, lane, nrows, keep);
         __syncwarp();   // the rows are read before the next chunk overwrites them
