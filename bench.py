@@ -33,10 +33,15 @@ sys.path.insert(0, ROOT)
 METRIC = "paths/s, iters/s; time to loss threshold, meta-estimator vs plain MC, 1 GB300"
 PATHS_PER_PIXEL = 12            # 2 proportional x (primal, adjoint fwd, replay) + 1 FD pair x 6
 # DRAM bytes (read + write) per launch of the traversal kernels, from one ncu capture of the
-# spiral256 iteration with re-tracing replays; "source" names the commit the kernels were
-# captured at, and the bench reports the figure only while the traversal source is unchanged
-# since then (its sha1 is compared), else null.
-TRACE_DRAM = {"source": None, "trace_cu_sha1": None, "bytes": {}}
+# spiral256 iteration with re-tracing replays (1-pass metrics dram__bytes_read.sum +
+# dram__bytes_write.sum, caches flushed before each launch, mean over 8 steady iterations, default
+# launch shape); "source" names the commit the kernels were captured at, and the bench reports
+# the figure only while the traversal source is unchanged since then (its sha1 is compared), else
+# null.
+TRACE_DRAM = {"source": "commit b3d29d8 (traversal source as of 92a0514)",
+              "trace_cu_sha1": "fa17a9773e7a31a7d8faccaf1871f9453c311651",
+              "bytes": {"trace_1_primal": 3154155, "trace_1_replay": 3812363,
+                        "trace_2_primal": 2444221, "trace_2_replay": 3009083}}
 
 def replica_scene(scene: dict, rank: int) -> dict:
     """Each rank optimises its own replica: the same problem under its own Philox key."""

@@ -1,5 +1,7 @@
 """Host logic of bench.py: parsing the clock samples taken during the timed region and the rule
 that rejects a timed region (and has it measured once more)."""
+import os
+
 import bench
 
 
@@ -69,6 +71,10 @@ def test_fp32_peak_and_recorded_traffic_rules():
     figure is reported only while the traversal source is the one it was captured from."""
     assert abs(bench.fp32_peak_tflops(152, 2070.0) - 80.54) < 0.01
     assert abs(bench.fp32_peak_tflops(148, 1965.0) - 148 * 256 * 1965e6 / 1e12) < 1e-9
+    import hashlib
+    with open(os.path.join(bench.ROOT, "paper_2309_15676_gb300", "csrc", "trace.cu"), "rb") as f:
+        same = hashlib.sha1(f.read()).hexdigest() == bench.TRACE_DRAM["trace_cu_sha1"]
+    assert bench.trace_traffic("trace_2_primal") == (bench.TRACE_DRAM["bytes"]["trace_2_primal"] if same else None)
     saved = dict(bench.TRACE_DRAM)
     try:
         bench.TRACE_DRAM.update({"source": "x", "trace_cu_sha1": "0" * 40, "bytes": {"trace_1_primal": 1.0}})
