@@ -712,8 +712,11 @@ def dominant_roofline(prof, counts, kernels, rooflines, fp32_peak, sms, sm_max):
     ck = counts.get(dom, {})
     flops = NODE_FLOPS * ck.get("node_tests", 0) + PRIM_FLOPS * ck.get("prim_tests", 0)
     ach = flops / (dk["ms"] * 1e-3) / 1e12 if flops else None
+    traffic = trace_traffic(dom)
     return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": (ach / fp32_peak) if ach else None, "traffic": trace_traffic(dom),
+            "frac": (ach / fp32_peak) if ach else None, "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold caches, "
+                               + TRACE_DRAM["source"]) if traffic is not None else None,
             "peak_basis": f"nominal FP32: {sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
             "ms_per_launch": dk["ms"] / dk["launches"], "share": kernels[dom]["share"],
             "rays_per_s": dk["units"] / (dk["ms"] * 1e-3),
