@@ -936,7 +936,10 @@ __global__ void __launch_bounds__(256, (shade_min_blocks<NB, MODE>())) k_shade(P
 // Units are fetched dynamically (persistent threads with dynamic ray fetching, after Aila and
 // Laine 2009): every lane keeps its own walk, and whenever A.refill or more lanes of a warp are
 // idle, those lanes take the next units from the launch's fetch counter (one atomic per warp),
-// so a warp does not wait for its slowest ray while units remain.
+// so a warp does not wait for its slowest ray while units remain. Once they are all taken, a
+// launch lasts as long as its longest walks, each a chain of dependent node and triangle tests on
+// one lane; the idle lanes then split those walks by taking over their deferred subtrees (the
+// cooperative tail below).
 // ---------------------------------------------------------------------------------
 struct Unit {
     int64_t j;   // queue entry
@@ -1028,8 +1031,92 @@ __device__ __forceinline__ void unit_finish(const PassArgs& A, int depth_sh, con
     }
 }
 
+// Cooperative tail of a traversal launch. Pairs the k-th idle lane with the k-th lane that has
+// deferred subtrees (k < the smaller count): that lane pops its top entry and the idle lane walks
+// the subtree as a helper of the ray's owner (a helper's own deferred entries can be handed on
+// again; the owner stays the one the results go to). The helper copies the ray and its current
+// closest distance, which only bounds the search: a hit it finds is compared with the owner's when
+// it is merged, under the same rule (nearer, ties to the smaller primitive id), so the owner ends
+// with the hit its own walk would have found.
+__device__ __forceinline__ void delegate_subtrees(unsigned idle, unsigned donors, unsigned lane, bool& busy,
+                                                  bool& helper, int& root, Unit& U, TravRay& R, int* stack) {
+    const int m = min(__popc(idle), __popc(donors));
+    const unsigned lt = (1u << lane) - 1u;
+    const bool take = ((idle >> lane) & 1u) && __popc(idle & lt) < m;
+    const bool give = ((donors >> lane) & 1u) && __popc(donors & lt) < m;
+    int entry = 0;
+    if (give) entry = stack[--R.sp];
+    int src = (int)lane;
+    if (take) {
+        unsigned d = donors;
+        for (int i = __popc(idle & lt); i > 0; --i) d &= d - 1u;
+        src = __ffs(d) - 1;
+    }
+    entry = __shfl_sync(FULL, entry, src);
+    const float o0 = __shfl_sync(FULL, R.o.x, src), o1 = __shfl_sync(FULL, R.o.y, src), o2 = __shfl_sync(FULL, R.o.z, src);
+    const float d0 = __shfl_sync(FULL, R.d.x, src), d1 = __shfl_sync(FULL, R.d.y, src), d2 = __shfl_sync(FULL, R.d.z, src);
+    const float ix = __shfl_sync(FULL, R.ix, src), iy = __shfl_sync(FULL, R.iy, src), iz = __shfl_sync(FULL, R.iz, src);
+    const float ox = __shfl_sync(FULL, R.ox, src), oy = __shfl_sync(FULL, R.oy, src), oz = __shfl_sync(FULL, R.oz, src);
+    const float t = __shfl_sync(FULL, R.t, src);
+    const int any = __shfl_sync(FULL, R.any ? 1 : 0, src);
+    const int q = __shfl_sync(FULL, U.q, src);
+    const int own = __shfl_sync(FULL, helper ? root : (int)lane, src);
+    if (take) {
+        R.o = mk(o0, o1, o2);
+        R.d = mk(d0, d1, d2);
+        R.ix = ix; R.iy = iy; R.iz = iz;
+        R.ox = ox; R.oy = oy; R.oz = oz;
+        R.sx = ix < 0.0f ? 1 : 0;
+        R.sy = iy < 0.0f ? 1 : 0;
+        R.sz = iz < 0.0f ? 1 : 0;
+        R.t = t;
+        R.b1 = R.b2 = 0.0f;
+        R.best = 0x7fffffff;
+        R.node = entry;
+        R.sp = 0;
+        R.any = any != 0;
+        R.hit_any = false;
+        R.complete = true;
+        U.q = q;
+        root = own;
+        helper = true;
+        busy = true;
+    }
+}
+
+// Helpers whose subtree walk ended (lanes in `fin`) hand their result to their owner, one at a
+// time in lane order: a nearer hit (ties: smaller primitive id), an any-hit (which ends the
+// owner's own walk), an overflowed stack.
+__device__ __forceinline__ void merge_helpers(unsigned fin, unsigned lane, bool busy, int root, TravRay& R) {
+    while (fin) {
+        const int src = __ffs(fin) - 1;
+        fin &= fin - 1u;
+        const float ht = __shfl_sync(FULL, R.t, src), hb1 = __shfl_sync(FULL, R.b1, src),
+                    hb2 = __shfl_sync(FULL, R.b2, src);
+        const int hbest = __shfl_sync(FULL, R.best, src);
+        const int hflags = __shfl_sync(FULL, (R.hit_any ? 1 : 0) | (R.complete ? 0 : 2), src);
+        const int hroot = __shfl_sync(FULL, root, src);
+        if ((int)lane == hroot) {
+            if (hbest != 0x7fffffff && (ht < R.t || (ht == R.t && hbest < R.best))) {
+                R.t = ht;
+                R.b1 = hb1;
+                R.b2 = hb2;
+                R.best = hbest;
+            }
+            if (hflags & 1) {
+                R.hit_any = true;
+                if (busy) {
+                    R.node = NODE_EMPTY;
+                    R.sp = 0;
+                }
+            }
+            if (hflags & 2) R.complete = false;
+        }
+    }
+}
+
 template <int NB, int MODE, bool STATS>
-__global__ void __launch_bounds__(256, NB == 1 ? 4 : 3) k_trace(PassArgs A, int depth_ext, int depth_sh) {
+__global__ void __launch_bounds__(256, 3) k_trace(PassArgs A, int depth_ext, int depth_sh) {
     const Node* s_nodes;
     const int n_staged = stage_nodes(A, s_nodes);
     const int64_t n_ext = depth_ext == 1 ? A.n_paths : min((int64_t)A.cnt[CNT_Q + depth_ext], A.qcap);
@@ -1043,9 +1130,14 @@ __global__ void __launch_bounds__(256, NB == 1 ? 4 : 3) k_trace(PassArgs A, int 
     Unit U{0, 0, 0};
     TravCount tc;
     bool busy = false, more = n > 0;
+    // cooperative tail: once the units are all taken, idle lanes take deferred subtrees of the
+    // warp's remaining walks (helper lanes), and an owner whose own walk ended waits for its
+    // helpers before it finishes its unit
+    bool helper = false, waiting = false;
+    int root = 0;   // helper: lane of the walk's owner
     const int refill = min(max(A.refill, 1), 32);
     while (true) {
-        const unsigned idle = __ballot_sync(FULL, !busy);
+        const unsigned idle = __ballot_sync(FULL, !busy && !waiting);
         if (more && __popc(idle) >= refill) {
             const unsigned cnt = (unsigned)__popc(idle);
             uint32_t base = 0;
@@ -1057,13 +1149,36 @@ __global__ void __launch_bounds__(256, NB == 1 ? 4 : 3) k_trace(PassArgs A, int 
                 if (u < n) busy = unit_setup<NB>(A, depth_ext, u, n_eu, U, R);
             }
         }
-        if (!__any_sync(FULL, busy)) {
+        if (!more) {
+            // lanes still free after this iteration's fetch (which may have taken the last units)
+            const unsigned free_now = __ballot_sync(FULL, !busy && !waiting);
+            const unsigned donors = __ballot_sync(FULL, busy && R.sp > 0);
+            if (free_now && donors) delegate_subtrees(free_now, donors, lane, busy, helper, root, U, R, stack);
+        }
+        if (!__any_sync(FULL, busy || waiting)) {
             if (!more) break;
             continue;
         }
-        if (busy && trav_step<STATS>(A.probs[U.q], s_nodes, U.q == A.smem_prob ? n_staged : 0, R, stack, tc)) {
-            unit_finish<NB, MODE, STATS>(A, depth_sh, U, R, tc);
+        bool fin = false;
+        if (busy) fin = trav_step<STATS>(A.probs[U.q], s_nodes, U.q == A.smem_prob ? n_staged : 0, R, stack, tc);
+        if (!__any_sync(FULL, helper || waiting)) {
+            if (fin) {
+                unit_finish<NB, MODE, STATS>(A, depth_sh, U, R, tc);
+                busy = false;
+            }
+            continue;
+        }
+        merge_helpers(__ballot_sync(FULL, fin && helper), lane, busy, root, R);
+        if (fin) {
             busy = false;
+            if (helper) helper = false;
+            else waiting = true;
+        }
+        // an owner's group: itself and the helpers still walking for it
+        const unsigned grp = __match_any_sync(FULL, (busy && helper) ? root : (int)lane);
+        if (waiting && __popc(grp) == 1) {
+            unit_finish<NB, MODE, STATS>(A, depth_sh, U, R, tc);
+            waiting = false;
         }
     }
     if (STATS) {
