@@ -38,10 +38,10 @@ PATHS_PER_PIXEL = 12            # 2 proportional x (primal, adjoint fwd, replay)
 # launch shape); "source" names the commit the kernels were captured at, and the bench reports
 # the figure only while the traversal source is unchanged since then (its sha1 is compared), else
 # null.
-TRACE_DRAM = {"source": "commit b3d29d8 (traversal source as of 92a0514)",
-              "trace_cu_sha1": "fa17a9773e7a31a7d8faccaf1871f9453c311651",
-              "bytes": {"trace_1_primal": 3154155, "trace_1_replay": 3812363,
-                        "trace_2_primal": 2444221, "trace_2_replay": 3009083}}
+TRACE_DRAM = {"source": "commit ca4d55e",
+              "trace_cu_sha1": "f2099e752b1ba3e1268ee412c1956315e0bbc9ca",
+              "bytes": {"trace_1_primal": 3108504, "trace_1_replay": 3759248,
+                        "trace_2_primal": 2468456, "trace_2_replay": 3035280}}
 
 def replica_scene(scene: dict, rank: int) -> dict:
     """Each rank optimises its own replica: the same problem under its own Philox key."""
