@@ -62,3 +62,48 @@ def test_launch_shapes_give_the_same_iterations(shape):
     assert np.abs(Fa).max() > 0
     assert rel_l2(Fb, Fa) < 1e-5 and rel_l2(dFb, dFa) < 1e-5, (rel_l2(Fb, Fa), rel_l2(dFb, dFa))
     assert params_match(pa, pb)
+
+
+@pytest.mark.parametrize("shape", [dict(block_size=256, blocks_per_sm=1), dict(blocks_per_sm=2), dict(trace_refill=32)])
+def test_per_sample_radiance_is_bit_identical_across_launch_shapes(shape):
+    """Each path's radiance is accumulated by one thread per depth, so only the hits could make
+    it depend on the launch shape. The shape decides which lanes take which rays and, once the
+    rays of a launch are all taken, which idle lanes walk which deferred subtrees for which owner;
+    the nearest hit (ties to the smaller primitive id) and the any-hit answer must not change, so
+    every sample of a render (closest hits and shadow rays) and of an FD render pair is the same
+    bit for bit."""
+    torch = need_gpu()
+    from paper_2309_15676_gb300.api import Context
+    w = synth.workload_spiral(64, 48, 64, 16, 32, max_depth=5)
+    tex = torch.from_numpy(w.init_tex).cuda()
+    tex_b = torch.from_numpy(np.clip(w.init_tex + 0.05, 0.0, 1.0).astype(np.float32)).cuda()
+    out = []
+    for kw in ({}, shape):
+        ctx = Context(0, **kw)
+        pid = ctx.add_scene(w.scene)
+        s = ctx.render_samples(pid, tex, spp=6, stream=5, iteration=3).cpu().numpy()
+        a, b = ctx.render_pair(pid, tex, tex_b, spp=3, iteration=3)
+        out.append((s, a.cpu().numpy(), b.cpu().numpy()))
+        ctx.close()
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
+def test_tiny_launches_match_the_oracle():
+    """A 6 x 5 image: every traversal launch holds fewer rays than a block has lanes, so nearly
+    every walk is shared among helper lanes; the samples still match the oracle."""
+    torch = need_gpu()
+    from oracle import orc
+    from paper_2309_15676_gb300.api import Context
+    w = synth.workload_spiral(6, 5, 64, 16, 32, max_depth=5)
+    ctx = Context(0)
+    pid = ctx.add_scene(w.scene)
+    spp = 8
+    got = ctx.render_samples(pid, torch.from_numpy(w.init_tex).cuda(), spp=spp, stream=5, iteration=1).cpu().numpy()
+    ctx.close()
+    npix = 30
+    idx = np.arange(spp * npix)
+    ref = orc.render_samples(orc.Scene(w.scene), w.init_tex, idx % npix, idx // npix, 1, 5)
+    got = got.reshape(spp * npix, 3)
+    ok = np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-6, axis=1)
+    assert ok.all(), np.argwhere(~ok)
