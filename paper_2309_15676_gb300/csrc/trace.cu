@@ -168,13 +168,16 @@ __device__ __forceinline__ void trav_begin(TravRay& R, v3 o, v3 d, float tmax, b
 // One step of the BVH walk: descend through inner nodes (nearest child first, the others
 // deferred) until a leaf, test its triangles, take the next deferred subtree. Returns true when
 // the walk has finished (stack empty, or any-hit found).
+// The caller passes the tree's arrays themselves (kept in registers for the whole walk), not the
+// problem record in global memory: re-reading them from it would put one more dependent load in
+// front of every node fetch.
 template <bool STATS>
-__device__ __forceinline__ bool trav_step(const ProblemDev& P, const Node* s_nodes, int smem_n, TravRay& R,
-                                          int* stack, TravCount& tc) {
+__device__ __forceinline__ bool trav_step(const Node* __restrict__ nodes, const TriGeo* __restrict__ tris,
+                                          const Node* s_nodes, int smem_n, TravRay& R, int* stack, TravCount& tc) {
     const float grow = 1.0f + 4.8e-7f;   // conservative box exit (a few ulp)
     int node = R.node;
     while (node >= 0 && node != NODE_EMPTY) {
-        const NodeRay n = load_node(P.nodes, s_nodes, smem_n, node, R.sx, R.sy, R.sz);
+        const NodeRay n = load_node(nodes, s_nodes, smem_n, node, R.sx, R.sy, R.sz);
         if (STATS) tc.nodes++;
         const float tfar = R.t * grow;
         // slab test of the four children; a miss (or an unused slot) sorts last
@@ -220,7 +223,7 @@ __device__ __forceinline__ bool trav_step(const ProblemDev& P, const Node* s_nod
     const int first = x >> 3, count = (x & 7) + 1;
     if (STATS) tc.prims += count;
     for (int k = 0; k < count; ++k) {
-        const TriGeo T = load_tri(P.tris, first + k);
+        const TriGeo T = load_tri(tris, first + k);
         float t, u, v;
         if (tri_test(T, R.o, R.d, t, u, v)) {
             const int pid = __float_as_int(T.v0.w);
@@ -1135,6 +1138,8 @@ __global__ void __launch_bounds__(256, 3) k_trace(PassArgs A, int depth_ext, int
     // helpers before it finishes its unit
     bool helper = false, waiting = false;
     int root = 0;   // helper: lane of the walk's owner
+    const Node* t_nodes = nullptr;     // the walk's tree (problem U.q)
+    const TriGeo* t_tris = nullptr;
     const int refill = min(max(A.refill, 1), 32);
     while (true) {
         const unsigned idle = __ballot_sync(FULL, !busy && !waiting);
@@ -1147,20 +1152,31 @@ __global__ void __launch_bounds__(256, 3) k_trace(PassArgs A, int depth_ext, int
             if (!busy) {
                 const int64_t u = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
                 if (u < n) busy = unit_setup<NB>(A, depth_ext, u, n_eu, U, R);
+                if (busy) {
+                    t_nodes = A.probs[U.q].nodes;
+                    t_tris = A.probs[U.q].tris;
+                }
             }
         }
         if (!more) {
             // lanes still free after this iteration's fetch (which may have taken the last units)
             const unsigned free_now = __ballot_sync(FULL, !busy && !waiting);
             const unsigned donors = __ballot_sync(FULL, busy && R.sp > 0);
-            if (free_now && donors) delegate_subtrees(free_now, donors, lane, busy, helper, root, U, R, stack);
+            if (free_now && donors) {
+                const bool was = busy;
+                delegate_subtrees(free_now, donors, lane, busy, helper, root, U, R, stack);
+                if (busy && !was) {
+                    t_nodes = A.probs[U.q].nodes;
+                    t_tris = A.probs[U.q].tris;
+                }
+            }
         }
         if (!__any_sync(FULL, busy || waiting)) {
             if (!more) break;
             continue;
         }
         bool fin = false;
-        if (busy) fin = trav_step<STATS>(A.probs[U.q], s_nodes, U.q == A.smem_prob ? n_staged : 0, R, stack, tc);
+        if (busy) fin = trav_step<STATS>(t_nodes, t_tris, s_nodes, U.q == A.smem_prob ? n_staged : 0, R, stack, tc);
         if (!__any_sync(FULL, helper || waiting)) {
             if (fin) {
                 unit_finish<NB, MODE, STATS>(A, depth_sh, U, R, tc);
