@@ -34,5 +34,9 @@ def test_async_target_and_loss_match_synchronous_calls():
         out.append((st["loss"], ctx.get_params(pid).cpu().numpy()))
         ctx.close()
     (la, pa), (lb, pb) = out
-    assert abs(la - lb) <= 1e-9 * lb
+    # the two contexts add their gradient records with float atomics, in whatever order the
+    # records arrive (the lanes that trace a path, and so write its records, depend on the
+    # scheduling), so their parameters, and the loss rendered from them, agree only up to that
+    # rounding; the loss each context delivers asynchronously is checked bit for bit above
+    assert abs(la - lb) <= 1e-6 * lb
     assert params_match(pa, pb)
