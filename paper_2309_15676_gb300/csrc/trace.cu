@@ -69,20 +69,22 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
     return r;
 }
 
+// Moller-Trumbore. The three numerators and the reciprocal are independent and the decision is
+// taken once at the end, without branches: lanes of a warp that would reject at different stages
+// stay together, and the reciprocal's latency overlaps the other products (same arithmetic, same
+// decisions as a test that rejects stage by stage).
 __device__ __forceinline__ bool tri_test(const TriGeo& T, v3 o, v3 d, float& t, float& u, float& v) {
     const v3 e1 = mk(T.e1.x, T.e1.y, T.e1.z), e2 = mk(T.e2.x, T.e2.y, T.e2.z);
     const v3 pv = cross(d, e2);
     const float det = dot(e1, pv);
-    if (det == 0.0f) return false;
-    const float inv = 1.0f / det;
     const v3 tv = o - mk(T.v0.x, T.v0.y, T.v0.z);
-    u = dot(tv, pv) * inv;
-    if (u < 0.0f || u > 1.0f) return false;
     const v3 qv = cross(tv, e1);
-    v = dot(d, qv) * inv;
-    if (v < 0.0f || u + v > 1.0f) return false;
-    t = dot(e2, qv) * inv;
-    return t > 0.0f;
+    const float un = dot(tv, pv), vn = dot(d, qv), tn = dot(e2, qv);
+    const float inv = 1.0f / det;
+    u = un * inv;
+    v = vn * inv;
+    t = tn * inv;
+    return det != 0.0f && u >= 0.0f && u <= 1.0f && v >= 0.0f && u + v <= 1.0f && t > 0.0f;
 }
 
 __device__ __forceinline__ TriGeo load_tri(const TriGeo* __restrict__ tris, int i) {
