@@ -38,10 +38,10 @@ PATHS_PER_PIXEL = 12            # 2 proportional x (primal, adjoint fwd, replay)
 # launch shape); "source" names the commit the kernels were captured at, and the bench reports
 # the figure only while the traversal source is unchanged since then (its sha1 is compared), else
 # null.
-TRACE_DRAM = {"source": "commit f4f2e07",
-              "trace_cu_sha1": "0d1f47185b8696bfc9938445fc56ebba6e59abed",
-              "bytes": {"trace_1_primal": 3144099, "trace_1_replay": 3794245,
-                        "trace_2_primal": 2467920, "trace_2_replay": 3037008}}
+TRACE_DRAM = {"source": "commit a6f1620",
+              "trace_cu_sha1": "c8a35e5e79a8cf39fe16a8d1c35f72c5bf72d3d7",
+              "bytes": {"trace_1_primal": 3139165, "trace_1_replay": 3793813,
+                        "trace_2_primal": 2466795, "trace_2_replay": 3037200}}
 
 def replica_scene(scene: dict, rank: int) -> dict:
     """Each rank optimises its own replica: the same problem under its own Philox key."""
