@@ -224,11 +224,21 @@ __device__ __forceinline__ bool trav_step(const Node* __restrict__ nodes, const 
     const int x = ~node;
     const int first = x >> 3, count = (x & 7) + 1;
     if (STATS) tc.prims += count;
-    for (int k = 0; k < count; ++k) {
-        const TriGeo T = load_tri(tris, first + k);
-        float t, u, v;
-        if (tri_test(T, R.o, R.d, t, u, v)) {
-            const int pid = __float_as_int(T.v0.w);
+    // two triangles per round: their loads go out together and their tests are independent; they
+    // are taken in leaf order, as one at a time would
+    for (int k = 0; k < count; k += 2) {
+        const bool two = k + 1 < count;
+        const TriGeo T0 = load_tri(tris, first + k);
+        const TriGeo T1 = load_tri(tris, first + (two ? k + 1 : k));
+        float t0, u0, v0, t1, u1, v1;
+        const bool h0 = tri_test(T0, R.o, R.d, t0, u0, v0);
+        const bool h1 = two && tri_test(T1, R.o, R.d, t1, u1, v1);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const bool h = m == 0 ? h0 : h1;
+            if (!h) continue;
+            const float t = m == 0 ? t0 : t1, u = m == 0 ? u0 : u1, v = m == 0 ? v0 : v1;
+            const int pid = __float_as_int(m == 0 ? T0.v0.w : T1.v0.w);
             if (R.any) {
                 if (t < R.t) {
                     R.hit_any = true;
