@@ -38,10 +38,10 @@ PATHS_PER_PIXEL = 12            # 2 proportional x (primal, adjoint fwd, replay)
 # launch shape); "source" names the commit the kernels were captured at, and the bench reports
 # the figure only while the traversal source is unchanged since then (its sha1 is compared), else
 # null.
-TRACE_DRAM = {"source": "commit a6f1620",
-              "trace_cu_sha1": "c8a35e5e79a8cf39fe16a8d1c35f72c5bf72d3d7",
-              "bytes": {"trace_1_primal": 3139165, "trace_1_replay": 3793813,
-                        "trace_2_primal": 2466795, "trace_2_replay": 3037200}}
+TRACE_DRAM = {"source": "commit 345b3a8",
+              "trace_cu_sha1": "95d60442f8fff51fe3b6fb008a44a9477b404ea0",
+              "bytes": {"trace_1_primal": 3138256, "trace_1_replay": 3788395,
+                        "trace_2_primal": 2465544, "trace_2_replay": 3037579}}
 
 def replica_scene(scene: dict, rank: int) -> dict:
     """Each rank optimises its own replica: the same problem under its own Philox key."""
